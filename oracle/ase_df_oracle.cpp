@@ -1,0 +1,847 @@
+// ORACLE -- test infrastructure only.
+//
+// A plain, serial, FP64 CPU implementation of the ASE-DF finite-volume residual of
+// "An Adaptive Reconstruction Method for Arbitrary High-Order Accuracy Using
+// Discontinuity Feedback" (arXiv 2410.05489), written from the paper, step by step, so
+// that it can be checked against the paper by eye.  It is the reference the CUDA
+// library is compared with; it shares no code, header, table or constant with it.
+// Only tests/, __graft_entry__.smoke() and bench.py's CPU baseline / reference arm may
+// load it.  It is compiled with -O2 -ffp-contract=off, so every a*b+c rounds twice,
+// exactly as written here.
+//
+// What it computes (section / equation of the paper in brackets):
+//   * zero-mean polynomial basis Z_q on the cell [-1,0]           (Sec. 3, basis list)
+//   * discontinuity strength sigma per Gauss point / per face     (Sec. 3.1, Eq. sigma_m)
+//   * DF factor alpha_S of a stencil                              (Sec. 3.1, Eq. 3.2)
+//   * WENOZ-AO(5,3) with DF (fallback branch)                     (Sec. 3.2)
+//   * linear 5th / 7th / 9th order polynomials                    (Sec. 3.2-3.4)
+//   * stencil selection                                           (Algorithm 1)
+//   * Lax-Friedrichs flux                                         (Sec. 2.3)
+//   * Gauss quadrature over each face and the flux difference     (Sec. 2.1, Eq. 2.3-2.4)
+//   * SSP-RK3                                                     (Sec. 2.3, Eq. SSP-RK3)
+//
+// Readings of places where the paper is garbled or silent (each is listed with its
+// reason in the project's design notes):
+//   G1  Z_q(xi) = xi^q - (-1)^q/(q+1): the printed constants have flipped signs; this is
+//       the only zero-mean basis on [-1,0] in which the printed W_x coefficients solve
+//       the cell-average problem.
+//   G2  "2f_3" in the 7th-order W_x1 is 2 W_3.   G3/G4: missing W_x factors restored.
+//   G5  tau_Z uses the three distinct |beta5 - beta3_k| terms.
+//   G6  beta3_k come from the undamped sub-stencil polynomials.
+//   G7  sigma is feedback: the sigma a residual consumes is the one the previous
+//       residual evaluation produced (previous RK stage); sigma^0 comes from a residual
+//       evaluated with sigma = 0 (all-linear states).
+//   G8  the face sigma is the arithmetic mean of the Gauss-point sigmas.
+//   G9  Ma_n = u_n / c, Ma_t = u_t / c with each side's own sound speed.
+//   G10 A_S sums the faces between the cells of stencil S.
+//   G11 A_S association: A_S3(k) = left + right; A_S5 = (s_-3/2 + s_-1/2) + (s_1/2 + s_3/2);
+//       A_S7 = A_S5 + (s_-5/2 + s_5/2); A_S9 = A_S7 + (s_-7/2 + s_7/2).  This form is
+//       invariant under mirroring the stencil, bit for bit.
+//   G12 smooth iff A_S < sigma_thres; otherwise alpha = sigma_thres / A_S.
+//   G13 the scheme of order r takes the largest m <= r whose stencil is smooth.
+//   G14 the tangential DF of a face state uses the sigma column of its own cell.
+//   G15 G = (r-1)/2 Gauss-Legendre points per face (1 for r = 3), fixed by r.
+//   G16 conservative variables, component by component; alpha shared by components.
+//   G17 local Lax-Friedrichs speed per Gauss point, normal velocity.
+//   G18 dt = cfl / max((|u|+c)/dx + (|v|+c)/dy) over the cell averages and, where an
+//       inflow boundary is present, its fixed inflow state.
+//   G20 order 3: one 3-cell stencil, W_0 + alpha_S3_0 (W_x1 Z_1 + W_x2 Z_2).
+//   G21 positivity: a Gauss point whose reconstructed state (either side) has rho <= 0,
+//       p <= 0 or a non-finite value takes the two cell averages for its flux, and its
+//       sigma is set to 1e30.
+//
+// Data layout: W is [C][ny][nx] (C = 3 in 1D: rho, rho u, E; C = 4 in 2D: rho, rho u,
+// rho v, E), sigma_x is [ny][nx+1] (x-face f sits between cells f-1 and f), sigma_y is
+// [ny+1][nx].  Face fluxes Fx are [C][ny][nx+1], Fy are [C][ny+1][nx].
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+// ---------------------------------------------------------------------------------
+// Scalar type.  The default build is plain double.  The ORACLE_COUNT_OPS build
+// replaces it by a double that counts the FP64 operations done on it (used only to
+// report how much arithmetic the oracle itself performs).
+// ---------------------------------------------------------------------------------
+#ifdef ORACLE_COUNT_OPS
+struct OpCounts { long long add, mul, div, sqrt; };
+static OpCounts g_ops = {0, 0, 0, 0};
+struct real {
+  double v;
+  real() : v(0.0) {}
+  real(double x) : v(x) {}
+};
+static inline real operator+(real a, real b) { g_ops.add++; return real(a.v + b.v); }
+static inline real operator-(real a, real b) { g_ops.add++; return real(a.v - b.v); }
+static inline real operator-(real a) { return real(-a.v); }
+static inline real operator*(real a, real b) { g_ops.mul++; return real(a.v * b.v); }
+static inline real operator/(real a, real b) { g_ops.div++; return real(a.v / b.v); }
+static inline real& operator+=(real& a, real b) { a = a + b; return a; }
+static inline bool operator<(real a, real b) { return a.v < b.v; }
+static inline bool operator<=(real a, real b) { return a.v <= b.v; }
+static inline bool operator>(real a, real b) { return a.v > b.v; }
+static inline double val(real a) { return a.v; }
+static inline real sqrt_(real a) { g_ops.sqrt++; return real(std::sqrt(a.v)); }
+#else
+typedef double real;
+static inline double val(real a) { return a; }
+static inline real sqrt_(real a) { return std::sqrt(a); }
+#endif
+static inline real rabs(real a) { return val(a) < 0.0 ? -a : a; }
+static inline real rmax(real a, real b) { return val(a) < val(b) ? b : a; }
+
+// ---------------------------------------------------------------------------------
+// Problem description.  Its own copy; the Python wrapper fills it field by field.
+// ---------------------------------------------------------------------------------
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2 };
+
+struct OracleParams {
+  int32_t ndim;        // 1 or 2
+  int32_t order;       // r = 3, 5, 7, 9
+  int64_t nx, ny;      // cells (ny = 1 in 1D)
+  double x0, x1, y0, y1;
+  double gamma;
+  double sigma_thres;  // 2.0 in the paper (Sec. 4.1)
+  double cfl;
+  int32_t bc[4];       // x-lo, x-hi, y-lo, y-hi
+  double inflow[4];    // rho, u, v, p of the x-lo inflow band
+  double inflow_lo, inflow_hi;  // the band is inflow_lo < y < inflow_hi
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// Sec. 3 (reading G1): zero-mean basis on the reconstructing cell [-1, 0], face at 0.
+// Cell m of a stencil occupies [m-1, m].
+// ---------------------------------------------------------------------------------
+double Zq(int q, double xi) {
+  if (q == 0) return 1.0;
+  double p = 1.0;
+  for (int i = 0; i < q; ++i) p *= xi;
+  double mean = ((q % 2) == 0 ? 1.0 : -1.0) / (double)(q + 1);  // mean of xi^q on [-1,0]
+  return p - mean;
+}
+
+// ---------------------------------------------------------------------------------
+// Coefficient tables of Sec. 3.2-3.4 as the paper prints them (with readings G2-G4).
+// Row q-1 gives W_xq = (sum_m num[m+4] * W_m) / den, m = -4..4.
+// ---------------------------------------------------------------------------------
+struct CoefRow { double den; double num[9]; };
+
+// Sec. 3.2, the three 3-cell sub-stencils S3_{-1}, S3_0, S3_1.
+const CoefRow kS3[3][2] = {
+  {{1.0, {0, 0, 1, -3, 2, 0, 0, 0, 0}}, {2.0, {0, 0, 1, -2, 1, 0, 0, 0, 0}}},
+  {{1.0, {0, 0, 0, 0, -1, 1, 0, 0, 0}}, {2.0, {0, 0, 0, 1, -2, 1, 0, 0, 0}}},
+  {{1.0, {0, 0, 0, 0, -1, 1, 0, 0, 0}}, {2.0, {0, 0, 0, 0, 1, -2, 1, 0, 0}}},
+};
+// Sec. 3.2, the 5-cell stencil S5.
+const CoefRow kS5[4] = {
+  {12.0, {0, 0, 0, 1, -15, 15, -1, 0, 0}},
+  {8.0, {0, 0, -1, 6, -8, 2, 1, 0, 0}},
+  {6.0, {0, 0, 0, -1, 3, -3, 1, 0, 0}},
+  {24.0, {0, 0, 1, -4, 6, -4, 1, 0, 0}},
+};
+// Sec. 3.3, the 7-cell stencil S7 (reading G2 for W_x1).
+const CoefRow kS7[6] = {
+  {180.0, {0, 0, -2, 25, -245, 245, -25, 2, 0}},
+  {240.0, {0, 7, -57, 210, -230, 15, 63, -8, 0}},
+  {36.0, {0, 0, 1, -11, 28, -28, 11, -1, 0}},
+  {144.0, {0, -2, 15, -39, 46, -24, 3, 1, 0}},
+  {120.0, {0, 0, -1, 5, -10, 10, -5, 1, 0}},
+  {720.0, {0, 1, -6, 15, -20, 15, -6, 1, 0}},
+};
+// Sec. 3.4, the 9-cell stencil S9.
+const CoefRow kS9[8] = {
+  {5040.0, {0, 9, -119, 889, -7175, 7175, -889, 119, -9}},
+  {30240.0, {-205, 2081, -9835, 28679, -27895, -2065, 11459, -2455, 236}},
+  {1440.0, {0, -7, 89, -587, 1365, -1365, 587, -89, 7}},
+  {3456.0, {13, -128, 556, -1160, 1174, -464, -68, 88, -11}},
+  {480.0, {0, 1, -11, 41, -75, 75, -41, 11, -1}},
+  {8640.0, {-5, 46, -170, 334, -380, 250, -86, 10, 1}},
+  {5040.0, {0, -1, 7, -21, 35, -35, 21, -7, 1}},
+  {40320.0, {1, -8, 28, -56, 70, -56, 28, -8, 1}},
+};
+
+// W_xq of one table row from the stencil values Wm[m+4], m = -4..4.
+real coef(const CoefRow& row, const real* Wm) {
+  real s = 0.0;
+  for (int i = 0; i < 9; ++i)
+    if (row.num[i] != 0.0) s += real(row.num[i]) * Wm[i];
+  return s / real(row.den);
+}
+
+// P(xi) = W_0 + sum_q W_xq Z_q(xi) for the table of an n-cell stencil (n-1 rows).
+real eval_linear(const CoefRow* rows, int nrows, const real* Wm, double xi) {
+  real P = Wm[4];
+  for (int q = 1; q <= nrows; ++q) P += coef(rows[q - 1], Wm) * real(Zq(q, xi));
+  return P;
+}
+
+// Sec. 3.1, Eq. (3.2): DF factor of a stencil from the summed face strengths A.
+real df_alpha(real A, double thres) {
+  if (A < real(thres)) return real(1.0);  // reading G12
+  return real(thres) / A;
+}
+
+// Stencil sums of Sec. 3.1 with the association of reading G11.  sig[m+3] is the face
+// strength sigma_{m-1/2} between stencil cells m-1 and m, m = -3..4.
+struct StencilSums { real s3m, s30, s3p, s5, s7, s9; };
+StencilSums stencil_sums(const real* sig) {
+  // sig index: face m - 1/2 -> m + 3 (m = -3..4): s_{-7/2}=0, s_{-5/2}=1, s_{-3/2}=2,
+  // s_{-1/2}=3, s_{1/2}=4, s_{3/2}=5, s_{5/2}=6, s_{7/2}=7.
+  StencilSums A;
+  A.s3m = sig[2] + sig[3];
+  A.s30 = sig[3] + sig[4];
+  A.s3p = sig[4] + sig[5];
+  A.s5 = (sig[2] + sig[3]) + (sig[4] + sig[5]);
+  A.s7 = A.s5 + (sig[1] + sig[6]);
+  A.s9 = A.s7 + (sig[0] + sig[7]);
+  return A;
+}
+
+// Sec. 3.2: smoothness indicator of a 3-cell polynomial W_0 + a1 Z_1 + a2 Z_2,
+// beta = sum_q int_{-1}^{0} (d^q P / d xi^q)^2 d xi  (Eq. LocalSmoothnessIndicator with
+// the Delta x powers absorbed by the local coordinate), which integrates to
+// (a1 - a2)^2 + (13/3) a2^2.
+real beta3(real a1, real a2) {
+  real d = a1 - a2;
+  return d * d + real(13.0 / 3.0) * a2 * a2;
+}
+
+// Linear weights of Sec. 3.2 with d_Hi = d_Lo = 0.85.
+const double kDHi = 0.85, kDLo = 0.85;
+const double kEps = 1e-6;
+
+// WENOZ-AO(5,3) with DF (Sec. 3.2), one component, evaluated at npts points.
+// alpha[0..2] = alpha of S3_{-1}, S3_0, S3_1; alpha[3] = alpha of S5.
+// force_linear_weights replaces the normalised nonlinear weights by the linear ones
+// (used only by the tests of the AO identity).
+void weno_ao53_df(const real* Wm, const real* alpha, int npts, const double* xi, real* out,
+                  bool force_linear_weights, real* beta_out) {
+  real a1[3], a2[3];
+  for (int k = 0; k < 3; ++k) {
+    a1[k] = coef(kS3[k][0], Wm);
+    a2[k] = coef(kS3[k][1], Wm);
+  }
+  real b[4];
+  for (int q = 0; q < 4; ++q) b[q] = coef(kS5[q], Wm);
+
+  // smoothness indicators (reading G6: undamped polynomials) and the simple beta5
+  real beta[3];
+  for (int k = 0; k < 3; ++k) beta[k] = beta3(a1[k], a2[k]);
+  real beta5 = (beta[0] + real(4.0) * beta[1] + beta[2]) / real(6.0) + rabs(beta[0] - beta[2]);
+  // tau_Z (reading G5)
+  real tau = (rabs(beta5 - beta[0]) + rabs(beta5 - beta[1]) + rabs(beta5 - beta[2])) / real(3.0);
+  if (beta_out) {
+    beta_out[0] = beta[0]; beta_out[1] = beta[1]; beta_out[2] = beta[2];
+    beta_out[3] = beta5; beta_out[4] = tau;
+  }
+
+  // linear weights
+  const double d5 = kDHi;
+  const double d3[3] = {(1.0 - kDHi) * (1.0 - kDLo) / 2.0, (1.0 - kDHi) * kDLo,
+                        (1.0 - kDHi) * (1.0 - kDLo) / 2.0};
+  // WENO-Z weights and their normalisation
+  real w5 = real(d5) * (real(1.0) + (tau * tau) / ((beta5 + real(kEps)) * (beta5 + real(kEps))));
+  real w3[3];
+  for (int k = 0; k < 3; ++k)
+    w3[k] = real(d3[k]) * (real(1.0) + (tau * tau) / ((beta[k] + real(kEps)) * (beta[k] + real(kEps))));
+  real wsum = w5 + w3[0] + w3[1] + w3[2];
+  real wb5 = w5 / wsum;
+  real wb3[3] = {w3[0] / wsum, w3[1] / wsum, w3[2] / wsum};
+  if (force_linear_weights) {
+    wb5 = real(d5);
+    for (int k = 0; k < 3; ++k) wb3[k] = real(d3[k]);
+  }
+
+  for (int p = 0; p < npts; ++p) {
+    const double x = xi[p];
+    // DF-damped polynomials
+    real P3[3];
+    for (int k = 0; k < 3; ++k)
+      P3[k] = Wm[4] + alpha[k] * (a1[k] * real(Zq(1, x)) + a2[k] * real(Zq(2, x)));
+    real P5 = Wm[4] + alpha[3] * (b[0] * real(Zq(1, x)) + b[1] * real(Zq(2, x)) +
+                                  b[2] * real(Zq(3, x)) + b[3] * real(Zq(4, x)));
+    // AO combination
+    real inner = P5 / real(d5);
+    for (int k = 0; k < 3; ++k) inner = inner - (real(d3[k]) / real(d5)) * P3[k];
+    real P = wb5 * inner;
+    for (int k = 0; k < 3; ++k) P += wb3[k] * P3[k];
+    out[p] = P;
+  }
+}
+
+// Branch identifiers (also the histogram slots).
+enum {
+  BR_LIN9 = 0, BR_LIN7 = 1, BR_LIN5 = 2, BR_WENO = 3, BR_LIN3 = 4, BR_DF3 = 5, BR_FIRST = 6,
+  BR_COUNT = 7
+};
+
+// Algorithm 1 capped at the scheme order r (reading G13) for one cell and one
+// component.  Wm[m+4] = W_m (m = -k..k, others unused), sig[m+3] = sigma_{m-1/2}.
+// Evaluates the chosen polynomial at npts points xi[] into out[]; returns the branch.
+int ase_df_reconstruct(int r, const real* Wm, const real* sig, double thres, int npts,
+                       const double* xi, real* out) {
+  StencilSums A = stencil_sums(sig);
+  if (r == 3) {  // reading G20
+    real a = df_alpha(A.s30, thres);
+    real a1 = coef(kS3[1][0], Wm), a2 = coef(kS3[1][1], Wm);
+    for (int p = 0; p < npts; ++p)
+      out[p] = Wm[4] + a * (a1 * real(Zq(1, xi[p])) + a2 * real(Zq(2, xi[p])));
+    return (A.s30 < real(thres)) ? BR_LIN3 : BR_DF3;
+  }
+  if (!(A.s5 < real(thres))) {
+    // alpha_S5 < 1: WENOZ-AO(5,3) with DF
+    real alpha[4] = {df_alpha(A.s3m, thres), df_alpha(A.s30, thres), df_alpha(A.s3p, thres),
+                     df_alpha(A.s5, thres)};
+    weno_ao53_df(Wm, alpha, npts, xi, out, false, nullptr);
+    return BR_WENO;
+  }
+  int m = 5;
+  if (r >= 7 && A.s7 < real(thres)) {
+    m = 7;
+    if (r >= 9 && A.s9 < real(thres)) m = 9;
+  }
+  const CoefRow* rows = (m == 5) ? kS5 : (m == 7) ? kS7 : kS9;
+  for (int p = 0; p < npts; ++p) out[p] = eval_linear(rows, m - 1, Wm, xi[p]);
+  return (m == 5) ? BR_LIN5 : (m == 7) ? BR_LIN7 : BR_LIN9;
+}
+
+// ---------------------------------------------------------------------------------
+// Gauss-Legendre points on [0,1] (reading G15): closed forms for 1..4 points.
+// ---------------------------------------------------------------------------------
+void gauss_legendre01(int G, double* t, double* w) {
+  if (G == 1) {
+    t[0] = 0.5; w[0] = 1.0;
+  } else if (G == 2) {
+    double a = 1.0 / std::sqrt(3.0);
+    t[0] = 0.5 * (1.0 - a); t[1] = 0.5 * (1.0 + a);
+    w[0] = 0.5; w[1] = 0.5;
+  } else if (G == 3) {
+    double a = std::sqrt(3.0 / 5.0);
+    t[0] = 0.5 * (1.0 - a); t[1] = 0.5; t[2] = 0.5 * (1.0 + a);
+    w[0] = 5.0 / 18.0; w[1] = 8.0 / 18.0; w[2] = 5.0 / 18.0;
+  } else {  // G == 4
+    double s = 2.0 / 7.0 * std::sqrt(6.0 / 5.0);
+    double xa = std::sqrt(3.0 / 7.0 - s), xb = std::sqrt(3.0 / 7.0 + s);
+    double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+    t[0] = 0.5 * (1.0 - xb); t[1] = 0.5 * (1.0 - xa); t[2] = 0.5 * (1.0 + xa); t[3] = 0.5 * (1.0 + xb);
+    w[0] = 0.5 * wb; w[1] = 0.5 * wa; w[2] = 0.5 * wa; w[3] = 0.5 * wb;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Euler physics of Sec. 2.3.
+// ---------------------------------------------------------------------------------
+struct Prim { real rho, un, ut, p, c; bool ok; };
+
+// Primitive variables of a state given in the face frame: q = (rho, rho u_n, [rho u_t], E).
+Prim primitives(const real* q, int C, double gamma) {
+  Prim s;
+  s.rho = q[0];
+  s.un = q[1] / q[0];
+  s.ut = (C == 4) ? q[2] / q[0] : real(0.0);
+  real E = q[C - 1];
+  real kinetic = real(0.5) * q[0] * (s.un * s.un + s.ut * s.ut);
+  s.p = real(gamma - 1.0) * (E - kinetic);
+  s.ok = std::isfinite(val(s.rho)) && std::isfinite(val(s.p)) && std::isfinite(val(s.un)) &&
+         std::isfinite(val(s.ut)) && val(s.rho) > 0.0 && val(s.p) > 0.0;
+  s.c = s.ok ? sqrt_(real(gamma) * s.p / s.rho) : real(0.0);
+  return s;
+}
+
+// Physical flux in the face frame: (rho u_n, rho u_n^2 + p, rho u_n u_t, u_n (E + p)).
+void phys_flux(const real* q, const Prim& s, int C, real* F) {
+  F[0] = q[1];
+  F[1] = q[1] * s.un + s.p;
+  if (C == 4) F[2] = q[1] * s.ut;
+  F[C - 1] = s.un * (q[C - 1] + s.p);
+}
+
+// Sec. 3.1, discontinuity strength of one Gauss point (readings G9).
+real sigma_point(const Prim& L, const Prim& R, int C) {
+  real dp = rabs(L.p - R.p);
+  real s = dp / L.p + dp / R.p;
+  real dmn = L.un / L.c - R.un / R.c;
+  s += dmn * dmn;
+  if (C == 4) {
+    real dmt = L.ut / L.c - R.ut / R.c;
+    s += dmt * dmt;
+  }
+  return s;
+}
+
+const double kSigmaBig = 1e30;  // reading G21
+
+// Sec. 2.3: local Lax-Friedrichs flux at one Gauss point plus its sigma.  qL, qR are
+// the reconstructed states in the face frame, cL, cR the cell averages of the two
+// cells (first-order states for reading G21).  Returns true if the positivity
+// fallback was taken.
+bool lf_flux_point(const real* qL, const real* qR, const real* cL, const real* cR, int C,
+                   double gamma, real* F, real* sigma) {
+  Prim L = primitives(qL, C, gamma), R = primitives(qR, C, gamma);
+  bool fallback = !(L.ok && R.ok);
+  const real* a = qL;
+  const real* b = qR;
+  if (fallback) {
+    a = cL; b = cR;
+    L = primitives(a, C, gamma);
+    R = primitives(b, C, gamma);
+  }
+  real FL[4], FR[4];
+  phys_flux(a, L, C, FL);
+  phys_flux(b, R, C, FR);
+  real lam = rmax(rabs(L.un) + L.c, rabs(R.un) + R.c);
+  for (int c = 0; c < C; ++c)
+    F[c] = real(0.5) * (FL[c] + FR[c]) - real(0.5) * lam * (b[c] - a[c]);
+  *sigma = fallback ? real(kSigmaBig) : sigma_point(L, R, C);
+  return fallback;
+}
+
+// ---------------------------------------------------------------------------------
+// Ghost cells (boundary conditions) as index maps.
+// ---------------------------------------------------------------------------------
+int64_t wrap(int64_t i, int64_t n) { int64_t m = i % n; return m < 0 ? m + n : m; }
+int64_t clampi(int64_t i, int64_t lo, int64_t hi) { return i < lo ? lo : (i > hi ? hi : i); }
+
+struct Grid {
+  const OracleParams* p;
+  int C;
+  int64_t nx, ny;
+  double dx, dy;
+
+  int64_t cell_x(int64_t i) const {
+    int bc = (i < 0) ? p->bc[0] : p->bc[1];
+    return bc == BC_PERIODIC ? wrap(i, nx) : clampi(i, 0, nx - 1);
+  }
+  int64_t cell_y(int64_t j) const {
+    if (p->ndim == 1) return 0;
+    int bc = (j < 0) ? p->bc[2] : p->bc[3];
+    return bc == BC_PERIODIC ? wrap(j, ny) : clampi(j, 0, ny - 1);
+  }
+  int64_t face_x(int64_t f) const {  // x-face index 0..nx
+    if (f >= 0 && f <= nx) return f;
+    int bc = (f < 0) ? p->bc[0] : p->bc[1];
+    return bc == BC_PERIODIC ? wrap(f, nx) : clampi(f, 0, nx);
+  }
+  int64_t face_y(int64_t g) const {  // y-face index 0..ny
+    if (g >= 0 && g <= ny) return g;
+    int bc = (g < 0) ? p->bc[2] : p->bc[3];
+    return bc == BC_PERIODIC ? wrap(g, ny) : clampi(g, 0, ny);
+  }
+  // Conservative value of component c of (possibly ghost) cell (i, j).
+  real W(const double* Wd, int c, int64_t i, int64_t j) const {
+    if (i < 0 && p->bc[0] == BC_INFLOW_BAND) {
+      double yc = p->y0 + ((double)j + 0.5) * dy;
+      if (yc > p->inflow_lo && yc < p->inflow_hi) return inflow_cons(c);
+    }
+    int64_t ii = cell_x(i), jj = cell_y(j);
+    return real(Wd[((int64_t)c * ny + jj) * nx + ii]);
+  }
+  real inflow_cons(int c) const {
+    double rho = p->inflow[0], u = p->inflow[1], v = p->inflow[2], pr = p->inflow[3];
+    double vv = (p->ndim == 2) ? v : 0.0;
+    double E = pr / (p->gamma - 1.0) + 0.5 * rho * (u * u + vv * vv);
+    if (c == 0) return real(rho);
+    if (c == 1) return real(rho * u);
+    if (p->ndim == 2 && c == 2) return real(rho * v);
+    return real(E);
+  }
+  double sx(const double* s, int64_t f, int64_t j) const {
+    return s[cell_y(j) * (nx + 1) + face_x(f)];
+  }
+  double sy(const double* s, int64_t i, int64_t g) const {
+    return s[face_y(g) * nx + cell_x(i)];
+  }
+};
+
+Grid make_grid(const OracleParams* p) {
+  Grid g;
+  g.p = p;
+  g.C = (p->ndim == 1) ? 3 : 4;
+  g.nx = p->nx;
+  g.ny = (p->ndim == 1) ? 1 : p->ny;
+  g.dx = (p->x1 - p->x0) / (double)p->nx;
+  g.dy = (p->ndim == 1) ? 1.0 : (p->y1 - p->y0) / (double)p->ny;
+  return g;
+}
+
+// ---------------------------------------------------------------------------------
+// Normal reconstruction of one cell along x (dir 0) or y (dir 1) to one of its two
+// faces.  to_right = true: the face at xi = 0 (the paper's left state of face i+1/2);
+// false: the face on the other side, done on the mirrored stencil (the right state of
+// face i-1/2).  Fills out[c] for all components; returns the branch of component 0
+// (the branch does not depend on the component).
+// ---------------------------------------------------------------------------------
+int normal_recon(const Grid& g, const double* Wd, const double* sig_n, int dir, int64_t i,
+                 int64_t j, bool to_right, real* out) {
+  const int r = g.p->order;
+  const int k = (r - 1) / 2;
+  const int s = to_right ? 1 : -1;  // mirrored stencil: W'_m = W_{-m}
+  real sig[8];
+  for (int m = -3; m <= 4; ++m) {
+    sig[m + 3] = real(0.0);
+    if (m < -k + 1 || m > k) continue;
+    // face between stencil cells m-1 and m (mirrored: between -m+1 and -m)
+    if (dir == 0) {
+      int64_t f = to_right ? i + m : i - m + 1;
+      sig[m + 3] = real(g.sx(sig_n, f, j));
+    } else {
+      int64_t f = to_right ? j + m : j - m + 1;
+      sig[m + 3] = real(g.sy(sig_n, i, f));
+    }
+  }
+  int branch = 0;
+  const double xi0 = 0.0;
+  for (int c = 0; c < g.C; ++c) {
+    real Wm[9];
+    for (int m = -4; m <= 4; ++m) {
+      Wm[m + 4] = real(0.0);
+      if (m < -k || m > k) continue;
+      Wm[m + 4] = (dir == 0) ? g.W(Wd, c, i + s * m, j) : g.W(Wd, c, i, j + s * m);
+    }
+    branch = ase_df_reconstruct(r, Wm, sig, g.p->sigma_thres, 1, &xi0, &out[c]);
+  }
+  return branch;
+}
+
+// Tangential reconstruction of face line-averages Q[t][c] (t = 0..2k over the
+// tangential stencil) at the G Gauss points, with the tangential face strengths
+// sigt[m+3] of the reconstructing cell's column / row.
+int tangential_recon(const Grid& g, const real Q[9][4], const real* sigt, int G,
+                     const double* eta, real out[4][4]) {
+  const int r = g.p->order;
+  const int k = (r - 1) / 2;
+  int branch = 0;
+  for (int c = 0; c < g.C; ++c) {
+    real Wm[9];
+    for (int m = -4; m <= 4; ++m) Wm[m + 4] = (m < -k || m > k) ? real(0.0) : Q[m + k][c];
+    real vals[4];
+    branch = ase_df_reconstruct(r, Wm, sigt, g.p->sigma_thres, G, eta, vals);
+    for (int q = 0; q < G; ++q) out[q][c] = vals[q];
+  }
+  return branch;
+}
+
+// Swap the normal and tangential momentum so that a y-face state is in its face frame
+// (Sec. 2.1, rotation T by 90 degrees; the sign of the tangential component does not
+// enter the Lax-Friedrichs flux or sigma, so a plain swap is used).
+void to_face_frame(real* q, int dir, int C) {
+  if (dir == 1 && C == 4) { real t = q[1]; q[1] = q[2]; q[2] = t; }
+}
+
+// ---------------------------------------------------------------------------------
+// Sec. 2.1 / 2.3: all face fluxes of one direction, with sigma_out and branch counts.
+// dir 0: x-faces f = 0..nx of every row j; dir 1: y-faces g = 0..ny of every column i.
+// Two passes: (1) the normal reconstruction of every cell of the band of rows (or
+// columns) the tangential stencils reach, to both of its faces; (2) per face, the
+// tangential reconstruction at the Gauss points and the Gauss-point fluxes.
+// ---------------------------------------------------------------------------------
+void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const double* sy_in,
+                 int dir, double* Fout, double* sig_out, int64_t* hist) {
+  const int r = g.p->order;
+  const int k = (r - 1) / 2;
+  const int C = g.C;
+  const bool twoD = (g.p->ndim == 2);
+  const int G = twoD ? ((r == 3) ? 1 : k) : 1;
+  const int kt = twoD ? k : 0;  // tangential half-width
+  double tq[4], wq[4], eta[4];
+  gauss_legendre01(G, tq, wq);
+  for (int q = 0; q < G; ++q) eta[q] = tq[q] - 1.0;  // Gauss points of the cell [-1, 0]
+
+  // extents: along the sweep (normal) n cells, across (tangential) m lines
+  const int64_t n = (dir == 0) ? g.nx : g.ny;
+  const int64_t mlines = (dir == 0) ? g.ny : g.nx;
+  const double* sig_n = (dir == 0) ? sx_in : sy_in;  // normal-direction strengths
+  const double* sig_t = (dir == 0) ? sy_in : sx_in;  // tangential-direction strengths
+
+  // Pass 1: normal reconstructions of cells a = -1..n (index a+1) on lines
+  // b = -kt..mlines-1+kt (index b+kt), to the "plus" face (QP) and "minus" face (QM).
+  const int64_t na = n + 2, nb = mlines + 2 * kt;
+  std::vector<real> QP((size_t)(na * nb * C)), QM((size_t)(na * nb * C));
+  std::vector<int> brP((size_t)(na * nb)), brM((size_t)(na * nb));
+  for (int64_t b = -kt; b < mlines + kt; ++b) {
+    for (int64_t a = -1; a <= n; ++a) {
+      int64_t i = (dir == 0) ? a : b, j = (dir == 0) ? b : a;
+      size_t idx = (size_t)((b + kt) * na + (a + 1));
+      real out[4];
+      brP[idx] = normal_recon(g, Wd, sig_n, dir, i, j, true, out);
+      for (int c = 0; c < C; ++c) QP[idx * C + c] = out[c];
+      brM[idx] = normal_recon(g, Wd, sig_n, dir, i, j, false, out);
+      for (int c = 0; c < C; ++c) QM[idx * C + c] = out[c];
+    }
+  }
+
+  // Pass 2: faces.  Face f (0..n) on line b sits between cells f-1 and f.
+  for (int64_t b = 0; b < mlines; ++b) {
+    for (int64_t f = 0; f <= n; ++f) {
+      real stateL[4][4], stateR[4][4];
+      for (int side = 0; side < 2; ++side) {
+        const int64_t a = (side == 0) ? f - 1 : f;   // reconstructing cell
+        const std::vector<real>& Qv = (side == 0) ? QP : QM;
+        real (*state)[4] = (side == 0) ? stateL : stateR;
+        if (!twoD) {
+          size_t idx = (size_t)(a + 1);
+          for (int c = 0; c < C; ++c) state[0][c] = Qv[idx * C + c];
+          hist[(side == 0 ? brP : brM)[idx]]++;
+          continue;
+        }
+        real Q[9][4];
+        for (int t = -k; t <= k; ++t) {
+          size_t idx = (size_t)((b + t + kt) * na + (a + 1));
+          for (int c = 0; c < C; ++c) Q[t + k][c] = Qv[idx * C + c];
+        }
+        hist[(side == 0 ? brP : brM)[(size_t)((b + kt) * na + (a + 1))]]++;
+        // tangential strengths of the reconstructing cell's column (dir 0) / row (dir 1)
+        real sigt[8];
+        for (int m = -3; m <= 4; ++m) {
+          sigt[m + 3] = real(0.0);
+          if (m < -k + 1 || m > k) continue;
+          if (dir == 0) sigt[m + 3] = real(g.sy(sig_t, a, b + m));
+          else sigt[m + 3] = real(g.sx(sig_t, b + m, a));
+        }
+        int brt = tangential_recon(g, Q, sigt, G, eta, state);
+        hist[brt]++;
+      }
+      // cell averages of the two cells (first-order states)
+      real cL[4], cR[4];
+      for (int c = 0; c < C; ++c) {
+        if (dir == 0) { cL[c] = g.W(Wd, c, f - 1, b); cR[c] = g.W(Wd, c, f, b); }
+        else { cL[c] = g.W(Wd, c, b, f - 1); cR[c] = g.W(Wd, c, b, f); }
+      }
+      to_face_frame(cL, dir, C);
+      to_face_frame(cR, dir, C);
+      real Fsum[4] = {0.0, 0.0, 0.0, 0.0};
+      real ssum = 0.0;
+      for (int q = 0; q < G; ++q) {
+        real qL[4], qR[4];
+        for (int c = 0; c < C; ++c) { qL[c] = stateL[q][c]; qR[c] = stateR[q][c]; }
+        to_face_frame(qL, dir, C);
+        to_face_frame(qR, dir, C);
+        real F[4], s;
+        if (lf_flux_point(qL, qR, cL, cR, C, g.p->gamma, F, &s)) hist[BR_FIRST]++;
+        to_face_frame(F, dir, C);  // back to (x, y) momentum order
+        for (int c = 0; c < C; ++c) Fsum[c] += real(wq[q]) * F[c];
+        ssum += s;
+      }
+      real sface = ssum / real((double)G);  // reading G8
+      if (dir == 0) {
+        for (int c = 0; c < C; ++c) Fout[((int64_t)c * g.ny + b) * (g.nx + 1) + f] = val(Fsum[c]);
+        sig_out[b * (g.nx + 1) + f] = val(sface);
+      } else {
+        for (int c = 0; c < C; ++c) Fout[((int64_t)c * (g.ny + 1) + f) * g.nx + b] = val(Fsum[c]);
+        sig_out[f * g.nx + b] = val(sface);
+      }
+    }
+  }
+}
+
+// Sec. 2.1, Eq. (2.3): L = -(1/|Omega|) sum over faces |l| * (Gauss-averaged flux . n).
+int residual(const OracleParams* p, const double* W, const double* sx_in, const double* sy_in,
+             double* L, double* sx_out, double* sy_out, double* Fx_out, double* Fy_out,
+             int64_t* hist) {
+  Grid g = make_grid(p);
+  const int C = g.C;
+  const int64_t nx = g.nx, ny = g.ny;
+  std::vector<double> Fx((size_t)(C * ny * (nx + 1)));
+  std::vector<double> Fy;
+  face_fluxes(g, W, sx_in, sy_in, 0, Fx.data(), sx_out, hist);
+  if (p->ndim == 2) {
+    Fy.resize((size_t)(C * (ny + 1) * nx));
+    face_fluxes(g, W, sx_in, sy_in, 1, Fy.data(), sy_out, hist);
+  }
+  for (int c = 0; c < C; ++c)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        real dFx = real(Fx[((int64_t)c * ny + j) * (nx + 1) + i + 1]) -
+                   real(Fx[((int64_t)c * ny + j) * (nx + 1) + i]);
+        real Lv = -(dFx / real(g.dx));
+        if (p->ndim == 2) {
+          real dFy = real(Fy[((int64_t)c * (ny + 1) + j + 1) * nx + i]) -
+                     real(Fy[((int64_t)c * (ny + 1) + j) * nx + i]);
+          Lv = Lv - dFy / real(g.dy);
+        }
+        L[((int64_t)c * ny + j) * nx + i] = val(Lv);
+      }
+  if (Fx_out) std::memcpy(Fx_out, Fx.data(), Fx.size() * sizeof(double));
+  if (Fy_out && p->ndim == 2) std::memcpy(Fy_out, Fy.data(), Fy.size() * sizeof(double));
+  return 0;
+}
+
+// Largest wave speed sum over the cells: max((|u|+c)/dx + (|v|+c)/dy); also reports
+// whether any cell average is non-physical.
+double max_speed(const OracleParams* p, const double* W, int* bad) {
+  Grid g = make_grid(p);
+  const int C = g.C;
+  const int64_t ncell = g.nx * g.ny;
+  double smax = 0.0;
+  *bad = 0;
+  for (int64_t n = 0; n < ncell; ++n) {
+    real q[4];
+    for (int c = 0; c < C; ++c) q[c] = real(W[(int64_t)c * ncell + n]);
+    Prim s = primitives(q, C, p->gamma);
+    if (!s.ok) { *bad = 1; continue; }
+    real v = (rabs(s.un) + s.c) / real(g.dx);
+    if (C == 4) v = v + (rabs(s.ut) + s.c) / real(g.dy);
+    if (val(v) > smax) smax = val(v);
+  }
+  // reading G18: the fixed inflow state of an inflow boundary also bounds the step
+  if (p->bc[0] == BC_INFLOW_BAND) {
+    real q[4];
+    for (int c = 0; c < C; ++c) q[c] = g.inflow_cons(c);
+    Prim s = primitives(q, C, p->gamma);
+    real v = (rabs(s.un) + s.c) / real(g.dx);
+    if (C == 4) v = v + (rabs(s.ut) + s.c) / real(g.dy);
+    if (val(v) > smax) smax = val(v);
+  }
+  return smax;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// C entry points (loaded by the Python wrapper oracle/oracle.py).
+// ---------------------------------------------------------------------------------
+extern "C" {
+
+int oracle_version() { return 1; }
+
+// One residual evaluation.  hist[BR_COUNT] accumulates branch counts (may be NULL);
+// Fx / Fy (may be NULL) receive the Gauss-averaged face fluxes.
+int oracle_residual(const OracleParams* p, const double* W, const double* sx_in,
+                    const double* sy_in, double* L, double* sx_out, double* sy_out,
+                    double* Fx, double* Fy, int64_t* hist) {
+  int64_t h[BR_COUNT] = {0};
+  int rc = residual(p, W, sx_in, sy_in, L, sx_out, sy_out, Fx, Fy, h);
+  if (hist) for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[b];
+  return rc;
+}
+
+// CFL time step dt = cfl / max((|u|+c)/dx + (|v|+c)/dy); returns -1 if a cell average
+// is non-physical.
+double oracle_cfl_dt(const OracleParams* p, const double* W) {
+  int bad = 0;
+  double s = max_speed(p, W, &bad);
+  if (bad || !(s > 0.0)) return -1.0;
+  return p->cfl / s;
+}
+
+// One SSP-RK3 step (Sec. 2.3) in place, with the sigma feedback of reading G7: each
+// stage consumes the sigma the previous stage produced; sx / sy hold sigma^n on entry
+// and the last stage's sigma on exit.  dt <= 0 takes the CFL step.  Returns the dt
+// used (negative on a non-physical cell average).
+double oracle_step(const OracleParams* p, double* W, double* sx, double* sy, double dt,
+                   int64_t* hist) {
+  Grid g = make_grid(p);
+  const int64_t nW = (int64_t)g.C * g.nx * g.ny;
+  const int64_t nsx = g.ny * (g.nx + 1);
+  const int64_t nsy = (p->ndim == 2) ? (g.ny + 1) * g.nx : 1;
+  if (!(dt > 0.0)) {
+    dt = oracle_cfl_dt(p, W);
+    if (dt < 0.0) return dt;
+  }
+  std::vector<double> Wn(W, W + nW), W1((size_t)nW), W2((size_t)nW), L((size_t)nW);
+  std::vector<double> sxa((size_t)nsx), sya((size_t)nsy), sxb((size_t)nsx), syb((size_t)nsy);
+  const real rdt = real(dt);
+  // stage 1
+  oracle_residual(p, Wn.data(), sx, sy, L.data(), sxa.data(), sya.data(), nullptr, nullptr, hist);
+  for (int64_t n = 0; n < nW; ++n) W1[n] = val(real(Wn[n]) + rdt * real(L[n]));
+  // stage 2
+  oracle_residual(p, W1.data(), sxa.data(), sya.data(), L.data(), sxb.data(), syb.data(), nullptr,
+                  nullptr, hist);
+  for (int64_t n = 0; n < nW; ++n)
+    W2[n] = val(real(0.75) * real(Wn[n]) + real(0.25) * real(W1[n]) + real(0.25) * rdt * real(L[n]));
+  // stage 3
+  oracle_residual(p, W2.data(), sxb.data(), syb.data(), L.data(), sx, sy, nullptr, nullptr, hist);
+  for (int64_t n = 0; n < nW; ++n)
+    W[n] = val(real(1.0 / 3.0) * real(Wn[n]) + real(2.0 / 3.0) * real(W2[n]) +
+               real(2.0 / 3.0) * rdt * real(L[n]));
+  return dt;
+}
+
+// sigma^0 (reading G7): the sigma of a residual evaluated with sigma_in = 0.
+int oracle_prime_sigma(const OracleParams* p, const double* W, double* sx, double* sy) {
+  Grid g = make_grid(p);
+  const int64_t nW = (int64_t)g.C * g.nx * g.ny;
+  const int64_t nsx = g.ny * (g.nx + 1);
+  const int64_t nsy = (p->ndim == 2) ? (g.ny + 1) * g.nx : 1;
+  std::vector<double> L((size_t)nW), zx((size_t)nsx, 0.0), zy((size_t)nsy, 0.0);
+  return oracle_residual(p, W, zx.data(), zy.data(), L.data(), sx, sy, nullptr, nullptr, nullptr);
+}
+
+// One-dimensional ASE-DF reconstruction of one cell (Algorithm 1 capped at r), for
+// tests: vals[m+k] = W_m (m = -k..k), sig[m+k-1] = sigma_{m-1/2} (m = -k+1..k);
+// evaluates the chosen polynomial at npts points xi (cell = [-1, 0]).  Returns the
+// branch id.
+int oracle_reconstruct(int r, const double* vals, const double* sig, double thres, int npts,
+                       const double* xi, double* out) {
+  const int k = (r - 1) / 2;
+  real Wm[9], s[8], o[16];
+  for (int m = -4; m <= 4; ++m) Wm[m + 4] = (m < -k || m > k) ? real(0.0) : real(vals[m + k]);
+  for (int m = -3; m <= 4; ++m) s[m + 3] = (m < -k + 1 || m > k) ? real(0.0) : real(sig[m + k - 1]);
+  if (npts > 16) return -1;
+  int br = ase_df_reconstruct(r, Wm, s, thres, npts, xi, o);
+  for (int q = 0; q < npts; ++q) out[q] = val(o[q]);
+  return br;
+}
+
+// WENOZ-AO(5,3) with explicit DF factors alpha[4] (S3_-1, S3_0, S3_1, S5), for tests.
+// vals[0..4] = W_-2..W_2.  beta_out[5] (may be NULL) = beta3_-1, beta3_0, beta3_1,
+// beta5_bar, tau_Z.
+void oracle_weno_ao53(const double* vals, const double* alpha, int npts, const double* xi,
+                      double* out, int force_linear_weights, double* beta_out) {
+  real Wm[9], a[4], o[16], b[5];
+  for (int m = -4; m <= 4; ++m) Wm[m + 4] = (m < -2 || m > 2) ? real(0.0) : real(vals[m + 2]);
+  for (int i = 0; i < 4; ++i) a[i] = real(alpha[i]);
+  if (npts > 16) npts = 16;
+  weno_ao53_df(Wm, a, npts, xi, o, force_linear_weights != 0, b);
+  for (int q = 0; q < npts; ++q) out[q] = val(o[q]);
+  if (beta_out) for (int i = 0; i < 5; ++i) beta_out[i] = val(b[i]);
+}
+
+// The printed coefficient table of one stencil, as numerator/denominator pairs:
+// stencil 0..2 = S3_-1, S3_0, S3_1; 5, 7, 9 = S5, S7, S9.  num[(q-1)*9 + m+4],
+// den[q-1].  Returns the number of rows.
+int oracle_coef_table(int stencil, double* num, double* den) {
+  const CoefRow* rows = nullptr;
+  int n = 0;
+  if (stencil >= 0 && stencil <= 2) { rows = kS3[stencil]; n = 2; }
+  else if (stencil == 5) { rows = kS5; n = 4; }
+  else if (stencil == 7) { rows = kS7; n = 6; }
+  else if (stencil == 9) { rows = kS9; n = 8; }
+  else return 0;
+  for (int q = 0; q < n; ++q) {
+    den[q] = rows[q].den;
+    for (int i = 0; i < 9; ++i) num[q * 9 + i] = rows[q].num[i];
+  }
+  return n;
+}
+
+// Zero-mean basis value Z_q(xi), for tests.
+double oracle_zq(int q, double xi) { return Zq(q, xi); }
+
+// Gauss-Legendre points and weights on [0, 1], for tests.
+void oracle_gauss01(int G, double* t, double* w) { gauss_legendre01(G, t, w); }
+
+// Lax-Friedrichs flux of one Gauss point in the face frame, for tests.  Returns 1 if
+// the positivity fallback (reading G21) was taken.
+int oracle_lf_flux(int C, double gamma, const double* qL, const double* qR, const double* cL,
+                   const double* cR, double* F, double* sigma) {
+  real a[4], b[4], ca[4], cb[4], f[4], s;
+  for (int c = 0; c < C; ++c) { a[c] = real(qL[c]); b[c] = real(qR[c]); ca[c] = real(cL[c]); cb[c] = real(cR[c]); }
+  int fb = lf_flux_point(a, b, ca, cb, C, gamma, f, &s) ? 1 : 0;
+  for (int c = 0; c < C; ++c) F[c] = val(f[c]);
+  *sigma = val(s);
+  return fb;
+}
+
+#ifdef ORACLE_COUNT_OPS
+// FP64 operations done since the last reset: add(+sub), mul, div, sqrt.
+void oracle_op_counts(long long* out) {
+  out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt;
+}
+void oracle_reset_op_counts() { g_ops = {0, 0, 0, 0}; }
+#endif
+
+}  // extern "C"
