@@ -1,0 +1,401 @@
+"""Benchmark: Mcell-updates/s per RK stage of the ASE-DF residual (2D Euler, FP64) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one SSP-RK3 step (three residual evaluations: x-face sweep, y-face sweep,
+flux difference + stage combination, plus the CFL wave-speed reduction) of the
+isentropic vortex on a 1024 x 1024 periodic grid with ASE-DF(9,7,5,3) (the 7th-order
+scheme is timed too and reported beside it).  Inputs are synthetic (closed-form initial
+data).  value = cells x 3 stages x K / (max over ranks of the device time of K steps).
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its own
+GPU (the solver has no data-path exchange on one grid per GPU): weak scaling.
+
+--impl reference runs the CPU oracle (the plain serial FP64 reference the library is
+checked against) on the host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2410_05489_gb300 import problems as P  # noqa: E402
+
+METRIC = "Mcell-updates/s per RK stage (2D Euler, ASE-DF 7th/9th, FP64) + % HBM roofline"
+UNIT = "Mcell-updates/s"
+N_GRID = 1024
+ORDER = 9
+ORDER_ALSO = 7
+HBM_BYTES_PER_CELL_STAGE_2D = 128.0  # read W^(s), W^n, write W^(s+1), sigma in/out, both directions
+
+
+def algorithmic_flops_per_face(ndim: int, r: int) -> float:
+    """FP64 operations (add, sub, mul, div, sqrt: 1 each) of one face of one sweep on the
+    all-smooth branch: the normal reconstruction of the face's cell evaluated at both of
+    its faces (2 C (2r-1)), the tangential reconstruction at the G Gauss points of both
+    states (2 C G (2r-1)), and per Gauss point the Lax-Friedrichs flux with primitives
+    and sigma (70 in 2D, 54 in 1D) plus the Gauss sum (2 C + 1); + 1 for the face sigma."""
+    C = 4 if ndim == 2 else 3
+    G = ((r - 1) // 2 if r > 3 else 1) if ndim == 2 else 1
+    phi = 70 if ndim == 2 else 54
+    normal = 2 * C * (2 * r - 1)
+    tang = 2 * C * G * (2 * r - 1) if ndim == 2 else 0
+    return normal + tang + G * (phi + 2 * C + 1) + 1
+
+
+def algorithmic_flops_per_cell_stage(ndim: int, r: int) -> float:
+    """Both sweeps plus the flux difference and RK combination (9 flops per component)."""
+    C = 4 if ndim == 2 else 3
+    return ndim * algorithmic_flops_per_face(ndim, r) + 9 * C
+
+
+# ----------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------------
+# distributed helpers (replicas)
+# ----------------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        import torch
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------
+def time_steps(A, torch, pb, W0, steps, warmup, flush_buf, profile=False):
+    """Device time (ms) of `steps` SSP-RK3 CFL steps, L2 flushed between steps."""
+    s = A.Solver(pb, W0)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        s.step()
+    torch.cuda.synchronize()
+    if profile:
+        A.ase_df_profile_enable(s.ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush_buf.fill_(float(k))  # writes 256 MiB: evicts the 129 MB L2 between timed steps
+        ev[k][0].record(stream)
+        s.step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    prof = None
+    if profile:
+        prof = A.ase_df_profile_read(s.ctx)
+        A.ase_df_profile_enable(s.ctx, False)
+    flags, last_dt, t = s.status()
+    s.close()
+    return sum(ms), prof, flags
+
+
+def time_e2e(A, torch, pb, W0, steps, warmup):
+    """Same metric through the public API with host buffers: every step copies W^n from
+    pinned host memory to the device and W^{n+1} back, inside the timed region."""
+    s = A.Solver(pb, W0)
+    host_in = torch.from_numpy(np.ascontiguousarray(W0)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        s.W.copy_(host_in, non_blocking=True)
+        s.step()
+        host_out.copy_(s.W, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        s.W.copy_(host_in, non_blocking=True)
+        s.step()
+        host_out.copy_(s.W, non_blocking=True)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.close()
+    nbytes = host_in.numel() * 8
+    return ms, nbytes, nbytes
+
+
+def cpu_baseline_sample(order: int):
+    """The oracle as it stands, one residual evaluation (= one RK stage) of the full
+    1024 x 1024 vortex workload on one host core."""
+    from oracle import oracle as O
+
+    O.build()
+    pb, W = P.isentropic_vortex(N_GRID, order)
+    sx, sy = P.zero_sigma(pb)  # the vortex is smooth: zero and primed sigma take the same branch
+    t0 = time.perf_counter()
+    O.residual(pb, W, sx, sy)
+    dt = time.perf_counter() - t0
+    return {"value": pb.ncells / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one residual evaluation (one RK stage) of the %dx%d r=%d vortex, serial C++ oracle, "
+                      "%.1f s" % (N_GRID, N_GRID, order, dt)}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2410_05489_gb300 import ase_df as A
+    from paper_2410_05489_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(local)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
+    fma_rate = A.ase_df_fp64_fma_rate()
+    peak_tflops = 2.0 * fma_rate / 1e12
+
+    pb, W0 = P.isentropic_vortex(args.n, args.order)
+    pb7, W7 = P.isentropic_vortex(args.n, ORDER_ALSO)
+
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, prof, flags = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush, profile=True)
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_max = max_over_ranks(ms, world)
+    ms7, _, _ = time_steps(A, torch, pb7, W7, args.steps, args.warmup, flush)
+    ms7_max = max_over_ranks(ms7, world)
+    e2e_ms, bi, bo = time_e2e(A, torch, pb, W0, args.steps, args.warmup)
+    e2e_ms = max_over_ranks(e2e_ms, world)
+
+    cells = pb.ncells
+    value = world * cells * 3 * args.steps / (ms_max * 1e-3) / 1e6
+    value7 = world * cells * 3 * args.steps / (ms7_max * 1e-3) / 1e6
+    e2e_value = world * cells * 3 * args.steps / (e2e_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel: the face sweep (x and y launches of one kernel)
+    sweep_ms = prof[0][0] + prof[0][1]
+    sweep_n = prof[1][0] + prof[1][1]
+    faces_per_launch = 0.5 * ((pb.nx + 1) * pb.ny + (pb.ny + 1) * pb.nx)
+    flops_per_launch = algorithmic_flops_per_face(2, args.order) * faces_per_launch
+    achieved = flops_per_launch / (sweep_ms / sweep_n * 1e-3) / 1e12
+    total_prof_ms = sum(prof[0])
+    hbm_gbs = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_gbs = json.load(f).get("hbm_gbs")
+    except OSError:
+        pass
+    hbm_achieved = value * 1e6 * HBM_BYTES_PER_CELL_STAGE_2D / 1e9
+    step_flops = algorithmic_flops_per_cell_stage(2, args.order) * cells * 3
+    out = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "isentropic vortex (strength 5, free stream (1,1,1,1), gamma 1.4) on periodic "
+                        "[0,10]^2, %dx%d cells, ASE-DF order %d, SSP-RK3 with CFL 0.5 dt, sigma_thres 2.0"
+                        % (args.n, args.n, args.order),
+            "nx": args.n, "ny": args.n, "order": args.order, "stages_per_step": 3,
+            "l2": "256 MiB device buffer written between timed steps (outside the step events)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "value_order7": round(value7, 3),
+            "ms_per_step_order7": round(ms7_max / args.steps, 4),
+        },
+        "roofline": {
+            "bound": "alu",
+            "kernel": "sweep_kernel (fused DF / ASE reconstruction / Gauss-point Lax-Friedrichs flux / sigma), "
+                      "x and y launches",
+            "achieved": round(achieved, 4),
+            "peak": round(peak_tflops, 4),
+            "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tflops, 4),
+            "traffic": None,
+            "peak_source": "FP64 FMA microbenchmark (ase_df_fp64_fma_rate) measured in this run, 2 flops per FMA",
+            "flops_per_launch": flops_per_launch,
+            "launch_ms": round(sweep_ms / sweep_n, 4),
+            "share_of_step_time": round(sweep_ms / total_prof_ms, 4) if total_prof_ms > 0 else None,
+            "step_frac_of_fp64_peak": round(step_flops * args.steps / (ms_max * 1e-3) / 1e12 / peak_tflops, 4),
+            "hbm": {"achieved_gbs": round(hbm_achieved, 2), "peak_gbs": hbm_gbs,
+                    "frac": round(hbm_achieved / hbm_gbs, 5) if hbm_gbs else None,
+                    "bytes_per_cell_stage": HBM_BYTES_PER_CELL_STAGE_2D},
+        },
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "gpu_launches": int(sum(prof[1])),
+        "clocks": clocks,
+        "status_flags": flags,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_sample(args.order)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ----------------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    O.build()
+    ns = args.ref_n
+    pb, W = P.isentropic_vortex(ns, args.order)
+    sx, sy = O.prime_sigma(pb, W)
+    for _ in range(args.warmup):
+        O.step(pb, W, sx, sy)
+    t0 = time.perf_counter()
+    Wk, sxk, syk = W, sx, sy
+    for _ in range(args.steps):
+        Wk, sxk, syk, _ = O.step(pb, Wk, sxk, syk)
+    dt = time.perf_counter() - t0
+    value = pb.ncells * 3 * args.steps / dt / 1e6
+    sample = ("per step: one SSP-RK3 step of the same vortex workload on a %dx%d grid (same order %d, "
+              "same per-cell arithmetic) by the serial C++ oracle" % (ns, ns, args.order))
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 5),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "isentropic vortex, ASE-DF order %d, SSP-RK3, CFL 0.5" % args.order,
+                   "nx": ns, "ny": ns, "order": args.order},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--order", type=int, default=ORDER)
+    ap.add_argument("--ref-n", type=int, default=96)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

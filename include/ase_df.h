@@ -1,0 +1,151 @@
+/*
+ * ase_df.h -- C ABI of the GB300 (sm_103a) FP64 library for the per-stage spatial
+ * residual of a finite-volume Euler solver with ASE-DF reconstruction
+ * (arXiv 2410.05489, "An Adaptive Reconstruction Method for Arbitrary High-Order
+ * Accuracy Using Discontinuity Feedback").
+ *
+ * The residual (Sec. 2.1, semi-discrete form) of one RK stage is
+ *     L(W) = -(1/|Omega|) sum_faces |l| sum_k eta_k F(x_k) . n
+ * with, on every face, (r-1)/2 Gauss points (Sec. 2.1; one point in 1D), the
+ * Lax-Friedrichs flux of Sec. 2.3 between reconstructed states, and the states from the
+ * adaptive stencil extension of Sec. 3 (Algorithm 1) driven by the discontinuity
+ * feedback factor of Sec. 3.1, Eq. (3.2): linear 5th/7th/9th order where the stencil is
+ * smooth, WENOZ-AO(5,3) with DF damping (Sec. 3.2) otherwise.  Time stepping is the
+ * SSP-RK3 of Sec. 2.3.
+ *
+ * Conventions (all entry points):
+ *   - Arrays are DEVICE pointers owned by the caller, FP64, C-contiguous:
+ *       W      [C][ny][nx]   conservative cell averages; C = 3 in 1D (rho, rho u, E),
+ *                            C = 4 in 2D (rho, rho u, rho v, E); 1D uses ny = 1.
+ *       sx     [ny][nx+1]    discontinuity strength sigma of the x-faces; x-face f lies
+ *                            between cells f-1 and f.
+ *       sy     [ny+1][nx]    sigma of the y-faces (2D only; pass NULL in 1D).
+ *       L      [C][ny][nx]   residual dW/dt.
+ *   - sigma is solver state: the sigma a residual consumes is the one the previous
+ *     residual (previous RK stage) produced; ase_df_prime_sigma gives sigma^0.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     stream-ordered and asynchronous; only ase_df_get_status synchronises.
+ *   - The context owns its scratch memory (face fluxes, RK stage states, sigma
+ *     ping-pong buffers); one context per host thread.
+ *   - Errors: argument and launch errors are returned at once (ase_df_last_error gives
+ *     the message); conditions found on the device (non-physical states, non-finite
+ *     values) are OR-ed into a device status word read by ase_df_get_status.  Nothing
+ *     traps or asserts on the device.
+ */
+#ifndef ASE_DF_H
+#define ASE_DF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ASE_DF_OK = 0,
+  ASE_DF_E_INVAL = 1,       /* bad argument or parameter */
+  ASE_DF_E_NOMEM = 2,       /* device allocation failed */
+  ASE_DF_E_CUDA = 3,        /* a CUDA call or launch failed */
+  ASE_DF_E_NONPHYSICAL = 4, /* the device status word reports a non-physical state */
+  ASE_DF_E_TIMEOUT = 5,     /* a bounded device wait ran out */
+  ASE_DF_E_BOUNDS = 6       /* a size exceeds a documented limit */
+} ase_df_status;
+
+typedef enum {
+  ASE_DF_BC_PERIODIC = 0,   /* ghost cells wrap around */
+  ASE_DF_BC_OUTFLOW = 1,    /* zero-gradient: ghost cells copy the nearest interior cell */
+  ASE_DF_BC_INFLOW_BAND = 2 /* x-lo only: ghost cells whose centre y lies in
+                               (inflow_lo, inflow_hi) hold inflow_state; outflow elsewhere */
+} ase_df_bc;
+
+/* Device status word bits (ase_df_get_status). */
+#define ASE_DF_FLAG_NONPHYSICAL 0x1u   /* a cell average with rho <= 0, p <= 0 or non-finite */
+#define ASE_DF_FLAG_POSITIVITY  0x2u   /* informational: a Gauss point took the first-order
+                                          states (non-physical reconstructed state) */
+#define ASE_DF_FLAG_DT          0x4u   /* the CFL step came out non-positive or non-finite */
+
+/* Problem statement (Sec. 2: 1D/2D Euler on a uniform Cartesian grid). */
+typedef struct {
+  int32_t ndim;            /* 1 or 2 */
+  int32_t order;           /* scheme order r: 3, 5, 7 or 9 */
+  int64_t nx, ny;          /* cells; ny is ignored (taken as 1) in 1D */
+  double x0, x1, y0, y1;   /* domain [x0,x1] x [y0,y1] */
+  double gamma;            /* ratio of specific heats, > 1 */
+  double sigma_thres;      /* DF threshold of Eq. (3.2); the paper uses 2.0 (Sec. 4.1) */
+  double cfl;              /* CFL number for dt = cfl / max((|u|+c)/dx + (|v|+c)/dy) */
+  int32_t bc[4];           /* ase_df_bc of x-lo, x-hi, y-lo, y-hi */
+  double inflow_state[4];  /* primitive (rho, u, v, p) of an x-lo inflow band */
+  double inflow_lo, inflow_hi;
+  double t_end;            /* > 0: CFL steps are shortened so that t never passes t_end */
+} ase_df_params;
+
+typedef struct ase_df_ctx ase_df_ctx;
+
+/* Validates p and allocates the context and its device scratch on the current device.
+ * Limits: nx, ny <= 2^20 and C*(nx+1)*(ny+1) < 2^31.  Returns ASE_DF_E_INVAL /
+ * ASE_DF_E_BOUNDS / ASE_DF_E_NOMEM without allocating anything on failure; *out is
+ * NULL then. */
+ase_df_status ase_df_init(const ase_df_params* p, ase_df_ctx** out);
+
+/* Frees the context and its device memory (synchronises the device first). */
+void ase_df_destroy(ase_df_ctx* ctx);
+
+/* sigma^0 (Sec. 3.1, feedback): the face strengths of a residual evaluated with
+ * sigma_in = 0, i.e. from all-linear r-th order states.  Writes sx (and sy in 2D). */
+ase_df_status ase_df_prime_sigma(ase_df_ctx* ctx, const double* W, double* sx, double* sy,
+                                 void* stream);
+
+/* One residual evaluation (Sec. 2.1 Eq. 2.3 with Sec. 3 reconstruction and the Sec. 2.3
+ * flux): reads W and sigma_in, writes L and sigma_out (sx_out, sy_out must not alias
+ * sx_in, sy_in).  The Gauss-averaged face fluxes stay in the context
+ * (ase_df_copy_face_fluxes). */
+ase_df_status ase_df_residual(ase_df_ctx* ctx, const double* W, const double* sx_in,
+                              const double* sy_in, double* L, double* sx_out, double* sy_out,
+                              void* stream);
+
+/* Copies the face fluxes of the last residual evaluation on this context:
+ * Fx [C][ny][nx+1], Fy [C][ny+1][nx] (NULL in 1D). */
+ase_df_status ase_df_copy_face_fluxes(ase_df_ctx* ctx, double* Fx, double* Fy, void* stream);
+
+/* One SSP-RK3 step (Sec. 2.3, Eq. SSP-RK3) in place: W holds W^n on entry and W^{n+1}
+ * on exit; sx/sy hold sigma^n on entry and the third stage's sigma on exit (each stage
+ * consumes the sigma of the stage before).  dt > 0: that step; dt <= 0: the CFL step of
+ * W^n (including the inflow state, if any), shortened to t_end.  The device keeps the
+ * time t and the last dt (ase_df_get_status). */
+ase_df_status ase_df_step(ase_df_ctx* ctx, double* W, double* sx, double* sy, double dt,
+                          void* stream);
+
+/* Runs nsteps ase_df_step calls as one CUDA graph replay when possible (captured on the
+ * first call for the given pointers and dt mode, replayed afterwards). */
+ase_df_status ase_df_run(ase_df_ctx* ctx, double* W, double* sx, double* sy, double dt,
+                         int32_t nsteps, void* stream);
+
+/* Synchronises the stream of the last call and reads the device status word (ASE_DF_FLAG_*),
+ * the last dt and the time t.  Returns ASE_DF_E_NONPHYSICAL if that bit is set. */
+ase_df_status ase_df_get_status(ase_df_ctx* ctx, uint32_t* flags, double* last_dt, double* t);
+
+/* Clears the device status word and sets the device time t. */
+ase_df_status ase_df_reset(ase_df_ctx* ctx, double t, void* stream);
+
+/* Message of the last error on this context (or of the last failed ase_df_init when
+ * ctx is NULL). */
+const char* ase_df_last_error(const ase_df_ctx* ctx);
+
+/* Kernel timing with CUDA events recorded on the launching stream around every sweep,
+ * combine and wave-speed launch of this context (enable != 0 starts a new record, 0
+ * stops recording).  ase_df_profile_read synchronises, then returns per kernel kind
+ * (0: x-face sweep, 1: y-face sweep, 2: combine, 3: wave-speed reduction) the summed
+ * milliseconds ms[4] and the launch counts n[4]; at most 65536 launches are recorded. */
+ase_df_status ase_df_profile_enable(ase_df_ctx* ctx, int32_t enable);
+ase_df_status ase_df_profile_read(ase_df_ctx* ctx, double* ms, int64_t* n);
+
+/* FP64 throughput microbenchmark used as the roofline denominator: independent FMA
+ * chains on every SM; writes the achieved FP64 FMA instructions per second into
+ * *fma_per_s (flops = 2x).  Synchronises the device. */
+ase_df_status ase_df_fp64_fma_rate(double* fma_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASE_DF_H */

@@ -1,0 +1,261 @@
+"""Thin Python binding of the C ABI in include/ase_df.h (ctypes, argument marshalling only).
+
+Every function of the C ABI has a function of the same name here taking torch CUDA
+tensors (FP64, contiguous) and an optional torch stream; all computation runs in the
+library's CUDA kernels.  Importing this module loads libasedf.so and fails loudly when it
+is missing or no CUDA device is present: there is no CPU fallback.
+
+The Solver class bundles a context with its problem and device tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import torch
+
+from .problems import Problem
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libasedf.so")
+
+ASE_DF_OK = 0
+STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NONPHYSICAL", 5: "E_TIMEOUT", 6: "E_BOUNDS"}
+FLAG_NONPHYSICAL = 0x1
+FLAG_POSITIVITY = 0x2
+FLAG_DT = 0x4
+
+
+class AseDfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class ase_df_params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32), ("order", ctypes.c_int32),
+        ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("sigma_thres", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("bc", ctypes.c_int32 * 4), ("inflow_state", ctypes.c_double * 4),
+        ("inflow_lo", ctypes.c_double), ("inflow_hi", ctypes.c_double),
+        ("t_end", ctypes.c_double),
+    ]
+
+
+_c = ctypes
+_VP = _c.c_void_p
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libasedf.so is not built (%s); run paper_2410_05489_gb300.build.build()" % LIB_PATH)
+    lib = _c.CDLL(LIB_PATH)
+    P = _c.POINTER(ase_df_params)
+    CTX = _c.c_void_p
+    sig = {
+        "ase_df_init": ([P, _c.POINTER(CTX)], _c.c_int),
+        "ase_df_destroy": ([CTX], None),
+        "ase_df_prime_sigma": ([CTX, _VP, _VP, _VP, _VP], _c.c_int),
+        "ase_df_residual": ([CTX, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _c.c_int),
+        "ase_df_copy_face_fluxes": ([CTX, _VP, _VP, _VP], _c.c_int),
+        "ase_df_step": ([CTX, _VP, _VP, _VP, _c.c_double, _VP], _c.c_int),
+        "ase_df_run": ([CTX, _VP, _VP, _VP, _c.c_double, _c.c_int32, _VP], _c.c_int),
+        "ase_df_get_status": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)], _c.c_int),
+        "ase_df_reset": ([CTX, _c.c_double, _VP], _c.c_int),
+        "ase_df_last_error": ([CTX], _c.c_char_p),
+        "ase_df_fp64_fma_rate": ([_c.POINTER(_c.c_double)], _c.c_int),
+        "ase_df_profile_enable": ([CTX, _c.c_int32], _c.c_int),
+        "ase_df_profile_read": ([CTX, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64)], _c.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def params_from_problem(pb: Problem, t_end: float = 0.0) -> ase_df_params:
+    p = ase_df_params()
+    p.ndim, p.order = pb.ndim, pb.order
+    p.nx, p.ny = pb.nx, pb.nyc
+    p.x0, p.x1, p.y0, p.y1 = pb.x0, pb.x1, pb.y0, pb.y1
+    p.gamma, p.sigma_thres, p.cfl = pb.gamma, pb.sigma_thres, pb.cfl
+    for i, c in enumerate(pb.bc_codes()):
+        p.bc[i] = c
+    for i in range(4):
+        p.inflow_state[i] = pb.inflow[i]
+    p.inflow_lo, p.inflow_hi = pb.inflow_lo, pb.inflow_hi
+    p.t_end = t_end
+    return p
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return _c.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> _c.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _c.c_void_p(s.cuda_stream)
+
+
+def _check(ctx, status: int):
+    if status != ASE_DF_OK:
+        msg = _load().ase_df_last_error(ctx)
+        raise AseDfError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------------------------------
+# the C ABI, one function per entry point
+# ----------------------------------------------------------------------------------
+def ase_df_init(params: ase_df_params):
+    lib = _load()
+    ctx = _c.c_void_p()
+    st = lib.ase_df_init(_c.byref(params), _c.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def ase_df_destroy(ctx) -> None:
+    _load().ase_df_destroy(ctx)
+
+
+def ase_df_prime_sigma(ctx, W, sx, sy, stream=None) -> None:
+    _check(ctx, _load().ase_df_prime_sigma(ctx, _ptr(W), _ptr(sx), _ptr(sy), _stream(stream)))
+
+
+def ase_df_residual(ctx, W, sx_in, sy_in, L, sx_out, sy_out, stream=None) -> None:
+    _check(ctx, _load().ase_df_residual(ctx, _ptr(W), _ptr(sx_in), _ptr(sy_in), _ptr(L), _ptr(sx_out),
+                                        _ptr(sy_out), _stream(stream)))
+
+
+def ase_df_copy_face_fluxes(ctx, Fx, Fy, stream=None) -> None:
+    _check(ctx, _load().ase_df_copy_face_fluxes(ctx, _ptr(Fx), _ptr(Fy), _stream(stream)))
+
+
+def ase_df_step(ctx, W, sx, sy, dt: float = 0.0, stream=None) -> None:
+    _check(ctx, _load().ase_df_step(ctx, _ptr(W), _ptr(sx), _ptr(sy), float(dt), _stream(stream)))
+
+
+def ase_df_run(ctx, W, sx, sy, dt: float, nsteps: int, stream=None) -> None:
+    _check(ctx, _load().ase_df_run(ctx, _ptr(W), _ptr(sx), _ptr(sy), float(dt), int(nsteps), _stream(stream)))
+
+
+def ase_df_get_status(ctx) -> Tuple[int, float, float]:
+    flags = _c.c_uint32()
+    dt = _c.c_double()
+    t = _c.c_double()
+    st = _load().ase_df_get_status(ctx, _c.byref(flags), _c.byref(dt), _c.byref(t))
+    if st not in (ASE_DF_OK, 4):
+        _check(ctx, st)
+    return int(flags.value), float(dt.value), float(t.value)
+
+
+def ase_df_reset(ctx, t: float = 0.0, stream=None) -> None:
+    _check(ctx, _load().ase_df_reset(ctx, float(t), _stream(stream)))
+
+
+def ase_df_last_error(ctx) -> str:
+    m = _load().ase_df_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def ase_df_profile_enable(ctx, enable: bool) -> None:
+    _check(ctx, _load().ase_df_profile_enable(ctx, int(bool(enable))))
+
+
+def ase_df_profile_read(ctx):
+    """-> (ms[4], n[4]) per kernel kind: x-sweep, y-sweep, combine, wave-speed."""
+    ms = (_c.c_double * 4)()
+    n = (_c.c_int64 * 4)()
+    _check(ctx, _load().ase_df_profile_read(ctx, ms, n))
+    return list(ms), list(n)
+
+
+def ase_df_fp64_fma_rate() -> float:
+    r = _c.c_double()
+    _check(None, _load().ase_df_fp64_fma_rate(_c.byref(r)))
+    return float(r.value)
+
+
+# ----------------------------------------------------------------------------------
+# convenience wrapper
+# ----------------------------------------------------------------------------------
+class Solver:
+    """A context plus the device state of one problem.
+
+    W, sx, sy are FP64 CUDA tensors of shapes pb.state_shape, pb.sx_shape, pb.sy_shape.
+    """
+
+    def __init__(self, pb: Problem, W0=None, t_end: float = 0.0, device: str = "cuda"):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the ASE-DF library needs a CUDA device")
+        self.pb = pb
+        self.device = torch.device(device)
+        self.ctx = ase_df_init(params_from_problem(pb, t_end))
+        self.W = torch.zeros(pb.state_shape, dtype=torch.float64, device=self.device)
+        self.sx = torch.zeros(pb.sx_shape, dtype=torch.float64, device=self.device)
+        self.sy = torch.zeros(pb.sy_shape, dtype=torch.float64, device=self.device)
+        if W0 is not None:
+            self.set_state(W0)
+
+    def _sy(self, t):
+        return t if self.pb.ndim == 2 else None
+
+    def set_state(self, W0, prime: bool = True) -> None:
+        self.W.copy_(torch.as_tensor(W0, dtype=torch.float64))
+        if prime:
+            self.prime()
+        ase_df_reset(self.ctx, 0.0)
+
+    def prime(self) -> None:
+        ase_df_prime_sigma(self.ctx, self.W, self.sx, self._sy(self.sy))
+
+    def residual(self, W=None, sx=None, sy=None):
+        W = self.W if W is None else W
+        sx = self.sx if sx is None else sx
+        sy = self.sy if sy is None else sy
+        L = torch.empty_like(W)
+        sxo = torch.empty_like(sx)
+        syo = torch.empty_like(sy)
+        ase_df_residual(self.ctx, W, sx, self._sy(sy), L, sxo, self._sy(syo))
+        return L, sxo, syo
+
+    def face_fluxes(self):
+        pb = self.pb
+        Fx = torch.empty((pb.ncomp, pb.nyc, pb.nx + 1), dtype=torch.float64, device=self.device)
+        Fy = torch.empty((pb.ncomp, pb.ny + 1, pb.nx), dtype=torch.float64, device=self.device) if pb.ndim == 2 else None
+        ase_df_copy_face_fluxes(self.ctx, Fx, Fy)
+        return Fx, Fy
+
+    def step(self, dt: float = 0.0) -> None:
+        ase_df_step(self.ctx, self.W, self.sx, self._sy(self.sy), dt)
+
+    def run(self, nsteps: int, dt: float = 0.0) -> None:
+        ase_df_run(self.ctx, self.W, self.sx, self._sy(self.sy), dt, nsteps)
+
+    def status(self):
+        return ase_df_get_status(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None) is not None:
+            ase_df_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,468 @@
+// C ABI of the ASE-DF library (declared in include/ase_df.h): validation, context and
+// scratch management, and the launch sequences of one residual and of one SSP-RK3 step.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ase_df.h"
+#include "ase_df_internal.cuh"
+
+using namespace asedf;
+
+struct ase_df_ctx {
+  ase_df_params p;
+  int C, K, dim;
+  GridInfo g;
+  Tables tab;
+  double dx, dy, inv_dx, inv_dy, inflow_speed;
+  // device scratch owned by the context
+  double *Fx, *Fy;          // face fluxes
+  double *W1, *W2;          // RK stage states
+  double *sxa, *sya, *sxb, *syb;  // sigma ping-pong
+  double *zsx, *zsy;        // zero sigma (priming)
+  DevState* st;
+  // CUDA graph of one step (ase_df_run)
+  cudaGraphExec_t graph_exec;
+  double* g_W;
+  double* g_sx;
+  double* g_sy;
+  double g_dt;
+  cudaStream_t cap_stream;
+  cudaStream_t last_stream;
+  // kernel timing (ase_df_profile_*)
+  bool prof_on;
+  std::vector<cudaEvent_t>* prof_ev;  // pairs (start, stop)
+  std::vector<int>* prof_kind;
+  char err[512];
+};
+
+static const size_t kProfMax = 65536;
+
+// Records an event pair around one launch when profiling is on (never during capture).
+struct ProfScope {
+  ase_df_ctx* c;
+  cudaStream_t s;
+  int kind;
+  cudaEvent_t e1;
+  bool on;
+  ProfScope(ase_df_ctx* c_, cudaStream_t s_, int kind_) : c(c_), s(s_), kind(kind_), e1(nullptr), on(false) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (!c->prof_on || cs != cudaStreamCaptureStatusNone || c->prof_kind->size() >= kProfMax) return;
+    cudaEvent_t e0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return;
+    cudaEventRecord(e0, s);
+    c->prof_ev->push_back(e0);
+    on = true;
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(e1, s);
+    c->prof_ev->push_back(e1);
+    c->prof_kind->push_back(kind);
+  }
+};
+
+static void prof_clear(ase_df_ctx* c) {
+  if (!c->prof_ev) return;
+  for (cudaEvent_t e : *c->prof_ev) cudaEventDestroy(e);
+  c->prof_ev->clear();
+  c->prof_kind->clear();
+}
+
+static char g_init_err[512] = "";
+
+static ase_df_status fail(ase_df_ctx* c, ase_df_status s, const char* fmt, ...) {
+  char* dst = c ? c->err : g_init_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+static ase_df_status cuda_fail(ase_df_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, ASE_DF_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static double sound_speed_sum(const ase_df_params& p, double inv_dx, double inv_dy) {
+  const double rho = p.inflow_state[0], u = p.inflow_state[1], v = p.inflow_state[2], pr = p.inflow_state[3];
+  const double c = std::sqrt(p.gamma * pr / rho);
+  double s = (std::fabs(u) + c) * inv_dx;
+  if (p.ndim == 2) s += (std::fabs(v) + c) * inv_dy;
+  return s;
+}
+
+extern "C" {
+
+ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
+  if (!out) return fail(nullptr, ASE_DF_E_INVAL, "out is NULL");
+  *out = nullptr;
+  if (!pin) return fail(nullptr, ASE_DF_E_INVAL, "params is NULL");
+  ase_df_params p = *pin;
+  if (p.ndim != 1 && p.ndim != 2) return fail(nullptr, ASE_DF_E_INVAL, "ndim must be 1 or 2 (got %d)", p.ndim);
+  if (p.order != 3 && p.order != 5 && p.order != 7 && p.order != 9)
+    return fail(nullptr, ASE_DF_E_INVAL, "order must be 3, 5, 7 or 9 (got %d)", p.order);
+  if (p.ndim == 1) p.ny = 1;
+  if (p.nx < 1 || p.ny < 1) return fail(nullptr, ASE_DF_E_INVAL, "nx, ny must be >= 1");
+  if (p.nx > (1 << 20) || p.ny > (1 << 20)) return fail(nullptr, ASE_DF_E_BOUNDS, "nx, ny must be <= 2^20");
+  const int C = (p.ndim == 1) ? 3 : 4;
+  if ((double)C * (double)(p.nx + 1) * (double)(p.ny + 1) >= 2147483648.0)
+    return fail(nullptr, ASE_DF_E_BOUNDS, "C*(nx+1)*(ny+1) must be < 2^31");
+  if (!(p.x1 > p.x0) || (p.ndim == 2 && !(p.y1 > p.y0)))
+    return fail(nullptr, ASE_DF_E_INVAL, "empty domain");
+  if (!(p.gamma > 1.0) || !std::isfinite(p.gamma)) return fail(nullptr, ASE_DF_E_INVAL, "gamma must be > 1");
+  if (!(p.sigma_thres > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "sigma_thres must be > 0");
+  if (!(p.cfl > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "cfl must be > 0");
+  for (int s = 0; s < 4; ++s) {
+    if (p.bc[s] < 0 || p.bc[s] > 2) return fail(nullptr, ASE_DF_E_INVAL, "bad boundary code %d", p.bc[s]);
+    if (p.bc[s] == ASE_DF_BC_INFLOW_BAND && s != 0)
+      return fail(nullptr, ASE_DF_E_INVAL, "the inflow band is supported on x-lo only");
+    if (p.ndim == 1 && s >= 2) p.bc[s] = ASE_DF_BC_OUTFLOW;
+  }
+  if ((p.bc[0] == ASE_DF_BC_PERIODIC) != (p.bc[1] == ASE_DF_BC_PERIODIC))
+    return fail(nullptr, ASE_DF_E_INVAL, "periodic boundaries must come in pairs (x)");
+  if (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_PERIODIC) != (p.bc[3] == ASE_DF_BC_PERIODIC))
+    return fail(nullptr, ASE_DF_E_INVAL, "periodic boundaries must come in pairs (y)");
+  if (p.bc[0] == ASE_DF_BC_INFLOW_BAND && !(p.inflow_state[0] > 0.0 && p.inflow_state[3] > 0.0))
+    return fail(nullptr, ASE_DF_E_INVAL, "inflow state must have rho > 0 and p > 0");
+
+  ase_df_ctx* c = new (std::nothrow) ase_df_ctx;
+  if (!c) return fail(nullptr, ASE_DF_E_NOMEM, "host allocation failed");
+  std::memset(c, 0, sizeof(*c));
+  c->prof_ev = new (std::nothrow) std::vector<cudaEvent_t>();
+  c->prof_kind = new (std::nothrow) std::vector<int>();
+  if (!c->prof_ev || !c->prof_kind) {
+    delete c->prof_ev;
+    delete c->prof_kind;
+    delete c;
+    return fail(nullptr, ASE_DF_E_NOMEM, "host allocation failed");
+  }
+  c->p = p;
+  c->C = C;
+  c->K = (p.order - 1) / 2;
+  c->dim = p.ndim;
+  c->dx = (p.x1 - p.x0) / (double)p.nx;
+  c->dy = (p.ndim == 2) ? (p.y1 - p.y0) / (double)p.ny : 1.0;
+  c->inv_dx = 1.0 / c->dx;
+  c->inv_dy = (p.ndim == 2) ? 1.0 / c->dy : 0.0;
+  GridInfo& g = c->g;
+  g.nx = (int)p.nx;
+  g.ny = (int)p.ny;
+  for (int s = 0; s < 4; ++s) g.bc[s] = p.bc[s];
+  g.band_j0 = 1;
+  g.band_j1 = 0;  // empty
+  if (p.bc[0] == ASE_DF_BC_INFLOW_BAND) {
+    // rows whose centre y0 + (j + 1/2) dy lies strictly inside (inflow_lo, inflow_hi)
+    int j0 = -1, j1 = -2;
+    for (int j = 0; j < g.ny; ++j) {
+      const double yc = p.y0 + ((double)j + 0.5) * c->dy;
+      if (yc > p.inflow_lo && yc < p.inflow_hi) {
+        if (j0 < 0) j0 = j;
+        j1 = j;
+      }
+    }
+    if (j0 >= 0) { g.band_j0 = j0; g.band_j1 = j1; }
+    const double rho = p.inflow_state[0], u = p.inflow_state[1], v = p.inflow_state[2], pr = p.inflow_state[3];
+    g.inflow_cons[0] = rho;
+    g.inflow_cons[1] = rho * u;
+    if (C == 4) {
+      g.inflow_cons[2] = rho * v;
+      g.inflow_cons[3] = pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+    } else {
+      g.inflow_cons[2] = pr / (p.gamma - 1.0) + 0.5 * rho * u * u;
+    }
+    c->inflow_speed = sound_speed_sum(p, c->inv_dx, c->inv_dy);
+  }
+  g.gamma = p.gamma;
+  g.thres = p.sigma_thres;
+  build_tables(p.order, p.ndim, &c->tab);
+
+  const size_t nW = (size_t)C * g.nx * g.ny;
+  const size_t nFx = (size_t)C * g.ny * (g.nx + 1);
+  const size_t nFy = (p.ndim == 2) ? (size_t)C * (g.ny + 1) * g.nx : 1;
+  const size_t nsx = (size_t)g.ny * (g.nx + 1);
+  const size_t nsy = (p.ndim == 2) ? (size_t)(g.ny + 1) * g.nx : 1;
+  struct { double** ptr; size_t n; } allocs[] = {
+    {&c->Fx, nFx}, {&c->Fy, nFy}, {&c->W1, nW}, {&c->W2, nW}, {&c->sxa, nsx}, {&c->sya, nsy},
+    {&c->sxb, nsx}, {&c->syb, nsy}, {&c->zsx, nsx}, {&c->zsy, nsy},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc((void**)a.ptr, a.n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      ase_df_destroy(c);
+      return fail(nullptr, ASE_DF_E_NOMEM, "device allocation of %zu bytes failed", a.n * sizeof(double));
+    }
+  }
+  if (cudaMalloc((void**)&c->st, sizeof(DevState)) != cudaSuccess) {
+    cudaGetLastError();
+    ase_df_destroy(c);
+    return fail(nullptr, ASE_DF_E_NOMEM, "device allocation of the status word failed");
+  }
+  cudaError_t e = cudaMemset(c->zsx, 0, nsx * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->zsy, 0, nsy * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->st, 0, sizeof(DevState));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    ase_df_destroy(c);
+    return fail(nullptr, ASE_DF_E_CUDA, "init: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return ASE_DF_OK;
+}
+
+void ase_df_destroy(ase_df_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  double* ptrs[] = {c->Fx, c->Fy, c->W1, c->W2, c->sxa, c->sya, c->sxb, c->syb, c->zsx, c->zsy};
+  for (double* q : ptrs)
+    if (q) cudaFree(q);
+  if (c->st) cudaFree(c->st);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  prof_clear(c);
+  delete c->prof_ev;
+  delete c->prof_kind;
+  delete c;
+}
+
+const char* ase_df_last_error(const ase_df_ctx* c) { return c ? c->err : g_init_err; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// launch sequences
+// ---------------------------------------------------------------------------------
+static cudaError_t sweep(ase_df_ctx* c, int dir, const double* W, const double* sx, const double* sy,
+                         double* F, double* s_out, cudaStream_t s) {
+  SweepArgs a;
+  a.W = W;
+  a.s_norm = (dir == 0) ? sx : sy;
+  a.s_tan = (dir == 0) ? sy : sx;
+  a.F = F;
+  a.s_out = s_out;
+  a.st = c->st;
+  ProfScope prof(c, s, dir);
+  switch (c->p.order) {
+    case 3: return launch_sweep_r3(c->dim, dir, c->g, a, c->tab, s);
+    case 5: return launch_sweep_r5(c->dim, dir, c->g, a, c->tab, s);
+    case 7: return launch_sweep_r7(c->dim, dir, c->g, a, c->tab, s);
+    default: return launch_sweep_r9(c->dim, dir, c->g, a, c->tab, s);
+  }
+}
+
+// Face fluxes of both directions of W with sigma_in = (sx, sy), sigma_out -> (sxo, syo).
+static cudaError_t face_fluxes(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
+                               double* sxo, double* syo, cudaStream_t s) {
+  cudaError_t e = sweep(c, 0, W, sx, sy, c->Fx, sxo, s);
+  if (e != cudaSuccess || c->dim == 1) return e;
+  return sweep(c, 1, W, sx, sy, c->Fy, syo, s);
+}
+
+static cudaError_t combine(ase_df_ctx* c, int stage, const double* Wn, const double* Ws, double* out,
+                           double dt_fixed, cudaStream_t s) {
+  CombineArgs a;
+  a.Fx = c->Fx;
+  a.Fy = c->Fy;
+  a.Wn = Wn;
+  a.Ws = Ws;
+  a.out = out;
+  a.st = c->st;
+  a.inv_dx = c->inv_dx;
+  a.inv_dy = c->inv_dy;
+  a.dt_fixed = dt_fixed;
+  a.cfl = c->p.cfl;
+  a.t_end = c->p.t_end;
+  a.inflow_speed = c->inflow_speed;
+  a.stage = stage;
+  ProfScope prof(c, s, 2);
+  return launch_combine(c->dim, c->g, a, s);
+}
+
+static ase_df_status check_ptrs(ase_df_ctx* c, const void* W, const void* sx, const void* sy) {
+  if (!c) return ASE_DF_E_INVAL;
+  if (!W || !sx) return fail(c, ASE_DF_E_INVAL, "NULL state or sigma pointer");
+  if (c->dim == 2 && !sy) return fail(c, ASE_DF_E_INVAL, "sy must not be NULL in 2D");
+  return ASE_DF_OK;
+}
+
+static ase_df_status step_launches(ase_df_ctx* c, double* W, double* sx, double* sy, double dt,
+                                   cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (!(dt > 0.0)) {
+    SpeedArgs sa;
+    sa.W = W;
+    sa.st = c->st;
+    sa.inv_dx = c->inv_dx;
+    sa.inv_dy = c->inv_dy;
+    {
+      ProfScope prof(c, s, 3);
+      e = launch_max_speed(c->dim, c->g, sa, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "max_speed");
+  }
+  const double dtf = (dt > 0.0) ? dt : 0.0;
+  // stage 1
+  if ((e = face_fluxes(c, W, sx, sy, c->sxa, c->sya, s)) != cudaSuccess) return cuda_fail(c, e, "stage 1 sweep");
+  if ((e = combine(c, 1, W, W, c->W1, dtf, s)) != cudaSuccess) return cuda_fail(c, e, "stage 1 combine");
+  // stage 2
+  if ((e = face_fluxes(c, c->W1, c->sxa, c->sya, c->sxb, c->syb, s)) != cudaSuccess) return cuda_fail(c, e, "stage 2 sweep");
+  if ((e = combine(c, 2, W, c->W1, c->W2, dtf, s)) != cudaSuccess) return cuda_fail(c, e, "stage 2 combine");
+  // stage 3: sigma_out lands in the caller's sx / sy, W^{n+1} in W
+  if ((e = face_fluxes(c, c->W2, c->sxb, c->syb, sx, sy, s)) != cudaSuccess) return cuda_fail(c, e, "stage 3 sweep");
+  if ((e = combine(c, 3, W, c->W2, W, dtf, s)) != cudaSuccess) return cuda_fail(c, e, "stage 3 combine");
+  return ASE_DF_OK;
+}
+
+extern "C" {
+
+ase_df_status ase_df_residual(ase_df_ctx* c, const double* W, const double* sx_in, const double* sy_in,
+                              double* L, double* sx_out, double* sy_out, void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx_in, sy_in);
+  if (r != ASE_DF_OK) return r;
+  if (!L || !sx_out || (c->dim == 2 && !sy_out)) return fail(c, ASE_DF_E_INVAL, "NULL output pointer");
+  if (sx_out == sx_in || (c->dim == 2 && sy_out == sy_in))
+    return fail(c, ASE_DF_E_INVAL, "sigma_out must not alias sigma_in");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  cudaError_t e = face_fluxes(c, W, sx_in, sy_in, sx_out, sy_out, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual sweep");
+  e = combine(c, 0, W, W, L, 0.0, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual combine");
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_prime_sigma(ase_df_ctx* c, const double* W, double* sx, double* sy, void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx, sy);
+  if (r != ASE_DF_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  cudaError_t e = face_fluxes(c, W, c->zsx, c->zsy, sx, sy, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "prime_sigma");
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_copy_face_fluxes(ase_df_ctx* c, double* Fx, double* Fy, void* stream) {
+  if (!c || !Fx || (c->dim == 2 && !Fy)) return c ? fail(c, ASE_DF_E_INVAL, "NULL pointer") : ASE_DF_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nFx = (size_t)c->C * c->g.ny * (c->g.nx + 1);
+  cudaError_t e = cudaMemcpyAsync(Fx, c->Fx, nFx * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && c->dim == 2) {
+    const size_t nFy = (size_t)c->C * (c->g.ny + 1) * c->g.nx;
+    e = cudaMemcpyAsync(Fy, c->Fy, nFy * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy_face_fluxes");
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_step(ase_df_ctx* c, double* W, double* sx, double* sy, double dt, void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx, sy);
+  if (r != ASE_DF_OK) return r;
+  if (!std::isfinite(dt)) return fail(c, ASE_DF_E_INVAL, "dt is not finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return step_launches(c, W, sx, sy, dt, s);
+}
+
+ase_df_status ase_df_run(ase_df_ctx* c, double* W, double* sx, double* sy, double dt, int32_t nsteps,
+                         void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx, sy);
+  if (r != ASE_DF_OK) return r;
+  if (nsteps < 0) return fail(c, ASE_DF_E_INVAL, "nsteps < 0");
+  if (!std::isfinite(dt)) return fail(c, ASE_DF_E_INVAL, "dt is not finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  if (nsteps == 0) return ASE_DF_OK;
+  const double dtkey = (dt > 0.0) ? dt : 0.0;
+  if (!c->graph_exec || c->g_W != W || c->g_sx != sx || c->g_sy != sy || c->g_dt != dtkey) {
+    if (c->graph_exec) {
+      cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+    }
+    if (!c->cap_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(c, e, "capture stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+    ase_df_status st = step_launches(c, W, sx, sy, dtkey, c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (st != ASE_DF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    e = cudaGraphInstantiate(&c->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      c->graph_exec = nullptr;
+      return cuda_fail(c, e, "graph instantiate");
+    }
+    c->g_W = W;
+    c->g_sx = sx;
+    c->g_sy = sy;
+    c->g_dt = dtkey;
+  }
+  for (int32_t i = 0; i < nsteps; ++i) {
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  }
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_get_status(ase_df_ctx* c, uint32_t* flags, double* last_dt, double* t) {
+  if (!c) return ASE_DF_E_INVAL;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_status sync");
+  DevState h;
+  e = cudaMemcpy(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_status copy");
+  if (flags) *flags = h.flags;
+  if (last_dt) *last_dt = h.last_dt;
+  if (t) *t = h.t;
+  if (h.flags & ASE_DF_FLAG_NONPHYSICAL) return fail(c, ASE_DF_E_NONPHYSICAL, "non-physical state on the device");
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_profile_enable(ase_df_ctx* c, int32_t enable) {
+  if (!c) return ASE_DF_E_INVAL;
+  if (enable) {
+    cudaDeviceSynchronize();
+    prof_clear(c);
+  }
+  c->prof_on = enable != 0;
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_profile_read(ase_df_ctx* c, double* ms, int64_t* n) {
+  if (!c || !ms || !n) return c ? fail(c, ASE_DF_E_INVAL, "NULL pointer") : ASE_DF_E_INVAL;
+  for (int k = 0; k < 4; ++k) { ms[k] = 0.0; n[k] = 0; }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile_read sync");
+  for (size_t i = 0; i < c->prof_kind->size(); ++i) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, (*c->prof_ev)[2 * i], (*c->prof_ev)[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile_read elapsed");
+    const int k = (*c->prof_kind)[i];
+    ms[k] += t;
+    n[k] += 1;
+  }
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_reset(ase_df_ctx* c, double t, void* stream) {
+  if (!c) return ASE_DF_E_INVAL;
+  cudaError_t e = launch_state_kernel(c->st, 0, t, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reset");
+  c->last_stream = (cudaStream_t)stream;
+  return ASE_DF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal declarations shared by the CUDA translation units of the ASE-DF library.
+//
+// Method (arXiv 2410.05489): per face, adaptive stencil extension (Sec. 3, Algorithm 1)
+// driven by the discontinuity feedback factor (Sec. 3.1, Eq. 3.2), WENOZ-AO(5,3) with DF
+// damping as the fallback (Sec. 3.2), Gauss-point states (Sec. 2.1), local
+// Lax-Friedrichs flux and discontinuity strength per Gauss point (Sec. 2.3, Sec. 3.1),
+// flux difference (Sec. 2.1, Eq. 2.3) and SSP-RK3 (Sec. 2.3).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace asedf {
+
+// Evaluation points of a reconstruction polynomial on its cell [-1, 0]:
+//   0: xi = 0 (the "plus" face), 1: xi = -1 (the "minus" face), 2..: Gauss points.
+constexpr int kMaxPts = 6;
+
+// Reconstruction tables of one scheme order, built on the host by exact rational
+// inversion of the cell-average moment problem (see ase_df_tables.cpp).
+struct Tables {
+  // lin[b][p][t]: weight of W_{t-4} in the value at point p of the linear polynomial of
+  // the centred (2b+3)-cell stencil (b = 0..3 for 3, 5, 7, 9 cells).
+  double lin[4][kMaxPts][9];
+  // sub[k][p][j]: weight of the j-th cell (offsets k-2+j) of sub-stencil S3_{k-1} in its
+  // undamped quadratic's value at point p.
+  double sub[3][kMaxPts][3];
+  // cq[k][q][j]: coefficient of xi^(q+1) of that quadratic (for the smoothness indicator).
+  double cq[3][2][3];
+  double gw[4];   // Gauss weights on [0, 1]
+  double d5, d3[3];  // linear weights of WENOZ-AO(5,3) (Sec. 3.2, d_Hi = d_Lo = 0.85)
+  double eps;        // 1e-6 (Sec. 3.2)
+};
+
+// Device-resident solver status.
+struct DevState {
+  unsigned long long max_speed_bits;  // atomicMax over the bit patterns of non-negative doubles
+  double dt;        // the step of the current SSP-RK3 step
+  double t;         // time
+  double last_dt;
+  unsigned int flags;
+  unsigned int pad;
+};
+
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2 };
+
+// Grid and boundary description handed to the kernels.
+struct GridInfo {
+  int nx, ny;         // cells (ny = 1 in 1D)
+  int bc[4];          // x-lo, x-hi, y-lo, y-hi
+  int band_j0, band_j1;  // rows whose ghost cells at x < 0 take the inflow state
+  double inflow_cons[4];
+  double gamma;
+  double thres;
+};
+
+struct SweepArgs {
+  const double* W;        // [C][ny][nx]
+  const double* s_norm;   // sigma of the faces normal to the sweep
+  const double* s_tan;    // sigma of the faces along the sweep lines (2D)
+  double* F;              // face fluxes of this direction
+  double* s_out;          // sigma_out of this direction
+  DevState* st;
+};
+
+struct CombineArgs {
+  const double* Fx;   // [C][ny][nx+1]
+  const double* Fy;   // [C][ny+1][nx] (2D)
+  const double* Wn;   // W^n
+  const double* Ws;   // stage input W^(s)
+  double* out;        // W^(s+1) (or L for stage 0)
+  DevState* st;
+  double inv_dx, inv_dy;
+  double dt_fixed;    // > 0: this dt; otherwise the CFL dt (stage 1 computes it)
+  double cfl, t_end, inflow_speed;
+  int stage;          // 0: out = L; 1, 2, 3: SSP-RK3 stages
+};
+
+struct SpeedArgs {
+  const double* W;
+  DevState* st;
+  double inv_dx, inv_dy;
+};
+
+// Host-side launchers, one set per scheme order (ase_df_sweep.cu is compiled once per
+// order).  dim = 1 or 2; dir = 0 (x-faces) or 1 (y-faces).
+cudaError_t launch_sweep_r3(int dim, int dir, const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s);
+cudaError_t launch_sweep_r5(int dim, int dir, const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s);
+cudaError_t launch_sweep_r7(int dim, int dir, const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s);
+cudaError_t launch_sweep_r9(int dim, int dir, const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s);
+
+cudaError_t launch_combine(int dim, const GridInfo& g, const CombineArgs& a, cudaStream_t s);
+cudaError_t launch_max_speed(int dim, const GridInfo& g, const SpeedArgs& a, cudaStream_t s);
+cudaError_t launch_state_kernel(DevState* st, int op, double t, cudaStream_t s);
+
+// Tables of scheme order r (host, exact rational arithmetic).
+void build_tables(int r, int ndim, Tables* out);
+
+}  // namespace asedf

@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every entry point include/ase_df.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(ase_df_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2410_05489_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_symbols()
+    for n in ("ase_df_init", "ase_df_destroy", "ase_df_residual", "ase_df_step", "ase_df_prime_sigma",
+              "ase_df_get_status", "ase_df_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_params_struct_layout_matches_header():
+    """The ctypes mirror of ase_df_params has the C layout (offsets of the last fields)."""
+    from paper_2410_05489_gb300.ase_df import ase_df_params
+
+    assert ase_df_params.bc.offset == 80
+    assert ase_df_params.inflow_state.offset == 96
+    assert ase_df_params.t_end.offset == 144
+    assert ctypes.sizeof(ase_df_params) == 152
+
+
+def test_init_rejects_bad_parameters_without_a_device(lib):
+    """Validation happens before any CUDA call, so it works on a CPU-only host."""
+    from paper_2410_05489_gb300 import ase_df as A
+    from paper_2410_05489_gb300.problems import Problem
+
+    for bad in (dict(order=4), dict(nx=0), dict(gamma=1.0), dict(ndim=3), dict(cfl=0.0)):
+        kw = dict(ndim=2, nx=8, ny=8, order=5)
+        kw.update(bad)
+        pb = Problem(**kw)
+        with pytest.raises(A.AseDfError) as ei:
+            A.ase_df_init(A.params_from_problem(pb))
+        assert ei.value.status == 1
+    pb = Problem(ndim=2, nx=8, ny=8, bc=("periodic", "outflow", "outflow", "outflow"))
+    with pytest.raises(A.AseDfError):
+        A.ase_df_init(A.params_from_problem(pb))
+    pb = Problem(ndim=2, nx=1 << 21, ny=8)
+    with pytest.raises(A.AseDfError) as ei:
+        A.ase_df_init(A.params_from_problem(pb))
+    assert ei.value.status == 6

@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle on the same
+seeded inputs.
+
+Tolerances (per component c, normalised by the largest magnitude of that component):
+  * residual L:               max|L_gpu - L_cpu| / max|L_cpu|      <= 1e-12
+  * face fluxes:              max|F_gpu - F_cpu| / max|F_cpu|      <= 1e-13
+  * sigma_out:                |s_gpu - s_cpu| <= 1e-12 (1 + |s_cpu|) elementwise
+  * after 100 SSP-RK3 steps:  max|W_gpu - W_cpu| / max|W_cpu|      <= 1e-9
+Branch decisions are taken from the same sigma_in with the same association on both
+sides, so they agree exactly; the remaining differences are rounding (FMA contraction,
+reciprocal multiplications).
+"""
+import numpy as np
+import pytest
+
+from paper_2410_05489_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+TOL_L = 1e-12
+TOL_F = 1e-13
+TOL_STEPS = 1e-9
+
+
+@pytest.fixture(scope="module")
+def A():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2410_05489_gb300 import build
+
+    build.build()
+    from paper_2410_05489_gb300 import ase_df
+
+    return ase_df
+
+
+def to_dev(a):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def comp_err(gpu, cpu):
+    errs = []
+    for c in range(cpu.shape[0]):
+        scale = np.abs(cpu[c]).max()
+        d = np.abs(gpu[c] - cpu[c]).max()
+        errs.append(d / scale if scale > 0 else d)
+    return max(errs)
+
+
+def gpu_residual(A, pb, W, sx, sy):
+    import torch
+
+    ctx = A.ase_df_init(A.params_from_problem(pb))
+    try:
+        Wd, sxd, syd = to_dev(W), to_dev(sx), to_dev(sy)
+        L = torch.empty_like(Wd)
+        sxo = torch.empty_like(sxd)
+        syo = torch.empty_like(syd)
+        two = pb.ndim == 2
+        A.ase_df_residual(ctx, Wd, sxd, syd if two else None, L, sxo, syo if two else None)
+        Fx = torch.empty((pb.ncomp, pb.nyc, pb.nx + 1), dtype=torch.float64, device="cuda")
+        Fy = torch.empty((pb.ncomp, pb.ny + 1, pb.nx), dtype=torch.float64, device="cuda") if two else None
+        A.ase_df_copy_face_fluxes(ctx, Fx, Fy)
+        flags, _, _ = A.ase_df_get_status(ctx)
+        return (L.cpu().numpy(), sxo.cpu().numpy(), syo.cpu().numpy(), Fx.cpu().numpy(),
+                Fy.cpu().numpy() if two else None, flags)
+    finally:
+        A.ase_df_destroy(ctx)
+
+
+def check_residual(A, oracle, pb, W, sx, sy):
+    Lc, sxc, syc, Fxc, Fyc, hist = oracle.residual(pb, W, sx, sy)
+    Lg, sxg, syg, Fxg, Fyg, _ = gpu_residual(A, pb, W, sx, sy)
+    assert comp_err(Fxg, Fxc) <= TOL_F
+    if pb.ndim == 2:
+        assert comp_err(Fyg, Fyc) <= TOL_F
+    assert comp_err(Lg, Lc) <= TOL_L, comp_err(Lg, Lc)
+    assert np.all(np.abs(sxg - sxc) <= 1e-12 * (1 + np.abs(sxc)))
+    if pb.ndim == 2:
+        assert np.all(np.abs(syg - syc) <= 1e-12 * (1 + np.abs(syc)))
+    return hist
+
+
+def make_case(kind, ndim, order, seed, nx, ny):
+    if kind == "smooth":
+        pb = P.Problem(ndim=ndim, nx=nx, ny=ny, order=order, bc=("periodic",) * 4,
+                       x1=2.0, y1=1.5)
+        return pb, P.smooth_random(pb, seed)
+    if kind == "noise":
+        pb = P.Problem(ndim=ndim, nx=nx, ny=ny, order=order, bc=("outflow", "outflow", "periodic", "periodic"))
+        return pb, P.white_noise(pb, seed)
+    if kind == "riemann":
+        if ndim == 1:
+            return P.riemann_1d(nx, order, seed)
+        return P.riemann_2d(nx, order, seed, ny=ny)
+    if kind == "jet":
+        pb, W = P.high_mach_jet(nx, ny, order)
+        # a few oracle steps so that the jet has entered the domain
+        from oracle import oracle as O
+
+        W, *_ = O.run(pb, W, nsteps=3)
+        return pb, W
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("order", [3, 5, 7, 9])
+@pytest.mark.parametrize("kind", ["smooth", "noise", "riemann"])
+def test_residual_parity_2d(A, oracle, order, kind):
+    """Several tiles with ragged tails in both directions (tiles are 32 faces x 8 lines)."""
+    pb, W = make_case(kind, 2, order, 10 + order, 67, 45)
+    check_residual(A, oracle, pb, W, *oracle.prime_sigma(pb, W))
+    sx, sy = P.random_sigma(pb, order, 1.0)  # stencil sums straddle sigma_thres = 2
+    hist = check_residual(A, oracle, pb, W, sx, sy)
+    if order >= 5:
+        assert hist[3] > 0  # the WENO/DF fallback was exercised
+
+
+@pytest.mark.parametrize("order", [3, 5, 7, 9])
+@pytest.mark.parametrize("kind", ["smooth", "noise", "riemann"])
+def test_residual_parity_1d(A, oracle, order, kind):
+    pb, W = make_case(kind, 1, order, 20 + order, 300, 1)
+    check_residual(A, oracle, pb, W, *oracle.prime_sigma(pb, W))
+    check_residual(A, oracle, pb, W, *P.random_sigma(pb, order, 1.0))
+
+
+@pytest.mark.parametrize("order", [5, 9])
+def test_residual_parity_jet_inflow(A, oracle, order):
+    pb, W = make_case("jet", 2, order, 0, 80, 40)
+    check_residual(A, oracle, pb, W, *oracle.prime_sigma(pb, W))
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (5, 4), (9, 2), (33, 9)])
+@pytest.mark.parametrize("order", [3, 9])
+def test_residual_parity_tiny_and_edge_grids(A, oracle, shape, order):
+    """Stencils wider than the grid (periodic wrap and outflow clamp), single-cell grids,
+    exact tile multiples plus one."""
+    nx, ny = shape
+    for bc in (("periodic",) * 4, ("outflow",) * 4):
+        pb = P.Problem(ndim=2, nx=nx, ny=ny, order=order, bc=bc)
+        W = P.white_noise(pb, nx * 7 + ny)
+        sx, sy = P.random_sigma(pb, 3, 0.6)
+        check_residual(A, oracle, pb, W, sx, sy)
+        pb1 = P.Problem(ndim=1, nx=nx * ny, order=order, bc=bc)
+        W1 = P.white_noise(pb1, nx + ny)
+        check_residual(A, oracle, pb1, W1, *P.random_sigma(pb1, 4, 0.6))
+
+
+def test_free_stream_is_exact_on_gpu(A):
+    for ndim, r in ((1, 9), (2, 9), (2, 3)):
+        pb = P.Problem(ndim=ndim, nx=40, ny=20, order=r, bc=("periodic",) * 4)
+        prim = (1.3, 0.7, -0.4, 2.1) if ndim == 2 else (1.3, 0.7, 2.1)
+        U = P.conservative([np.full((pb.nyc, pb.nx), v) for v in prim], pb.gamma, ndim)
+        L, sx, sy, *_ = gpu_residual(A, pb, U, *P.zero_sigma(pb))
+        assert np.all(L == 0.0) and np.all(sx == 0.0) and np.all(sy == 0.0)
+
+
+def run_gpu(A, pb, W, nsteps, dt=0.0, t_end=0.0, graph=False):
+    s = A.Solver(pb, W, t_end=t_end)
+    try:
+        if graph:
+            s.run(nsteps, dt)
+        else:
+            for _ in range(nsteps):
+                s.step(dt)
+        flags, last_dt, t = s.status()
+        return s.W.cpu().numpy(), s.sx.cpu().numpy(), s.sy.cpu().numpy(), flags, last_dt, t
+    finally:
+        s.close()
+
+
+def test_prime_and_cfl_dt_parity(A, oracle):
+    for pb, W in (P.isentropic_vortex(48, 7), P.sod(200, 5), P.high_mach_jet(64, 32, 9)):
+        s = A.Solver(pb, W)
+        try:
+            sxg, syg = s.sx.cpu().numpy(), s.sy.cpu().numpy()
+            sxc, syc = oracle.prime_sigma(pb, W)
+            assert np.all(np.abs(sxg - sxc) <= 1e-12 * (1 + np.abs(sxc)))
+            if pb.ndim == 2:
+                assert np.all(np.abs(syg - syc) <= 1e-12 * (1 + np.abs(syc)))
+            s.step()
+            _, dt, t = s.status()
+            dtc = oracle.cfl_dt(pb, W)
+            assert abs(dt - dtc) <= 1e-14 * dtc and abs(t - dt) <= 1e-15 * dt
+        finally:
+            s.close()
+
+
+@pytest.mark.parametrize("order", [5, 7, 9])
+def test_100_steps_parity_vortex(A, oracle, order):
+    pb, W = P.isentropic_vortex(40, order)
+    dt = 0.5 * oracle.cfl_dt(pb, W)
+    Wc, *_ = oracle.run(pb, W, nsteps=100, dt=dt)
+    Wg, _, _, flags, _, t = run_gpu(A, pb, W, 100, dt)
+    assert flags & A.FLAG_NONPHYSICAL == 0
+    assert abs(t - 100 * dt) < 1e-12
+    assert comp_err(Wg, Wc) <= TOL_STEPS
+
+
+def test_100_steps_parity_sod_cfl(A, oracle):
+    """Shock tube with CFL steps (device-side dt), the DF fallback active at the shock."""
+    pb, W = P.sod(200, 5)
+    Wc, sxc, _, tc, n = oracle.run(pb, W, nsteps=100)
+    Wg, sxg, _, flags, _, t = run_gpu(A, pb, W, 100)
+    assert abs(t - tc) <= 1e-12 * tc
+    assert comp_err(Wg, Wc) <= TOL_STEPS
+
+
+def test_graph_run_matches_steps(A):
+    pb, W = P.isentropic_vortex(48, 9)
+    Wa, sxa, sya, *_ = run_gpu(A, pb, W, 7)
+    Wb, sxb, syb, *_ = run_gpu(A, pb, W, 7, graph=True)
+    np.testing.assert_array_equal(Wa, Wb)
+    np.testing.assert_array_equal(sxa, sxb)
+
+
+def test_t_end_clamps_the_last_step(A, oracle):
+    pb, W = P.sod(100, 5)
+    Wc, _, _, tc, n = oracle.run(pb, W, t_end=0.05)
+    Wg, _, _, flags, _, t = run_gpu(A, pb, W, n + 3, t_end=0.05)  # extra steps are no-ops
+    assert abs(t - 0.05) < 1e-15 and abs(tc - 0.05) < 1e-15
+    assert comp_err(Wg, Wc) <= TOL_STEPS
+
+
+def test_nonphysical_state_is_flagged(A):
+    pb, W = P.isentropic_vortex(32, 5)
+    W = W.copy()
+    W[0, 10, 10] = -1.0
+    _, _, _, flags, _, _ = run_gpu(A, pb, W, 1)
+    assert flags & A.FLAG_NONPHYSICAL
+
+
+def test_argument_errors(A):
+    import torch
+
+    pb, W = P.isentropic_vortex(16, 5)
+    s = A.Solver(pb, W)
+    try:
+        L = torch.empty_like(s.W)
+        with pytest.raises(A.AseDfError):  # sigma_out aliasing sigma_in
+            A.ase_df_residual(s.ctx, s.W, s.sx, s.sy, L, s.sx, s.sy)
+        with pytest.raises(A.AseDfError):  # missing sy in 2D
+            A.ase_df_step(s.ctx, s.W, s.sx, None, 0.0)
+        with pytest.raises(A.AseDfError):
+            A.ase_df_step(s.ctx, s.W, s.sx, s.sy, float("nan"))
+    finally:
+        s.close()
