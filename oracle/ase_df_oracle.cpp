@@ -538,8 +538,10 @@ void to_face_frame(real* q, int dir, int C) {
 // columns) the tangential stencils reach, to both of its faces; (2) per face, the
 // tangential reconstruction at the Gauss points and the Gauss-point fluxes.
 // ---------------------------------------------------------------------------------
+// Faces f in [f_lo, f_hi] on lines b in [b_lo, b_hi] (the whole grid: [0, n] x [0, m-1]).
 void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const double* sy_in,
-                 int dir, double* Fout, double* sig_out, int64_t* hist) {
+                 int dir, double* Fout, double* sig_out, int64_t* hist, int64_t f_lo, int64_t f_hi,
+                 int64_t b_lo, int64_t b_hi) {
   const int r = g.p->order;
   const int k = (r - 1) / 2;
   const int C = g.C;
@@ -556,15 +558,16 @@ void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const dou
   const double* sig_n = (dir == 0) ? sx_in : sy_in;  // normal-direction strengths
   const double* sig_t = (dir == 0) ? sy_in : sx_in;  // tangential-direction strengths
 
-  // Pass 1: normal reconstructions of cells a = -1..n (index a+1) on lines
-  // b = -kt..mlines-1+kt (index b+kt), to the "plus" face (QP) and "minus" face (QM).
-  const int64_t na = n + 2, nb = mlines + 2 * kt;
+  // Pass 1: normal reconstructions of cells a = f_lo-1..f_hi (index a-f_lo+1) on lines
+  // b = b_lo-kt..b_hi+kt (index b-b_lo+kt), to the "plus" face (QP) and "minus" face (QM).
+  (void)mlines;
+  const int64_t na = f_hi - f_lo + 2, nb = b_hi - b_lo + 1 + 2 * kt;
   std::vector<real> QP((size_t)(na * nb * C)), QM((size_t)(na * nb * C));
   std::vector<int> brP((size_t)(na * nb)), brM((size_t)(na * nb));
-  for (int64_t b = -kt; b < mlines + kt; ++b) {
-    for (int64_t a = -1; a <= n; ++a) {
+  for (int64_t b = b_lo - kt; b <= b_hi + kt; ++b) {
+    for (int64_t a = f_lo - 1; a <= f_hi; ++a) {
       int64_t i = (dir == 0) ? a : b, j = (dir == 0) ? b : a;
-      size_t idx = (size_t)((b + kt) * na + (a + 1));
+      size_t idx = (size_t)((b - b_lo + kt) * na + (a - f_lo + 1));
       real out[4];
       brP[idx] = normal_recon(g, Wd, sig_n, dir, i, j, true, out);
       for (int c = 0; c < C; ++c) QP[idx * C + c] = out[c];
@@ -574,25 +577,25 @@ void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const dou
   }
 
   // Pass 2: faces.  Face f (0..n) on line b sits between cells f-1 and f.
-  for (int64_t b = 0; b < mlines; ++b) {
-    for (int64_t f = 0; f <= n; ++f) {
+  for (int64_t b = b_lo; b <= b_hi; ++b) {
+    for (int64_t f = f_lo; f <= f_hi; ++f) {
       real stateL[4][4], stateR[4][4];
       for (int side = 0; side < 2; ++side) {
         const int64_t a = (side == 0) ? f - 1 : f;   // reconstructing cell
         const std::vector<real>& Qv = (side == 0) ? QP : QM;
         real (*state)[4] = (side == 0) ? stateL : stateR;
         if (!twoD) {
-          size_t idx = (size_t)(a + 1);
+          size_t idx = (size_t)(a - f_lo + 1);
           for (int c = 0; c < C; ++c) state[0][c] = Qv[idx * C + c];
           hist[(side == 0 ? brP : brM)[idx]]++;
           continue;
         }
         real Q[9][4];
         for (int t = -k; t <= k; ++t) {
-          size_t idx = (size_t)((b + t + kt) * na + (a + 1));
+          size_t idx = (size_t)((b - b_lo + t + kt) * na + (a - f_lo + 1));
           for (int c = 0; c < C; ++c) Q[t + k][c] = Qv[idx * C + c];
         }
-        hist[(side == 0 ? brP : brM)[(size_t)((b + kt) * na + (a + 1))]]++;
+        hist[(side == 0 ? brP : brM)[(size_t)((b - b_lo + kt) * na + (a - f_lo + 1))]]++;
         // tangential strengths of the reconstructing cell's column (dir 0) / row (dir 1)
         real sigt[8];
         for (int m = -3; m <= 4; ++m) {
@@ -638,21 +641,23 @@ void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const dou
 }
 
 // Sec. 2.1, Eq. (2.3): L = -(1/|Omega|) sum over faces |l| * (Gauss-averaged flux . n).
+// Rows row_lo..row_hi of L (all rows: 0..ny-1); sigma_out and the face fluxes are
+// written for the faces those rows need.
 int residual(const OracleParams* p, const double* W, const double* sx_in, const double* sy_in,
              double* L, double* sx_out, double* sy_out, double* Fx_out, double* Fy_out,
-             int64_t* hist) {
+             int64_t* hist, int64_t row_lo, int64_t row_hi) {
   Grid g = make_grid(p);
   const int C = g.C;
   const int64_t nx = g.nx, ny = g.ny;
   std::vector<double> Fx((size_t)(C * ny * (nx + 1)));
   std::vector<double> Fy;
-  face_fluxes(g, W, sx_in, sy_in, 0, Fx.data(), sx_out, hist);
+  face_fluxes(g, W, sx_in, sy_in, 0, Fx.data(), sx_out, hist, 0, nx, row_lo, row_hi);
   if (p->ndim == 2) {
     Fy.resize((size_t)(C * (ny + 1) * nx));
-    face_fluxes(g, W, sx_in, sy_in, 1, Fy.data(), sy_out, hist);
+    face_fluxes(g, W, sx_in, sy_in, 1, Fy.data(), sy_out, hist, row_lo, row_hi + 1, 0, nx - 1);
   }
   for (int c = 0; c < C; ++c)
-    for (int64_t j = 0; j < ny; ++j)
+    for (int64_t j = row_lo; j <= row_hi; ++j)
       for (int64_t i = 0; i < nx; ++i) {
         real dFx = real(Fx[((int64_t)c * ny + j) * (nx + 1) + i + 1]) -
                    real(Fx[((int64_t)c * ny + j) * (nx + 1) + i]);
@@ -713,9 +718,22 @@ int oracle_residual(const OracleParams* p, const double* W, const double* sx_in,
                     const double* sy_in, double* L, double* sx_out, double* sy_out,
                     double* Fx, double* Fy, int64_t* hist) {
   int64_t h[BR_COUNT] = {0};
-  int rc = residual(p, W, sx_in, sy_in, L, sx_out, sy_out, Fx, Fy, h);
+  const int64_t ny = (p->ndim == 1) ? 1 : p->ny;
+  int rc = residual(p, W, sx_in, sy_in, L, sx_out, sy_out, Fx, Fy, h, 0, ny - 1);
   if (hist) for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[b];
   return rc;
+}
+
+// The residual of rows row_lo..row_hi only (the same arithmetic, restricted to the faces
+// those rows need); L, sigma_out and the face fluxes are full-size arrays of which only
+// those entries are written.  Used to check sampled rows of full-size grids.
+int oracle_residual_rows(const OracleParams* p, const double* W, const double* sx_in,
+                         const double* sy_in, double* L, double* sx_out, double* sy_out,
+                         int64_t row_lo, int64_t row_hi) {
+  const int64_t ny = (p->ndim == 1) ? 1 : p->ny;
+  if (row_lo < 0 || row_hi >= ny || row_lo > row_hi) return -1;
+  int64_t h[BR_COUNT] = {0};
+  return residual(p, W, sx_in, sy_in, L, sx_out, sy_out, nullptr, nullptr, h, row_lo, row_hi);
 }
 
 // CFL time step dt = cfl / max((|u|+c)/dx + (|v|+c)/dy); returns -1 if a cell average

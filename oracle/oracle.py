@@ -63,6 +63,9 @@ _libs = {}
 def _setup(lib):
     lib.oracle_residual.argtypes = [ctypes.POINTER(_Params), _P, _P, _P, _P, _P, _P, _P, _P, _I64]
     lib.oracle_residual.restype = ctypes.c_int
+    lib.oracle_residual_rows.argtypes = [ctypes.POINTER(_Params), _P, _P, _P, _P, _P, _P, ctypes.c_int64,
+                                         ctypes.c_int64]
+    lib.oracle_residual_rows.restype = ctypes.c_int
     lib.oracle_cfl_dt.argtypes = [ctypes.POINTER(_Params), _P]
     lib.oracle_cfl_dt.restype = ctypes.c_double
     lib.oracle_step.argtypes = [ctypes.POINTER(_Params), _P, _P, _P, ctypes.c_double, _I64]
@@ -134,6 +137,22 @@ def residual(pb, W, sx, sy, counting: bool = False):
     _lib(counting).oracle_residual(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), _ptr(L), _ptr(sxo),
                                    _ptr(syo), _ptr(Fx), _ptr(Fy), hist.ctypes.data_as(_I64))
     return L, sxo, syo, Fx, Fy, hist
+
+
+def residual_rows(pb, W, sx, sy, row_lo: int, row_hi: int):
+    """Rows row_lo..row_hi of L, sigma_x_out (same rows) and sigma_y_out (faces row_lo..
+    row_hi+1) of one residual evaluation; the oracle computes only what those rows need."""
+    W, sx, sy = _f64(W), _f64(sx), _f64(sy)
+    L = np.full(pb.state_shape, np.nan)
+    sxo = np.full(pb.sx_shape, np.nan)
+    syo = np.full(pb.sy_shape, np.nan)
+    p = _params(pb)
+    rc = _lib().oracle_residual_rows(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), _ptr(L), _ptr(sxo), _ptr(syo),
+                                     row_lo, row_hi)
+    if rc != 0:
+        raise ValueError("bad row range")
+    return (L[:, row_lo:row_hi + 1], sxo[row_lo:row_hi + 1],
+            syo[row_lo:row_hi + 2] if pb.ndim == 2 else None)
 
 
 def prime_sigma(pb, W) -> Tuple[np.ndarray, np.ndarray]:

@@ -1,0 +1,120 @@
+"""GPU checks at the full workload sizes, in the launch configuration the benchmark times:
+sampled rows against the oracle (which computes just those rows), and properties that
+hold at any size (conservation, positivity)."""
+import numpy as np
+import pytest
+
+from paper_2410_05489_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+ROWS_1024 = (0, 1, 255, 511, 512, 1022, 1023)
+
+
+@pytest.fixture(scope="module")
+def A():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2410_05489_gb300 import build
+
+    build.build()
+    from paper_2410_05489_gb300 import ase_df
+
+    return ase_df
+
+
+def dev(a):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def row_check(oracle, pb, W, sx, sy, Lg, sxg, syg, rows):
+    for j in rows:
+        Lc, sxc, syc = oracle.residual_rows(pb, W, sx, sy, j, j)
+        for c in range(pb.ncomp):
+            scale = max(np.abs(Lc[c]).max(), 1e-300)
+            assert np.abs(Lg[c, j:j + 1] - Lc[c]).max() <= 1e-12 * scale, (j, c)
+        g = sxg[j:j + 1]
+        assert np.all(np.abs(g - sxc) <= 1e-12 * (1 + np.abs(sxc)) + 1e-14 * sxc * sxc)
+        g = syg[j:j + 2]
+        assert np.all(np.abs(g - syc) <= 1e-12 * (1 + np.abs(syc)) + 1e-14 * syc * syc)
+
+
+@pytest.mark.parametrize("order", [7, 9])
+def test_vortex_1024_sampled_rows(A, oracle, order):
+    """The benchmark workload (1024^2 periodic vortex), with seeded random sigma_in so
+    that every branch of Algorithm 1 occurs; rows at both periodic seams and inside."""
+    import torch
+
+    pb, W = P.isentropic_vortex(1024, order)
+    sx, sy = P.random_sigma(pb, 99, 1.0)
+    s = A.Solver(pb, W)
+    try:
+        L, sxo, syo = s.residual(s.W, dev(sx), dev(sy))
+        torch.cuda.synchronize()
+        row_check(oracle, pb, W, sx, sy, L.cpu().numpy(), sxo.cpu().numpy(), syo.cpu().numpy(), ROWS_1024)
+    finally:
+        s.close()
+
+
+def test_vortex_1024_step_conserves(A):
+    """One CFL SSP-RK3 step of the benchmark workload: the periodic totals are conserved
+    to rounding, the state stays physical and the device status is clean."""
+    pb, W = P.isentropic_vortex(1024, 9)
+    s = A.Solver(pb, W)
+    try:
+        tot0 = W.sum(axis=(1, 2))
+        for _ in range(3):
+            s.step()
+        flags, dt, t = s.status()
+        Wn = s.W.cpu().numpy()
+        tot = Wn.sum(axis=(1, 2))
+        assert flags == 0 and t > 0
+        assert np.all(np.abs(tot - tot0) <= 1e-12 * np.abs(W).sum(axis=(1, 2)))
+    finally:
+        s.close()
+
+
+def test_jet_1600x800_sampled_rows(A, oracle):
+    """The high-Mach jet grid with its inflow band: rows at the domain edges and at both
+    edges of the band (rows 319/320 and 479/480), primed sigma from the oracle."""
+    import torch
+
+    pb, W = P.high_mach_jet(1600, 800, 9)
+    rows = (0, 319, 320, 479, 480, 799)
+    sx, sy = P.random_sigma(pb, 5, 0.8)
+    s = A.Solver(pb, W)
+    try:
+        L, sxo, syo = s.residual(s.W, dev(sx), dev(sy))
+        torch.cuda.synchronize()
+        row_check(oracle, pb, W, sx, sy, L.cpu().numpy(), sxo.cpu().numpy(), syo.cpu().numpy(), rows)
+    finally:
+        s.close()
+
+
+def test_jet_1600x800_positivity_to_t_end(A):
+    """Sec. 4.3, Example 6 (Ma ~ 20000 jet, Lax-Friedrichs, ASE-DF(9,7,5,3)) on the
+    1600 x 800 grid: density and pressure stay positive, nothing non-finite, up to
+    t = 1e-5."""
+    pb, W = P.high_mach_jet(1600, 800, 9)
+    s = A.Solver(pb, W, t_end=1e-5)
+    try:
+        n = 0
+        while True:
+            s.run(50)
+            n += 50
+            flags, dt, t = s.status()
+            assert not flags & A.FLAG_NONPHYSICAL, (n, t)
+            if t >= 1e-5 * (1 - 1e-12) or n > 2000:
+                break
+        Wn = s.W.cpu().numpy()
+        rho = Wn[0]
+        p = (pb.gamma - 1) * (Wn[3] - 0.5 * (Wn[1] ** 2 + Wn[2] ** 2) / rho)
+        assert np.all(np.isfinite(Wn)) and rho.min() > 0 and p.min() > 0
+        assert abs(t - 1e-5) < 1e-15
+        # the jet has travelled about 7418 * 1e-5 = 0.074 into the domain
+        assert Wn[1, 400, 100] > 1e3
+    finally:
+        s.close()
