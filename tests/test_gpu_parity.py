@@ -8,8 +8,9 @@ Tolerances (per component c, normalised by the largest magnitude of that compone
     (sigma ~ |p_l - p_r| / p: where a Gauss-point pressure is small, p carries the
     rounding of E - |m|^2/(2 rho), relative ~ eps E / p <~ eps sigma, so the error of
     sigma grows like eps sigma^2)
-  * L is normalised by max(max|L_c|, 1e-4 max|F_c| (1/dx + 1/dy)): below that, L itself
-    is flux-difference cancellation noise (e.g. a single-cell grid)
+  * L is normalised by max(max|L_c|, 1e-3 max|F_c| (1/dx + 1/dy)): the rounding of a
+    flux difference is ~1e-15 max|F| / dx, so below that floor L itself is
+    cancellation noise (e.g. a single-cell grid with random sigma)
   * after 100 SSP-RK3 steps:  max|W_gpu - W_cpu| / max|W_cpu|      <= 1e-9
 Branch decisions are taken from the same sigma_in with the same association on both
 sides, so they agree exactly; the remaining differences are rounding (FMA contraction,
@@ -60,7 +61,7 @@ def comp_err(gpu, cpu, floor=None):
 def residual_floor(pb, Fx, Fy):
     inv = 1.0 / pb.dx + (1.0 / pb.dy if pb.ndim == 2 else 0.0)
     F = [max(np.abs(Fx[c]).max(), np.abs(Fy[c]).max() if Fy is not None else 0.0) for c in range(pb.ncomp)]
-    return [1e-4 * f * inv for f in F]
+    return [1e-3 * f * inv for f in F]
 
 
 def gpu_residual(A, pb, W, sx, sy):
