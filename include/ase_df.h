@@ -139,6 +139,24 @@ const char* ase_df_last_error(const ase_df_ctx* ctx);
 ase_df_status ase_df_profile_enable(ase_df_ctx* ctx, int32_t enable);
 ase_df_status ase_df_profile_read(ase_df_ctx* ctx, double* ms, int64_t* n);
 
+/* The residual of ase_df_residual for callers that cannot allocate device memory (code
+ * running inside someone else's CUDA graph capture, real-time loops that must not
+ * synchronise the device, frameworks that own every device byte through their own
+ * pool).  The paper has no counterpart: this is a library-integration entry point.
+ * It takes no context: the face-flux scratch is one file-scope __device__ array of
+ * 2^21 doubles (16 MiB, held by every GPU that loads the library until exit), so it
+ * calls no cudaMalloc / cudaFree and no allocating library routine.  Arguments as
+ * ase_df_residual plus the problem p.  Limit: C*ny*(nx+1) + C*(ny+1)*nx (2D) or
+ * 3*(nx+1) (1D) face-flux doubles <= 2^21 - 32, e.g. 2D grids up to 511 x 511; larger
+ * grids return ASE_DF_E_BOUNDS.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress with that device current): make it before any
+ * stream capture.  All calls share the array, which keeps the last call's contents:
+ * calls that overlap on the GPU race and must not be issued.  Device-side conditions
+ * (status flags) are not reported; errors are the returned status only. */
+ase_df_status ase_df_residual_noalloc(const ase_df_params* p, const double* W, const double* sx_in,
+                                      const double* sy_in, double* L, double* sx_out, double* sy_out,
+                                      void* stream);
+
 /* FP64 throughput microbenchmark used as the roofline denominator: independent FMA
  * chains on every SM; writes the achieved FP64 FMA instructions per second into
  * *fma_per_s (flops = 2x).  Synchronises the device. */
