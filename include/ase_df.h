@@ -63,6 +63,10 @@ typedef enum {
 #define ASE_DF_FLAG_POSITIVITY  0x2u   /* informational: a Gauss point took the first-order
                                           states (non-physical reconstructed state) */
 #define ASE_DF_FLAG_DT          0x4u   /* the CFL step came out non-positive or non-finite */
+#define ASE_DF_FLAG_FROZEN      0x8u   /* informational: to stay physical, a cell kept its stage's
+                                          combination of W^n and W^(s) without the flux update
+                                          (last resort of the positivity repair; that cell is
+                                          not conservative in that stage) */
 
 /* Problem statement (Sec. 2: 1D/2D Euler on a uniform Cartesian grid). */
 typedef struct {
@@ -111,7 +115,14 @@ ase_df_status ase_df_copy_face_fluxes(ase_df_ctx* ctx, double* Fx, double* Fy, v
  * on exit; sx/sy hold sigma^n on entry and the third stage's sigma on exit (each stage
  * consumes the sigma of the stage before).  dt > 0: that step; dt <= 0: the CFL step of
  * W^n (including the inflow state, if any), shortened to t_end.  The device keeps the
- * time t and the last dt (ase_df_get_status). */
+ * time t and the last dt (ase_df_get_status).  After every stage, cells whose new
+ * average is non-physical are updated again with first-order Lax-Friedrichs fluxes on
+ * their faces (the paper's transition to first order for positivity, Sec. 1; up to 8
+ * passes, each re-doing the neighbours of newly failing cells); a cell still
+ * non-physical after that keeps its stage's combination of W^n and W^(s) without the
+ * flux update, with E raised to give p = 1e-13 of the kinetic energy density where
+ * rounding leaves a near-vacuum p <= 0 (ASE_DF_FLAG_FROZEN); ASE_DF_FLAG_NONPHYSICAL is
+ * raised only if that still fails (rho <= 0 or non-finite values). */
 ase_df_status ase_df_step(ase_df_ctx* ctx, double* W, double* sx, double* sy, double dt,
                           void* stream);
 
@@ -124,6 +135,16 @@ ase_df_status ase_df_run(ase_df_ctx* ctx, double* W, double* sx, double* sy, dou
  * the last dt and the time t.  Returns ASE_DF_E_NONPHYSICAL if that bit is set. */
 ase_df_status ase_df_get_status(ase_df_ctx* ctx, uint32_t* flags, double* last_dt, double* t);
 
+/* Diagnostics of the positivity repair of the stage updates (ase_df_step): synchronises,
+ * then writes into last_stage[18] (may be NULL) the counts of the most recent stage --
+ * [0]: cells the high-order update left non-physical, [p] (p = 1..8): cells newly
+ * non-physical after repair pass p, [9 + p] (p = 1..8): cells still non-physical after
+ * pass p -- into *total (may be NULL) the number of cells marked since the last
+ * ase_df_reset, and into *frozen (may be NULL) the number of cells that took the last
+ * resort since then. */
+ase_df_status ase_df_get_repair_stats(ase_df_ctx* ctx, uint32_t* last_stage, uint64_t* total,
+                                      uint64_t* frozen);
+
 /* Clears the device status word and sets the device time t. */
 ase_df_status ase_df_reset(ase_df_ctx* ctx, double t, void* stream);
 
@@ -134,8 +155,9 @@ const char* ase_df_last_error(const ase_df_ctx* ctx);
 /* Kernel timing with CUDA events recorded on the launching stream around every sweep,
  * combine and wave-speed launch of this context (enable != 0 starts a new record, 0
  * stops recording).  ase_df_profile_read synchronises, then returns per kernel kind
- * (0: x-face sweep, 1: y-face sweep, 2: combine, 3: wave-speed reduction) the summed
- * milliseconds ms[4] and the launch counts n[4]; at most 65536 launches are recorded. */
+ * (0: x-face sweep, 1: y-face sweep, 2: combine, 3: wave-speed reduction, 4: positivity
+ * repair pass) the summed milliseconds ms[5] and the launch counts n[5]; at most 65536
+ * launches are recorded. */
 ase_df_status ase_df_profile_enable(ase_df_ctx* ctx, int32_t enable);
 ase_df_status ase_df_profile_read(ase_df_ctx* ctx, double* ms, int64_t* n);
 

@@ -49,6 +49,16 @@
 //   G21 positivity: a Gauss point whose reconstructed state (either side) has rho <= 0,
 //       p <= 0 or a non-finite value takes the two cell averages for its flux, and its
 //       sigma is set to 1e30.
+//   G21b positivity of the stage update (the paper's "transition to a first-order scheme
+//       for preserving positivity"): after each RK stage a cell whose new average is
+//       non-physical is marked; every face of a marked cell takes the first-order
+//       Lax-Friedrichs flux of the stage's cell averages (and sigma 1e30), and every
+//       cell next to such a face is updated again; cells that turn non-physical in a pass
+//       are marked for the next one (8 passes at most).  A cell still non-physical after
+//       that keeps the stage's combination of W^n and W^(s) without the flux update (a
+//       convex combination of physical states); where rounding of a near-vacuum
+//       pressure still leaves p <= 0, E is raised to give p = 1e-13 of the kinetic
+//       energy density.  Not conservative at that cell.
 //
 // Data layout: W is [C][ny][nx] (C = 3 in 1D: rho, rho u, E; C = 4 in 2D: rho, rho u,
 // rho v, E), sigma_x is [ny][nx+1] (x-face f sits between cells f-1 and f), sigma_y is
@@ -275,7 +285,9 @@ void weno_ao53_df(const real* Wm, const real* alpha, int npts, const double* xi,
 // Branch identifiers (also the histogram slots).
 enum {
   BR_LIN9 = 0, BR_LIN7 = 1, BR_LIN5 = 2, BR_WENO = 3, BR_LIN3 = 4, BR_DF3 = 5, BR_FIRST = 6,
-  BR_COUNT = 7
+  BR_REPAIRED = 7,  // cell updates redone with first-order faces (reading G21b)
+  BR_FROZEN = 8,    // cells left without a flux update to stay physical (reading G21b)
+  BR_COUNT = 9
 };
 
 // Algorithm 1 capped at the scheme order r (reading G13) for one cell and one
@@ -745,37 +757,180 @@ double oracle_cfl_dt(const OracleParams* p, const double* W) {
   return p->cfl / s;
 }
 
-// One SSP-RK3 step (Sec. 2.3) in place, with the sigma feedback of reading G7: each
+}  // extern "C"
+
+namespace {
+
+// SSP-RK3 stage combination (Sec. 2.3, Eq. SSP-RK3) of one value.
+real rk_combine(int stage, real dt, real wn, real ws, real L) {
+  if (stage == 1) return wn + dt * L;
+  if (stage == 2) return real(0.75) * wn + real(0.25) * ws + real(0.25) * dt * L;
+  return real(1.0 / 3.0) * wn + real(2.0 / 3.0) * ws + real(2.0 / 3.0) * dt * L;
+}
+
+const int kRepairPasses = 8;
+
+// Reading G21b.  Stage update of every cell from the Gauss-averaged face fluxes Fx, Fy
+// of the stage, then the first-order repair passes.  Returns false if a cell is still
+// non-physical afterwards.
+bool stage_update(const Grid& g, int stage, real dt, const double* Wn, const double* Ws,
+                  const double* Fx, const double* Fy, double* sx_out, double* sy_out, double* Wout,
+                  int64_t* hist) {
+  const int C = g.C;
+  const int64_t nx = g.nx, ny = g.ny;
+  const int ndir = (g.p->ndim == 2) ? 2 : 1;
+  std::vector<int> mark((size_t)(nx * ny), 0);
+  auto marked = [&](int64_t i, int64_t j, int pass) {
+    const int m = mark[(size_t)(j * nx + i)];
+    return m >= 1 && m <= pass;
+  };
+  // the cell across a face, or -1 where that is a ghost (non-periodic boundary)
+  auto across = [&](int64_t k, int64_t n, int bc_lo, int bc_hi) -> int64_t {
+    if (k >= 0 && k < n) return k;
+    return (k < 0 ? bc_lo : bc_hi) == BC_PERIODIC ? wrap(k, n) : -1;
+  };
+  auto physical = [&](int64_t i, int64_t j) {
+    real q[4];
+    for (int c = 0; c < C; ++c) q[c] = real(Wout[((int64_t)c * ny + j) * nx + i]);
+    return primitives(q, C, g.p->gamma).ok;
+  };
+  // update of cell (i, j); in a repair pass the faces next to a marked cell take the
+  // first-order flux.  Returns whether any face did.
+  auto update = [&](int64_t i, int64_t j, int pass) {
+    real Fa[2][2][4];  // [dir][lower/upper face][component]
+    bool any_first = false;
+    for (int dir = 0; dir < ndir; ++dir) {
+      for (int side = 0; side < 2; ++side) {
+        const int64_t f = ((dir == 0) ? i : j) + side;
+        bool first = false;
+        if (pass > 0) {
+          const int64_t o = (dir == 0) ? across(i + (side ? 1 : -1), nx, g.p->bc[0], g.p->bc[1])
+                                       : across(j + (side ? 1 : -1), ny, g.p->bc[2], g.p->bc[3]);
+          const bool other = o >= 0 && ((dir == 0) ? marked(o, j, pass) : marked(i, o, pass));
+          first = marked(i, j, pass) || other;
+        }
+        if (first) {
+          real cl[4], cr[4], F[4], sg;
+          for (int c = 0; c < C; ++c) {
+            if (dir == 0) { cl[c] = g.W(Ws, c, f - 1, j); cr[c] = g.W(Ws, c, f, j); }
+            else { cl[c] = g.W(Ws, c, i, f - 1); cr[c] = g.W(Ws, c, i, f); }
+          }
+          to_face_frame(cl, dir, C);
+          to_face_frame(cr, dir, C);
+          lf_flux_point(cl, cr, cl, cr, C, g.p->gamma, F, &sg);
+          to_face_frame(F, dir, C);
+          for (int c = 0; c < C; ++c) Fa[dir][side][c] = F[c];
+          if (dir == 0) sx_out[j * (nx + 1) + f] = kSigmaBig;
+          else sy_out[f * nx + i] = kSigmaBig;
+          any_first = true;
+        } else {
+          for (int c = 0; c < C; ++c)
+            Fa[dir][side][c] = (dir == 0) ? real(Fx[((int64_t)c * ny + j) * (nx + 1) + f])
+                                          : real(Fy[((int64_t)c * (ny + 1) + f) * nx + i]);
+        }
+      }
+    }
+    for (int c = 0; c < C; ++c) {
+      real Lv = -((Fa[0][1][c] - Fa[0][0][c]) / real(g.dx));
+      if (ndir == 2) Lv = Lv - (Fa[1][1][c] - Fa[1][0][c]) / real(g.dy);
+      const int64_t w = ((int64_t)c * ny + j) * nx + i;
+      Wout[w] = val(rk_combine(stage, dt, real(Wn[w]), real(Ws[w]), Lv));
+    }
+    return any_first;
+  };
+
+  int newly = 0;
+  for (int64_t j = 0; j < ny; ++j)
+    for (int64_t i = 0; i < nx; ++i) {
+      update(i, j, 0);
+      if (!physical(i, j)) { mark[(size_t)(j * nx + i)] = 1; ++newly; }
+    }
+  for (int pass = 1; pass <= kRepairPasses && newly > 0; ++pass) {
+    newly = 0;
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        bool touched = marked(i, j, pass);
+        for (int side = 0; side < 2 && !touched; ++side) {
+          const int64_t oi = across(i + (side ? 1 : -1), nx, g.p->bc[0], g.p->bc[1]);
+          if (oi >= 0 && marked(oi, j, pass)) touched = true;
+          if (ndir == 2) {
+            const int64_t oj = across(j + (side ? 1 : -1), ny, g.p->bc[2], g.p->bc[3]);
+            if (oj >= 0 && marked(i, oj, pass)) touched = true;
+          }
+        }
+        if (!touched) continue;
+        if (update(i, j, pass) && hist) hist[BR_REPAIRED]++;
+        if (!physical(i, j) && mark[(size_t)(j * nx + i)] == 0) {
+          mark[(size_t)(j * nx + i)] = pass + 1;
+          ++newly;
+        }
+      }
+  }
+  bool ok = true;
+  for (int64_t j = 0; j < ny; ++j)
+    for (int64_t i = 0; i < nx; ++i) {
+      if (physical(i, j)) continue;
+      for (int c = 0; c < C; ++c) {
+        const int64_t w = ((int64_t)c * ny + j) * nx + i;
+        Wout[w] = val(rk_combine(stage, dt, real(Wn[w]), real(Ws[w]), real(0.0)));
+      }
+      const int64_t e = ((int64_t)(C - 1) * ny + j) * nx + i;
+      if (!physical(i, j) && Wout[j * nx + i] > 0.0 && std::isfinite(Wout[e])) {
+        // pressure at the rounding level of E: p := 1e-13 of the kinetic energy density
+        real rho = real(Wout[j * nx + i]), mm = real(0.0);
+        for (int c = 1; c < C - 1; ++c) {
+          real m = real(Wout[((int64_t)c * ny + j) * nx + i]);
+          mm = mm + m * m;
+        }
+        real ke = real(0.5) * mm / rho;
+        real big = rmax(ke, rabs(real(Wout[e])));
+        Wout[e] = val(ke + real(1e-13) * big / real(g.p->gamma - 1.0));
+      }
+      if (hist) hist[BR_FROZEN]++;
+      if (!physical(i, j)) ok = false;
+    }
+  return ok;
+}
+
+}  // namespace
+
+extern "C" {
+
+// One SSP-RK3 step (Sec. 2.3) in place, with the sigma feedback of reading G7 (each
 // stage consumes the sigma the previous stage produced; sx / sy hold sigma^n on entry
-// and the last stage's sigma on exit.  dt <= 0 takes the CFL step.  Returns the dt
-// used (negative on a non-physical cell average).
+// and the last stage's sigma on exit) and the positivity repair of reading G21b after
+// each stage.  dt <= 0 takes the CFL step.  Returns the dt used; negative if a cell
+// average is non-physical at the start or stays non-physical after a stage.
 double oracle_step(const OracleParams* p, double* W, double* sx, double* sy, double dt,
                    int64_t* hist) {
   Grid g = make_grid(p);
   const int64_t nW = (int64_t)g.C * g.nx * g.ny;
   const int64_t nsx = g.ny * (g.nx + 1);
   const int64_t nsy = (p->ndim == 2) ? (g.ny + 1) * g.nx : 1;
+  const int64_t nFx = (int64_t)g.C * g.ny * (g.nx + 1);
+  const int64_t nFy = (p->ndim == 2) ? (int64_t)g.C * (g.ny + 1) * g.nx : 1;
   if (!(dt > 0.0)) {
     dt = oracle_cfl_dt(p, W);
     if (dt < 0.0) return dt;
   }
   std::vector<double> Wn(W, W + nW), W1((size_t)nW), W2((size_t)nW), L((size_t)nW);
   std::vector<double> sxa((size_t)nsx), sya((size_t)nsy), sxb((size_t)nsx), syb((size_t)nsy);
+  std::vector<double> Fx((size_t)nFx), Fy((size_t)nFy);
   const real rdt = real(dt);
+  bool ok = true;
   // stage 1
-  oracle_residual(p, Wn.data(), sx, sy, L.data(), sxa.data(), sya.data(), nullptr, nullptr, hist);
-  for (int64_t n = 0; n < nW; ++n) W1[n] = val(real(Wn[n]) + rdt * real(L[n]));
+  oracle_residual(p, Wn.data(), sx, sy, L.data(), sxa.data(), sya.data(), Fx.data(), Fy.data(), hist);
+  ok &= stage_update(g, 1, rdt, Wn.data(), Wn.data(), Fx.data(), Fy.data(), sxa.data(), sya.data(),
+                     W1.data(), hist);
   // stage 2
-  oracle_residual(p, W1.data(), sxa.data(), sya.data(), L.data(), sxb.data(), syb.data(), nullptr,
-                  nullptr, hist);
-  for (int64_t n = 0; n < nW; ++n)
-    W2[n] = val(real(0.75) * real(Wn[n]) + real(0.25) * real(W1[n]) + real(0.25) * rdt * real(L[n]));
+  oracle_residual(p, W1.data(), sxa.data(), sya.data(), L.data(), sxb.data(), syb.data(), Fx.data(),
+                  Fy.data(), hist);
+  ok &= stage_update(g, 2, rdt, Wn.data(), W1.data(), Fx.data(), Fy.data(), sxb.data(), syb.data(),
+                     W2.data(), hist);
   // stage 3
-  oracle_residual(p, W2.data(), sxb.data(), syb.data(), L.data(), sx, sy, nullptr, nullptr, hist);
-  for (int64_t n = 0; n < nW; ++n)
-    W[n] = val(real(1.0 / 3.0) * real(Wn[n]) + real(2.0 / 3.0) * real(W2[n]) +
-               real(2.0 / 3.0) * rdt * real(L[n]));
-  return dt;
+  oracle_residual(p, W2.data(), sxb.data(), syb.data(), L.data(), sx, sy, Fx.data(), Fy.data(), hist);
+  ok &= stage_update(g, 3, rdt, Wn.data(), W2.data(), Fx.data(), Fy.data(), sx, sy, W, hist);
+  return ok ? dt : -dt;
 }
 
 // sigma^0 (reading G7): the sigma of a residual evaluated with sigma_in = 0.

@@ -23,7 +23,7 @@ _LIB = os.path.join(_BUILD, "libasedf_oracle.so")
 _LIB_COUNT = os.path.join(_BUILD, "libasedf_oracle_count.so")
 _lock = threading.Lock()
 
-BRANCHES = ("lin9", "lin7", "lin5", "weno_df", "lin3", "df3", "first_order")
+BRANCHES = ("lin9", "lin7", "lin5", "weno_df", "lin3", "df3", "first_order", "repaired", "frozen")
 
 
 def _compile(out: str, extra=()) -> None:
@@ -198,6 +198,8 @@ def run(pb, W, t_end: float = 0.0, nsteps: int = 0, dt: float = 0.0, sigma=None)
         if t_end and t + h > t_end:
             h = t_end - t
         W, sx, sy, h = step(pb, W, sx, sy, h)
+        if h < 0:
+            raise FloatingPointError("non-physical state after the step at t=%g" % t)
         t += h
         n += 1
     return W, sx, sy, t, n

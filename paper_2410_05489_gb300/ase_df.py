@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_NONPHYSI
 FLAG_NONPHYSICAL = 0x1
 FLAG_POSITIVITY = 0x2
 FLAG_DT = 0x4
+FLAG_FROZEN = 0x8
 
 
 class AseDfError(RuntimeError):
@@ -70,6 +71,8 @@ def _load():
         "ase_df_run": ([CTX, _VP, _VP, _VP, _c.c_double, _c.c_int32, _VP], _c.c_int),
         "ase_df_get_status": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)], _c.c_int),
         "ase_df_reset": ([CTX, _c.c_double, _VP], _c.c_int),
+        "ase_df_get_repair_stats": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_uint64),
+                                     _c.POINTER(_c.c_uint64)], _c.c_int),
         "ase_df_last_error": ([CTX], _c.c_char_p),
         "ase_df_fp64_fma_rate": ([_c.POINTER(_c.c_double)], _c.c_int),
         "ase_df_profile_enable": ([CTX, _c.c_int32], _c.c_int),
@@ -163,6 +166,15 @@ def ase_df_get_status(ctx) -> Tuple[int, float, float]:
     return int(flags.value), float(dt.value), float(t.value)
 
 
+def ase_df_get_repair_stats(ctx):
+    """-> (last_stage counts [18], cells marked since the last reset, cells frozen)."""
+    arr = (_c.c_uint32 * 18)()
+    tot = _c.c_uint64()
+    frz = _c.c_uint64()
+    _check(ctx, _load().ase_df_get_repair_stats(ctx, arr, _c.byref(tot), _c.byref(frz)))
+    return list(arr), int(tot.value), int(frz.value)
+
+
 def ase_df_reset(ctx, t: float = 0.0, stream=None) -> None:
     _check(ctx, _load().ase_df_reset(ctx, float(t), _stream(stream)))
 
@@ -177,9 +189,9 @@ def ase_df_profile_enable(ctx, enable: bool) -> None:
 
 
 def ase_df_profile_read(ctx):
-    """-> (ms[4], n[4]) per kernel kind: x-sweep, y-sweep, combine, wave-speed."""
-    ms = (_c.c_double * 4)()
-    n = (_c.c_int64 * 4)()
+    """-> (ms[5], n[5]) per kernel kind: x-sweep, y-sweep, combine, wave-speed, repair."""
+    ms = (_c.c_double * 5)()
+    n = (_c.c_int64 * 5)()
     _check(ctx, _load().ase_df_profile_read(ctx, ms, n))
     return list(ms), list(n)
 

@@ -26,6 +26,7 @@ struct ase_df_ctx {
   double *W1, *W2;          // RK stage states
   double *sxa, *sya, *sxb, *syb;  // sigma ping-pong
   double *zsx, *zsy;        // zero sigma (priming)
+  unsigned char* mark;      // per-cell marks of the positivity repair
   DevState* st;
   // CUDA graph of one step (ase_df_run)
   cudaGraphExec_t graph_exec;
@@ -200,6 +201,11 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
       return fail(nullptr, ASE_DF_E_NOMEM, "device allocation of %zu bytes failed", a.n * sizeof(double));
     }
   }
+  if (cudaMalloc((void**)&c->mark, (size_t)g.nx * g.ny) != cudaSuccess) {
+    cudaGetLastError();
+    ase_df_destroy(c);
+    return fail(nullptr, ASE_DF_E_NOMEM, "device allocation of the repair marks failed");
+  }
   if (cudaMalloc((void**)&c->st, sizeof(DevState)) != cudaSuccess) {
     cudaGetLastError();
     ase_df_destroy(c);
@@ -224,6 +230,7 @@ void ase_df_destroy(ase_df_ctx* c) {
   for (double* q : ptrs)
     if (q) cudaFree(q);
   if (c->st) cudaFree(c->st);
+  if (c->mark) cudaFree(c->mark);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   prof_clear(c);
@@ -265,9 +272,13 @@ static cudaError_t face_fluxes(ase_df_ctx* c, const double* W, const double* sx,
   return sweep(c, 1, W, sx, sy, c->Fy, syo, s);
 }
 
+// Stage combination (or L for stage 0); for stages 1..3 followed by the positivity
+// repair passes, which get the stage's sigma_out (sxo, syo).
 static cudaError_t combine(ase_df_ctx* c, int stage, const double* Wn, const double* Ws, double* out,
-                           double dt_fixed, cudaStream_t s) {
+                           double dt_fixed, cudaStream_t s, double* sxo = nullptr, double* syo = nullptr) {
+  cudaError_t e = cudaSuccess;
   CombineArgs a;
+  a.mark = c->mark;
   a.Fx = c->Fx;
   a.Fy = c->Fy;
   a.Wn = Wn;
@@ -281,8 +292,35 @@ static cudaError_t combine(ase_df_ctx* c, int stage, const double* Wn, const dou
   a.t_end = c->p.t_end;
   a.inflow_speed = c->inflow_speed;
   a.stage = stage;
-  ProfScope prof(c, s, 2);
-  return launch_combine(c->dim, c->g, a, s);
+  {
+    ProfScope prof(c, s, 2);
+    e = launch_combine(c->dim, c->g, a, s);
+  }
+  if (e != cudaSuccess || stage == 0) return e;
+  RepairArgs r;
+  r.mark = c->mark;
+  r.Fx = c->Fx;
+  r.Fy = c->Fy;
+  r.Wn = Wn;
+  r.Ws = Ws;
+  r.out = out;
+  r.sx_out = sxo;
+  r.sy_out = syo;
+  r.st = c->st;
+  r.inv_dx = c->inv_dx;
+  r.inv_dy = c->inv_dy;
+  r.dt_fixed = dt_fixed;
+  r.stage = stage;
+  for (int pass = 1; pass <= kRepairPasses && e == cudaSuccess; ++pass) {
+    r.pass = pass;
+    ProfScope prof(c, s, 4);
+    e = launch_repair(c->dim, c->g, r, s);
+  }
+  if (e == cudaSuccess) {
+    ProfScope prof(c, s, 4);
+    e = launch_freeze(c->dim, c->g, r, s);
+  }
+  return e;
 }
 
 static ase_df_status check_ptrs(ase_df_ctx* c, const void* W, const void* sx, const void* sy) {
@@ -310,13 +348,13 @@ static ase_df_status step_launches(ase_df_ctx* c, double* W, double* sx, double*
   const double dtf = (dt > 0.0) ? dt : 0.0;
   // stage 1
   if ((e = face_fluxes(c, W, sx, sy, c->sxa, c->sya, s)) != cudaSuccess) return cuda_fail(c, e, "stage 1 sweep");
-  if ((e = combine(c, 1, W, W, c->W1, dtf, s)) != cudaSuccess) return cuda_fail(c, e, "stage 1 combine");
+  if ((e = combine(c, 1, W, W, c->W1, dtf, s, c->sxa, c->sya)) != cudaSuccess) return cuda_fail(c, e, "stage 1 combine");
   // stage 2
   if ((e = face_fluxes(c, c->W1, c->sxa, c->sya, c->sxb, c->syb, s)) != cudaSuccess) return cuda_fail(c, e, "stage 2 sweep");
-  if ((e = combine(c, 2, W, c->W1, c->W2, dtf, s)) != cudaSuccess) return cuda_fail(c, e, "stage 2 combine");
+  if ((e = combine(c, 2, W, c->W1, c->W2, dtf, s, c->sxb, c->syb)) != cudaSuccess) return cuda_fail(c, e, "stage 2 combine");
   // stage 3: sigma_out lands in the caller's sx / sy, W^{n+1} in W
   if ((e = face_fluxes(c, c->W2, c->sxb, c->syb, sx, sy, s)) != cudaSuccess) return cuda_fail(c, e, "stage 3 sweep");
-  if ((e = combine(c, 3, W, c->W2, W, dtf, s)) != cudaSuccess) return cuda_fail(c, e, "stage 3 combine");
+  if ((e = combine(c, 3, W, c->W2, W, dtf, s, sx, sy)) != cudaSuccess) return cuda_fail(c, e, "stage 3 combine");
   return ASE_DF_OK;
 }
 
@@ -443,7 +481,7 @@ ase_df_status ase_df_profile_enable(ase_df_ctx* c, int32_t enable) {
 
 ase_df_status ase_df_profile_read(ase_df_ctx* c, double* ms, int64_t* n) {
   if (!c || !ms || !n) return c ? fail(c, ASE_DF_E_INVAL, "NULL pointer") : ASE_DF_E_INVAL;
-  for (int k = 0; k < 4; ++k) { ms[k] = 0.0; n[k] = 0; }
+  for (int k = 0; k < 5; ++k) { ms[k] = 0.0; n[k] = 0; }
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(c, e, "profile_read sync");
   for (size_t i = 0; i < c->prof_kind->size(); ++i) {
@@ -454,6 +492,24 @@ ase_df_status ase_df_profile_read(ase_df_ctx* c, double* ms, int64_t* n) {
     ms[k] += t;
     n[k] += 1;
   }
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_get_repair_stats(ase_df_ctx* c, uint32_t* last_stage, uint64_t* total,
+                                      uint64_t* frozen) {
+  if (!c) return ASE_DF_E_INVAL;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_repair_stats sync");
+  DevState h;
+  e = cudaMemcpy(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_repair_stats copy");
+  if (last_stage)
+    for (int k = 0; k <= kRepairPasses; ++k) {
+      last_stage[k] = h.cnt[k];
+      last_stage[kRepairPasses + 1 + k] = h.rbad[k];
+    }
+  if (total) *total = h.repaired_total;
+  if (frozen) *frozen = h.frozen_total;
   return ASE_DF_OK;
 }
 

@@ -28,9 +28,19 @@ struct Tables {
   // cq[k][q][j]: coefficient of xi^(q+1) of that quadratic (for the smoothness indicator).
   double cq[3][2][3];
   double gw[4];   // Gauss weights on [0, 1]
+  double hgw[4];  // gw / 2 (the 1/2 of the Lax-Friedrichs flux folded in)
+  // symmetric Gauss-point pairs of the order-r linear branch: for the point pair
+  // (eta_g, -1 - eta_g), g < G/2, value = E +- O with E = se[g][0] W_0 + sum_t se[g][t] (W_t + W_-t)
+  // and O = sum_t so[g][t] (W_t - W_-t), t = 1..k; the middle point of odd G uses se only.
+  double se[2][5];
+  double so[2][5];
   double d5, d3[3];  // linear weights of WENOZ-AO(5,3) (Sec. 3.2, d_Hi = d_Lo = 0.85)
   double eps;        // 1e-6 (Sec. 3.2)
 };
+
+// Positivity repair of a stage update (the paper's transition to first order for
+// positivity): at most this many passes per RK stage.
+constexpr int kRepairPasses = 8;
 
 // Device-resident solver status.
 struct DevState {
@@ -40,6 +50,13 @@ struct DevState {
   double last_dt;
   unsigned int flags;
   unsigned int pad;
+  // cnt[0]: cells the stage update left non-physical; cnt[p]: cells newly non-physical
+  // after repair pass p.  Cleared by the x-face sweep of every stage.
+  unsigned int cnt[kRepairPasses + 1];
+  // rbad[p]: cells still non-physical after repair pass p (marked before or not).
+  unsigned int rbad[kRepairPasses + 1];
+  unsigned long long repaired_total;  // cells marked by the repair since the last reset
+  unsigned long long frozen_total;    // cells left without a flux update (last resort)
 };
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2 };
@@ -64,6 +81,7 @@ struct SweepArgs {
 };
 
 struct CombineArgs {
+  unsigned char* mark;  // per cell: 0, or the pass (1..) in which it was found non-physical
   const double* Fx;   // [C][ny][nx+1]
   const double* Fy;   // [C][ny+1][nx] (2D)
   const double* Wn;   // W^n
@@ -74,6 +92,22 @@ struct CombineArgs {
   double dt_fixed;    // > 0: this dt; otherwise the CFL dt (stage 1 computes it)
   double cfl, t_end, inflow_speed;
   int stage;          // 0: out = L; 1, 2, 3: SSP-RK3 stages
+};
+
+struct RepairArgs {
+  unsigned char* mark;
+  const double* Fx;
+  const double* Fy;
+  const double* Wn;
+  const double* Ws;
+  double* out;
+  double* sx_out;     // sigma of the stage (faces switched to first order get 1e30)
+  double* sy_out;
+  DevState* st;
+  double inv_dx, inv_dy;
+  double dt_fixed;
+  int stage;
+  int pass;           // 1..kRepairPasses
 };
 
 struct SpeedArgs {
@@ -91,6 +125,8 @@ cudaError_t launch_sweep_r9(int dim, int dir, const GridInfo& g, const SweepArgs
 
 cudaError_t launch_combine(int dim, const GridInfo& g, const CombineArgs& a, cudaStream_t s);
 cudaError_t launch_max_speed(int dim, const GridInfo& g, const SpeedArgs& a, cudaStream_t s);
+cudaError_t launch_repair(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s);
+cudaError_t launch_freeze(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s);
 cudaError_t launch_state_kernel(DevState* st, int op, double t, cudaStream_t s);
 
 // Tables of scheme order r (host, exact rational arithmetic).

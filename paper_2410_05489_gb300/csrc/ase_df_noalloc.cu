@@ -150,7 +150,10 @@ bool build_tables_fixed(int r, int ndim, Tables* T) {
   const int G = (ndim == 2) ? (r == 3 ? 1 : (r - 1) / 2) : 1;
   long double gt[4], gwt[4];
   gauss_legendre_fixed(G, gt, gwt);
-  for (int g = 0; g < G; ++g) T->gw[g] = (double)gwt[g];
+  for (int g = 0; g < G; ++g) {
+    T->gw[g] = (double)gwt[g];
+    T->hgw[g] = (double)(0.5L * gwt[g]);
+  }
   const int npts = 2 + G;
   Q inv[9][9];
   for (int b = 0; b < 4; ++b) {
@@ -160,6 +163,26 @@ bool build_tables_fixed(int r, int ndim, Tables* T) {
     if (!moment_inverse_fixed(offs, n, inv)) return false;
     for (int p = 0; p < npts; ++p)
       for (int i = 0; i < n; ++i) T->lin[b][p][4 - h + i] = point_weight(inv, n, i, p, gt);
+  }
+  {
+    const int h = (r - 1) / 2, n = 2 * h + 1;
+    int offs[9];
+    for (int i = 0; i < n; ++i) offs[i] = i - h;
+    if (!moment_inverse_fixed(offs, n, inv)) return false;
+    for (int g = 0; g < (G + 1) / 2 && g < 2; ++g) {
+      long double w[9];
+      const long double xi = gt[g] - 1.0L;
+      for (int i = 0; i < n; ++i) {
+        long double sacc = 0;
+        for (int q = n - 1; q >= 0; --q) sacc = sacc * xi + qld(inv[q][i]);
+        w[i] = sacc;
+      }
+      T->se[g][0] = (double)w[h];
+      for (int t = 1; t <= h; ++t) {
+        T->se[g][t] = (double)(0.5L * (w[h + t] + w[h - t]));
+        T->so[g][t] = (double)(0.5L * (w[h + t] - w[h - t]));
+      }
+    }
   }
   for (int k = 0; k < 3; ++k) {
     int offs[3] = {k - 2, k - 1, k};

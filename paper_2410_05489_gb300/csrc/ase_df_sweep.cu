@@ -18,6 +18,7 @@
 
 #include <cuda_runtime.h>
 
+#include "ase_df_device.cuh"
 #include "ase_df_internal.cuh"
 
 #ifndef ASE_DF_ORDER
@@ -26,39 +27,6 @@
 
 namespace asedf {
 namespace {
-
-constexpr double kSigmaBig = 1e30;  // sigma of a Gauss point that took first-order states
-
-__device__ __forceinline__ int wrap_or_clamp(int i, int n, int bc_lo, int bc_hi) {
-  if (i < 0) {
-    if (bc_lo == BC_PERIODIC) { int m = i % n; return m < 0 ? m + n : m; }
-    return 0;
-  }
-  if (i >= n) {
-    if (bc_hi == BC_PERIODIC) return i % n;
-    return n - 1;
-  }
-  return i;
-}
-
-// face index 0..n along a direction with n cells
-__device__ __forceinline__ int face_map(int f, int n, int bc_lo, int bc_hi) {
-  if (f >= 0 && f <= n) return f;
-  if (f < 0) {
-    if (bc_lo == BC_PERIODIC) { int m = f % n; return m < 0 ? m + n : m; }
-    return 0;
-  }
-  if (bc_hi == BC_PERIODIC) return f % n;
-  return n;
-}
-
-__device__ __forceinline__ double fetch_w(const GridInfo& g, const double* __restrict__ W, int c,
-                                          int i, int j) {
-  if (i < 0 && g.bc[0] == BC_INFLOW_BAND && j >= g.band_j0 && j <= g.band_j1) return g.inflow_cons[c];
-  const int ii = wrap_or_clamp(i, g.nx, g.bc[0], g.bc[1]);
-  const int jj = wrap_or_clamp(j, g.ny, g.bc[2], g.bc[3]);
-  return __ldg(W + ((size_t)c * g.ny + jj) * g.nx + ii);
-}
 
 // Branch of Algorithm 1 capped at order R, from the 2K face strengths of a cell's
 // stencil, s[m+K-1] = sigma_{m-1/2} (m = -K+1..K).  Stencil sums use one fixed
@@ -192,76 +160,45 @@ __device__ __forceinline__ void recon_eval(const double* v, int vs, const Branch
   if (R >= 5) weno_eval<NP>(v, vs, br, T, p0, out);
 }
 
-// Primitive variables of a face-frame state q = (rho, m_n, [m_t], E).
-template <int C>
-struct Prim {
-  double rho, un, ut, p, c, inv_c;
-  bool ok;
-};
-
-template <int C, int NI, int TI>
-__device__ __forceinline__ Prim<C> primitives(const double* q, double gamma) {
-  Prim<C> s;
-  s.rho = q[0];
-  const double inv_rho = 1.0 / q[0];
-  s.un = q[NI] * inv_rho;
-  s.ut = (C == 4) ? q[TI] * inv_rho : 0.0;
-  const double mke = (C == 4) ? fma(q[NI], s.un, q[TI] * s.ut) : q[NI] * s.un;
-  s.p = (gamma - 1.0) * fma(-0.5, mke, q[C - 1]);
-  s.ok = (q[0] > 0.0) && (s.p > 0.0) && isfinite(s.p) && isfinite(s.un) && isfinite(s.ut) &&
-         isfinite(q[0]);
-  const double c2 = gamma * s.p * inv_rho;
-  s.c = s.ok ? sqrt(c2) : 0.0;
-  s.inv_c = s.ok ? 1.0 / s.c : 0.0;
-  return s;
+// Gauss-point values (tangential reconstruction, Sec. 2.1) of the order-R linear
+// branch, using the reflection symmetry of the centred stencil: the points eta and
+// -1 - eta share E = w_0 W_0 + sum e_t (W_t + W_-t) and differ in the sign of
+// O = sum o_t (W_t - W_-t).  Used for G >= 3, where it saves FMAs over G dot products.
+template <int R, int G>
+__device__ __forceinline__ void lin_gauss_sym(const double* v, int vs, const Tables& T, double* out) {
+  constexpr int K = (R - 1) / 2;
+  double S[K + 1], D[K + 1];
+#pragma unroll
+  for (int t = 1; t <= K; ++t) {
+    S[t] = v[t * vs] + v[-t * vs];
+    D[t] = v[t * vs] - v[-t * vs];
+  }
+#pragma unroll
+  for (int g = 0; g < (G + 1) / 2; ++g) {
+    double E = T.se[g][0] * v[0];
+#pragma unroll
+    for (int t = 1; t <= K; ++t) E = fma(T.se[g][t], S[t], E);
+    if (2 * g + 1 == G) {
+      out[g] = E;  // middle point
+    } else {
+      double O = T.so[g][1] * D[1];
+#pragma unroll
+      for (int t = 2; t <= K; ++t) O = fma(T.so[g][t], D[t], O);
+      out[g] = E + O;
+      out[G - 1 - g] = E - O;
+    }
+  }
 }
 
-// Local Lax-Friedrichs flux (Sec. 2.3) and sigma (Sec. 3.1) of one Gauss point; qa / qb
-// are the left / right states in (x, y) momentum order; NI / TI select the normal and
-// tangential momentum.  Falls back to the cell averages ca / cb when a state is
-// non-physical (returns true then).
-template <int C, int NI, int TI>
-__device__ __forceinline__ bool lf_point(const double* qa, const double* qb, const double* ca,
-                                         const double* cb, double gamma, double* F, double& sigma) {
-  Prim<C> L = primitives<C, NI, TI>(qa, gamma);
-  Prim<C> Rr = primitives<C, NI, TI>(qb, gamma);
-  const bool fb = !(L.ok && Rr.ok);
-  const double* a = qa;
-  const double* b = qb;
-  if (fb) {
-    a = ca;
-    b = cb;
-    L = primitives<C, NI, TI>(a, gamma);
-    Rr = primitives<C, NI, TI>(b, gamma);
+// Tangential reconstruction at the G Gauss points (points 2..G+1 of the tables).
+template <int R, int G>
+__device__ __forceinline__ void tang_eval(const double* v, int vs, const Branch& br, const Tables& T,
+                                          double* out) {
+  if (G >= 3 && br.m == R) {
+    lin_gauss_sym<R, G>(v, vs, T, out);
+    return;
   }
-  const double lam = fmax(fabs(L.un) + L.c, fabs(Rr.un) + Rr.c);
-  double FL[4], FR[4];
-  FL[0] = a[NI];
-  FR[0] = b[NI];
-  FL[NI] = fma(a[NI], L.un, L.p);
-  FR[NI] = fma(b[NI], Rr.un, Rr.p);
-  if (C == 4) {
-    FL[TI] = a[NI] * L.ut;
-    FR[TI] = b[NI] * Rr.ut;
-  }
-  FL[C - 1] = L.un * (a[C - 1] + L.p);
-  FR[C - 1] = Rr.un * (b[C - 1] + Rr.p);
-#pragma unroll
-  for (int c = 0; c < C; ++c) F[c] = 0.5 * ((FL[c] + FR[c]) - lam * (b[c] - a[c]));
-  if (fb) {
-    sigma = kSigmaBig;
-  } else {
-    const double dp = fabs(L.p - Rr.p);
-    double s = dp / L.p + dp / Rr.p;
-    const double dmn = L.un * L.inv_c - Rr.un * Rr.inv_c;
-    s = fma(dmn, dmn, s);
-    if (C == 4) {
-      const double dmt = L.ut * L.inv_c - Rr.ut * Rr.inv_c;
-      s = fma(dmt, dmt, s);
-    }
-    sigma = s;
-  }
-  return fb;
+  recon_eval<R, G>(v, vs, br, T, 2, out);
 }
 
 template <int R, int DIM>
@@ -270,8 +207,8 @@ struct Tile {
   static constexpr int C = (DIM == 1) ? 3 : 4;
   static constexpr int KT = (DIM == 2) ? K : 0;
   static constexpr int G = (DIM == 2) ? (R == 3 ? 1 : K) : 1;
-  static constexpr int TN = (DIM == 2) ? 32 : 128;   // faces along the sweep
-  static constexpr int TT = (DIM == 2) ? 8 : 1;      // lines
+  static constexpr int TN = (DIM == 2) ? 16 : 128;   // faces along the sweep
+  static constexpr int TT = (DIM == 2) ? 32 : 1;     // lines
   static constexpr int NT = (DIM == 2) ? 256 : 128;  // threads
   static constexpr int NA = TN + 1 + 2 * K;          // staged cells along the sweep
   static constexpr int NB = TT + 2 * KT;             // staged lines
@@ -306,6 +243,10 @@ sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tab
   const int tid = threadIdx.x;
   const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
   const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+  if (DIR == 0 && blockIdx.x == 0 && blockIdx.y == 0 && tid <= kRepairPasses) {
+    args.st->cnt[tid] = 0u;
+    args.st->rbad[tid] = 0u;
+  }
 
   // ---- stage cell averages: cells a0-1-K .. a0+TN-1+K, lines b0-KT .. b0+TT+KT-1 ----
   for (int idx = tid; idx < C * NB * NA; idx += NT) {
@@ -375,7 +316,7 @@ sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tab
         for (int c = 0; c < C; ++c) {
           const double* v = Q + (c * NB + tb + K) * NQ + qa;
           double out[G];
-          recon_eval<R, G>(v, NQ, bt, T, 2, out);
+          tang_eval<R, G>(v, NQ, bt, T, out);
 #pragma unroll
           for (int q = 0; q < G; ++q) st[side][q][c] = out[q];
         }
@@ -400,7 +341,7 @@ sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tab
       double F[C], sg;
       anyfb |= lf_point<C, NI, TI>(st[0][q], st[1][q], ca, cb, g.gamma, F, sg);
 #pragma unroll
-      for (int c = 0; c < C; ++c) Fs[c] = fma((DIM == 2) ? T.gw[q] : 1.0, F[c], Fs[c]);
+      for (int c = 0; c < C; ++c) Fs[c] = fma((DIM == 2) ? T.hgw[q] : 0.5, F[c], Fs[c]);
       ssum += sg;
     }
     if (anyfb) atomicOr(&args.st->flags, 0x2u);

@@ -145,7 +145,10 @@ void build_tables(int r, int ndim, Tables* T) {
   const int G = (ndim == 2) ? (r == 3 ? 1 : (r - 1) / 2) : 1;
   long double gt[4], gwt[4];
   gauss_legendre(G, gt, gwt);
-  for (int g = 0; g < G; ++g) T->gw[g] = (double)gwt[g];
+  for (int g = 0; g < G; ++g) {
+    T->gw[g] = (double)gwt[g];
+    T->hgw[g] = (double)(0.5L * gwt[g]);
+  }
   const int npts = 2 + G;
 
   auto eval_all = [&](const std::vector<std::vector<Rat>>& inv, int p, double* w) {
@@ -164,6 +167,28 @@ void build_tables(int r, int ndim, Tables* T) {
       double w[9];
       eval_all(inv, p, w);
       for (int i = 0; i < 2 * h + 1; ++i) T->lin[b][p][4 - h + i] = w[i];
+    }
+  }
+  // symmetric / antisymmetric weights of the order-r linear branch at the Gauss points
+  // (the reflection about the cell centre maps eta to -1 - eta and W_t to W_-t)
+  {
+    const int h = (r - 1) / 2;
+    std::vector<int> offs;
+    for (int o = -h; o <= h; ++o) offs.push_back(o);
+    auto inv = moment_inverse(offs);
+    for (int g = 0; g < (G + 1) / 2 && g < 2; ++g) {
+      long double w[9];
+      const long double xi = gt[g] - 1.0L;
+      for (int i = 0; i < 2 * h + 1; ++i) {
+        long double sacc = 0;
+        for (int q = 2 * h; q >= 0; --q) sacc = sacc * xi + to_ld(inv[q][i]);
+        w[i] = sacc;
+      }
+      T->se[g][0] = (double)w[h];
+      for (int t = 1; t <= h; ++t) {
+        T->se[g][t] = (double)(0.5L * (w[h + t] + w[h - t]));
+        T->so[g][t] = (double)(0.5L * (w[h + t] - w[h - t]));
+      }
     }
   }
   // 3-cell sub-stencils S3_{-1}, S3_0, S3_1
