@@ -220,7 +220,7 @@ struct Tile {
 };
 
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(Tile<R, DIM>::NT)
+__global__ void __launch_bounds__(Tile<R, DIM>::NT, 2)
 sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tables T) {
   using TL = Tile<R, DIM>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
