@@ -331,10 +331,60 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "status_flags": flags,
     }
+    if not args.no_batched:
+        out["batched"] = batched_bench(A, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample(args.order)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def batched_bench(A, torch, args):
+    """The batched workload (512 problems, 1D N in [128, 16384] and 2D N^2 with N in
+    [64, 512], random Riemann data, orders 3/5/7/9): CUDA-graph replays of batch steps
+    with the autotuned schedule, against one ase_df_step call per problem per step."""
+    from paper_2410_05489_gb300 import batch as Bt
+
+    probs = P.batched_problems()
+    bt = Bt.Batch([p for p, _ in probs], [w for _, w in probs])
+    tune = Bt.autotune(bt, steps=1)
+    bt.run(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ksteps = max(2, args.steps // 4)
+    e0.record()
+    bt.run(ksteps)
+    e1.record()
+    e1.synchronize()
+    ms_b = e0.elapsed_time(e1) / ksteps
+    flags, _, _ = bt.status()
+    cells = bt.ncells
+    bt.close()
+    # one problem per launch: a context per problem, ase_df_step on each in turn
+    solvers = [A.Solver(p, w) for p, w in probs]
+    for s_ in solvers:
+        s_.step()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(ksteps):
+        for s_ in solvers:
+            s_.step()
+    e1.record()
+    e1.synchronize()
+    ms_1 = e0.elapsed_time(e1) / ksteps
+    for s_ in solvers:
+        s_.close()
+    return {
+        "workload": "512 problems (256 1D, N log-uniform 128..16384; 256 2D N^2, N log-uniform 64..512), "
+                    "random Riemann data, orders 3/5/7/9, outflow, CFL 0.5, seed 20241008",
+        "cells": cells, "steps": ksteps,
+        "value": round(cells * 3 / (ms_b * 1e-3) / 1e6, 3), "unit": UNIT,
+        "ms_per_step": round(ms_b, 4),
+        "one_problem_per_launch": {"value": round(cells * 3 / (ms_1 * 1e-3) / 1e6, 3), "ms_per_step": round(ms_1, 4)},
+        "speedup": round(ms_1 / ms_b, 3),
+        "schedule": tune.get("schedule"),
+        "nonphysical_problems": int(((flags & 1) != 0).sum()),
+    }
 
 
 # ----------------------------------------------------------------------------------
@@ -391,6 +441,7 @@ def main():
     ap.add_argument("--order", type=int, default=ORDER)
     ap.add_argument("--ref-n", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -179,6 +179,59 @@ ase_df_status ase_df_residual_noalloc(const ase_df_params* p, const double* W, c
                                       const double* sy_in, double* L, double* sx_out, double* sy_out,
                                       void* stream);
 
+/* ---------------------------------------------------------------------------------
+ * Batched solves (no counterpart in the paper, whose solver advances one problem): n
+ * independent problems, 1D and 2D, of mixed order, advanced together, each with its own
+ * CFL dt, time and status.  Every sweep direction of every RK stage is ONE persistent
+ * launch over the tiles of all problems (work list ordered by cost, atomic work counter);
+ * the combination, positivity repair and CFL reduction run over per-problem cell chunks.
+ *
+ * State: the caller owns three packed device arrays -- W (each problem's [C][ny][nx]
+ * block back to back), sx (each [ny][nx+1]) and sy (each 2D problem's [ny+1][nx]; 1D
+ * problems take no room; may be NULL if all problems are 1D) -- laid out as
+ * ase_df_batch_layout reports.  The batch owns its scratch.  Limits: each problem as in
+ * ase_df_init, fewer than 2^31 cells in total.
+ * --------------------------------------------------------------------------------- */
+typedef struct ase_df_batch ase_df_batch;
+
+/* Validates the n problems p[0..n-1] and allocates the batch (descriptors, work lists,
+ * scratch) on the current device.  p[i].t_end bounds each problem's time. */
+ase_df_status ase_df_batch_init(const ase_df_params* p, int32_t n, ase_df_batch** out);
+void ase_df_batch_destroy(ase_df_batch* b);
+
+/* Offsets (in doubles) of problem i in the packed arrays: W block [w_off[i], w_off[i+1]),
+ * sx block [sx_off[i], sx_off[i+1]), sy block [sy_off[i], sy_off[i+1]); n+1 entries each
+ * (any pointer may be NULL). */
+ase_df_status ase_df_batch_layout(const ase_df_batch* b, int64_t* w_off, int64_t* sx_off, int64_t* sy_off);
+
+/* sigma^0 of every problem (as ase_df_prime_sigma); also resets every problem's time,
+ * dt and status. */
+ase_df_status ase_df_batch_prime_sigma(ase_df_batch* b, const double* W, double* sx, double* sy,
+                                       void* stream);
+
+/* One SSP-RK3 CFL step of every problem, in place (as ase_df_step with dt <= 0, including
+ * the positivity repair). */
+ase_df_status ase_df_batch_step(ase_df_batch* b, double* W, double* sx, double* sy, void* stream);
+
+/* nsteps batch steps as replays of one CUDA graph (captured on the first call for these
+ * pointers and the current schedule). */
+ase_df_status ase_df_batch_run(ase_df_batch* b, double* W, double* sx, double* sy, int32_t nsteps,
+                               void* stream);
+
+/* Synchronises; per problem: status flags (ASE_DF_FLAG_*), time, last dt (arrays of n;
+ * any may be NULL).  Returns ASE_DF_E_NONPHYSICAL if any problem reports that flag. */
+ase_df_status ase_df_batch_get_status(ase_df_batch* b, uint32_t* flags, double* t, double* last_dt);
+
+/* Schedule: persistent sweep CTAs per SM (1 or 2), work items ordered by cost (1) or by
+ * problem (0), cells per chunk of the per-cell kernels (256 .. 2^24).  Chosen by the
+ * autotuner of the Python package; results do not depend on it. */
+ase_df_status ase_df_batch_set_schedule(ase_df_batch* b, int32_t ctas_per_sm, int32_t order_by_cost,
+                                        int32_t chunk_cells);
+
+/* Message of the last error on this batch (or of the last failed ase_df_batch_init when
+ * b is NULL). */
+const char* ase_df_batch_last_error(const ase_df_batch* b);
+
 /* FP64 throughput microbenchmark used as the roofline denominator: independent FMA
  * chains on every SM; writes the achieved FP64 FMA instructions per second into
  * *fma_per_s (flops = 2x).  Synchronises the device. */

@@ -25,7 +25,7 @@ def _units():
     for r in (3, 5, 7, 9):
         units.append(("ase_df_sweep.cu", "sweep_r%d.o" % r, ["-DASE_DF_ORDER=%d" % r]))
     for src in ("ase_df_combine.cu", "ase_df_api.cu", "ase_df_fp64_peak.cu", "ase_df_tables.cpp",
-                "ase_df_noalloc.cu"):
+                "ase_df_noalloc.cu", "ase_df_batch.cu"):
         if os.path.exists(os.path.join(CSRC, src)):
             units.append((src, os.path.splitext(src)[0] + ".o", []))
     return units

@@ -21,251 +21,33 @@
 
 #include <cuda_runtime.h>
 
-#include "ase_df_device.cuh"
-#include "ase_df_internal.cuh"
+#include "ase_df_combine_body.cuh"
 
 namespace asedf {
 namespace {
 
-__device__ __forceinline__ double load_dt(const CombineArgs& a) {
-  return a.dt_fixed > 0.0 ? a.dt_fixed : a.st->dt;
-}
-
-__device__ __forceinline__ double rk_stage(int stage, double dt, double wn, double ws, double L) {
-  if (stage == 1) return fma(dt, L, ws);
-  if (stage == 2) return fma(0.25 * dt, L, fma(0.75, wn, 0.25 * ws));
-  return fma((2.0 / 3.0) * dt, L, fma(1.0 / 3.0, wn, (2.0 / 3.0) * ws));
-}
-
-// rho > 0 and p > 0 (tested on p rho = (gamma-1)(E rho - |m|^2/2)), all finite.
-template <int C>
-__device__ __forceinline__ bool physical_state(const double* q, double gamma) {
-  double mm = q[1] * q[1];
-  if (C == 4) mm = fma(q[2], q[2], mm);
-  const double pr = (gamma - 1.0) * fma(q[C - 1], q[0], -0.5 * mm);
-  return (q[0] > 0.0) && (pr > 0.0) && isfinite(pr);
-}
-
 template <int DIM>
 __global__ void __launch_bounds__(256) combine_kernel(const GridInfo g, const CombineArgs a) {
-  constexpr int C = (DIM == 1) ? 3 : 4;
-  const int nx = g.nx, ny = g.ny;
-  const size_t ncell = (size_t)nx * ny;
-  double dt = 0.0;
-  if (a.stage == 1) {
-    if (a.dt_fixed > 0.0) {
-      dt = a.dt_fixed;
-    } else {
-      const double smax = fmax(__longlong_as_double((long long)a.st->max_speed_bits), a.inflow_speed);
-      dt = a.cfl / smax;
-      if (a.t_end > 0.0) dt = fmax(0.0, fmin(dt, a.t_end - a.st->t));
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      a.st->dt = dt;
-      if (!(dt > 0.0) || !isfinite(dt)) {
-        if (!(a.t_end > 0.0 && a.st->t >= a.t_end)) atomicOr(&a.st->flags, 0x4u);
-      }
-    }
-  } else if (a.stage > 1) {
-    dt = load_dt(a);
-  }
-  bool bad = false;
-  unsigned int nmarked = 0;
-  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(n % nx), j = (int)(n / nx);
-    double q[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const size_t fx = ((size_t)c * ny + j) * (nx + 1) + i;
-      double L = -(a.Fx[fx + 1] - a.Fx[fx]) * a.inv_dx;
-      if (DIM == 2) {
-        const size_t fy = ((size_t)c * (ny + 1) + j) * nx + i;
-        L = fma(-(a.Fy[fy + nx] - a.Fy[fy]), a.inv_dy, L);
-      }
-      const size_t w = (size_t)c * ncell + n;
-      q[c] = (a.stage == 0) ? L : rk_stage(a.stage, dt, a.Wn[w], a.Ws[w], L);
-      a.out[w] = q[c];
-      if (!isfinite(q[c])) bad = true;
-    }
-    if (a.stage > 0) {
-      const bool ok = physical_state<C>(q, g.gamma);
-      a.mark[n] = ok ? 0 : 1;
-      nmarked += ok ? 0u : 1u;
-    }
-  }
-  if (a.stage == 0 && bad) atomicOr(&a.st->flags, 0x1u);
-  if (nmarked) {
-    atomicAdd(&a.st->cnt[0], nmarked);
-    atomicAdd(&a.st->repaired_total, (unsigned long long)nmarked);
-  }
-  if (a.stage == 3 && blockIdx.x == 0 && threadIdx.x == 0) {
-    a.st->t += dt;
-    a.st->last_dt = dt;
-    a.st->max_speed_bits = 0ull;  // ready for the next CFL reduction
-  }
+  const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  combine_range<DIM>(g, a, first, (size_t)g.nx * g.ny, stride, first == 0);
 }
 
-__device__ __forceinline__ int across(int k, int n, int bc_lo, int bc_hi) {
-  if (k >= 0 && k < n) return k;
-  return ((k < 0 ? bc_lo : bc_hi) == BC_PERIODIC) ? (k < 0 ? k + n : k - n) : -1;
-}
-
-// One repair pass: cells that are marked (passes 1..pass) or next to a marked cell are
-// updated again with the first-order flux on every face next to a marked cell.
 template <int DIM>
 __global__ void __launch_bounds__(256) repair_kernel(const GridInfo g, const RepairArgs a) {
-  constexpr int C = (DIM == 1) ? 3 : 4;
-  if (a.st->cnt[a.pass - 1] == 0u) return;  // no new marks in the previous pass
-  const int nx = g.nx, ny = g.ny;
-  const size_t ncell = (size_t)nx * ny;
-  const double dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.st->dt;
-  const unsigned int pass = (unsigned int)a.pass;
-  auto marked = [&](int i, int j) {
-    const unsigned int m = a.mark[(size_t)j * nx + i];
-    return m >= 1u && m <= pass;
-  };
-  unsigned int nnew = 0, nbad = 0;
-  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(n % nx), j = (int)(n / nx);
-    const bool self = marked(i, j);
-    const int il = across(i - 1, nx, g.bc[0], g.bc[1]), ir = across(i + 1, nx, g.bc[0], g.bc[1]);
-    const bool fL = self || (il >= 0 && marked(il, j));
-    const bool fR = self || (ir >= 0 && marked(ir, j));
-    bool fD = false, fU = false;
-    if (DIM == 2) {
-      const int jd = across(j - 1, ny, g.bc[2], g.bc[3]), ju = across(j + 1, ny, g.bc[2], g.bc[3]);
-      fD = self || (jd >= 0 && marked(i, jd));
-      fU = self || (ju >= 0 && marked(i, ju));
-    }
-    if (!(fL || fR || fD || fU)) continue;
-    double F[2][2][C];  // [dir][lower / upper face][component]
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int f = i + side;
-      if (side == 0 ? fL : fR) {
-        double cl[C], cr[C], F2[C], sg;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          cl[c] = fetch_w(g, a.Ws, c, f - 1, j);
-          cr[c] = fetch_w(g, a.Ws, c, f, j);
-        }
-        lf_point<C, 1, 2>(cl, cr, cl, cr, g.gamma, F2, sg);
-#pragma unroll
-        for (int c = 0; c < C; ++c) F[0][side][c] = 0.5 * F2[c];
-        a.sx_out[(size_t)j * (nx + 1) + f] = kSigmaBig;
-      } else {
-#pragma unroll
-        for (int c = 0; c < C; ++c) F[0][side][c] = a.Fx[((size_t)c * ny + j) * (nx + 1) + f];
-      }
-      if (DIM == 2) {
-        const int fy = j + side;
-        if (side == 0 ? fD : fU) {
-          double cl[C], cr[C], F2[C], sg;
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            cl[c] = fetch_w(g, a.Ws, c, i, fy - 1);
-            cr[c] = fetch_w(g, a.Ws, c, i, fy);
-          }
-          lf_point<C, 2, 1>(cl, cr, cl, cr, g.gamma, F2, sg);
-#pragma unroll
-          for (int c = 0; c < C; ++c) F[1][side][c] = 0.5 * F2[c];
-          a.sy_out[(size_t)fy * nx + i] = kSigmaBig;
-        } else {
-#pragma unroll
-          for (int c = 0; c < C; ++c) F[1][side][c] = a.Fy[((size_t)c * (ny + 1) + fy) * nx + i];
-        }
-      }
-    }
-    double q[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      double L = -(F[0][1][c] - F[0][0][c]) * a.inv_dx;
-      if (DIM == 2) L = fma(-(F[1][1][c] - F[1][0][c]), a.inv_dy, L);
-      const size_t w = (size_t)c * ncell + n;
-      q[c] = rk_stage(a.stage, dt, a.Wn[w], a.Ws[w], L);
-      a.out[w] = q[c];
-    }
-    if (!physical_state<C>(q, g.gamma)) {
-      ++nbad;
-      if (a.mark[n] == 0) {
-        a.mark[n] = (unsigned char)(pass + 1);
-        ++nnew;
-      }
-    }
-  }
-  if (nnew) {
-    atomicAdd(&a.st->cnt[pass], nnew);
-    atomicAdd(&a.st->repaired_total, (unsigned long long)nnew);
-  }
-  if (nbad) atomicAdd(&a.st->rbad[pass], nbad);
+  const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  repair_range<DIM>(g, a, first, (size_t)g.nx * g.ny, stride);
 }
 
-// Last resort after the repair passes (see the file comment).
 template <int DIM>
 __global__ void __launch_bounds__(256) freeze_kernel(const GridInfo g, const RepairArgs a) {
-  constexpr int C = (DIM == 1) ? 3 : 4;
-  if (a.st->cnt[0] == 0u) return;  // the stage update was physical everywhere
-  const size_t ncell = (size_t)g.nx * g.ny;
-  const double dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.st->dt;
-  unsigned int nfrozen = 0;
-  bool still_bad = false;
-  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += (size_t)gridDim.x * blockDim.x) {
-    double q[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) q[c] = a.out[(size_t)c * ncell + n];
-    if (physical_state<C>(q, g.gamma)) continue;
-#pragma unroll
-    for (int c = 0; c < C; ++c) q[c] = rk_stage(a.stage, dt, a.Wn[(size_t)c * ncell + n], a.Ws[(size_t)c * ncell + n], 0.0);
-    if (!physical_state<C>(q, g.gamma) && q[0] > 0.0 && isfinite(q[C - 1])) {
-      // a pressure at the rounding level of E (near vacuum): floor it at 1e-13 of the
-      // kinetic energy density by adjusting E
-      double mm = q[1] * q[1];
-      if (C == 4) mm = fma(q[2], q[2], mm);
-      const double ke = 0.5 * mm / q[0];
-      q[C - 1] = ke + 1e-13 * fmax(ke, fabs(q[C - 1])) / (g.gamma - 1.0);
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c) a.out[(size_t)c * ncell + n] = q[c];
-    ++nfrozen;
-    if (!physical_state<C>(q, g.gamma)) still_bad = true;
-  }
-  if (nfrozen) {
-    atomicAdd(&a.st->frozen_total, (unsigned long long)nfrozen);
-    atomicOr(&a.st->flags, 0x8u);
-  }
-  if (still_bad) atomicOr(&a.st->flags, 0x1u);
+  const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  freeze_range<DIM>(g, a, first, (size_t)g.nx * g.ny, stride);
 }
 
-// max over cells of (|u|+c)/dx [+ (|v|+c)/dy]; non-physical cells raise the flag.
 template <int DIM>
 __global__ void __launch_bounds__(256) max_speed_kernel(const GridInfo g, const SpeedArgs a) {
-  constexpr int C = (DIM == 1) ? 3 : 4;
-  const size_t ncell = (size_t)g.nx * g.ny;
-  double smax = 0.0;
-  bool bad = false;
-  for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < ncell; n += (size_t)gridDim.x * blockDim.x) {
-    double q[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) q[c] = a.W[(size_t)c * ncell + n];
-    if (!physical_state<C>(q, g.gamma)) {
-      bad = true;
-      continue;
-    }
-    const double rho = q[0];
-    const double inv_rho = 1.0 / rho;
-    const double u = q[1] * inv_rho;
-    const double v = (C == 4) ? q[2] * inv_rho : 0.0;
-    const double p = (g.gamma - 1.0) * (q[C - 1] - 0.5 * rho * (u * u + v * v));
-    const double c = sqrt(fmax(g.gamma * p * inv_rho, 0.0));
-    double s = (fabs(u) + c) * a.inv_dx;
-    if (C == 4) s = fma(fabs(v) + c, a.inv_dy, s);
-    smax = fmax(smax, s);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-  if ((threadIdx.x & 31) == 0 && smax > 0.0)
-    atomicMax(&a.st->max_speed_bits, (unsigned long long)__double_as_longlong(smax));
-  if (bad) atomicOr(&a.st->flags, 0x1u);
+  const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  max_speed_range<DIM>(g, a, first, (size_t)g.nx * g.ny, stride);
 }
 
 __global__ void state_kernel(DevState* st, int op, double t) {

@@ -1,0 +1,340 @@
+// Device body of the fused ASE-DF face sweep (shared by the one-problem kernel and the
+// batched persistent kernel).  See ase_df_sweep.cu for the algorithm.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ase_df_device.cuh"
+#include "ase_df_internal.cuh"
+
+namespace asedf {
+namespace {
+
+
+// Branch of Algorithm 1 capped at order R, from the 2K face strengths of a cell's
+// stencil, s[m+K-1] = sigma_{m-1/2} (m = -K+1..K).  Stencil sums use one fixed
+// association, symmetric under mirroring: A3 = left + right,
+// A5 = (s_-3/2 + s_-1/2) + (s_1/2 + s_3/2), A7 = A5 + (s_-5/2 + s_5/2),
+// A9 = A7 + (s_-7/2 + s_7/2).  Smooth iff A < sigma_thres; else alpha = sigma_thres / A.
+struct Branch {
+  int m;          // R..5 odd: linear m-th order; 0: WENOZ-AO(5,3)+DF; 3: linear 3; -3: DF-damped 3
+  double a3[3];   // alpha of S3_{-1}, S3_0, S3_1 (fallback)
+  double a5;      // alpha of S5 (fallback) / of S3_0 (DF-damped order 3)
+};
+
+template <int R>
+__device__ __forceinline__ Branch select_branch(const double* s, double thres) {
+  constexpr int K = (R - 1) / 2;
+  Branch b;
+  b.m = R;
+  b.a3[0] = b.a3[1] = b.a3[2] = 1.0;
+  b.a5 = 1.0;
+  const double sm12 = s[K - 1], sp12 = s[K];  // sigma_{-1/2}, sigma_{1/2}
+  if (R == 3) {
+    const double A = sm12 + sp12;
+    if (A < thres) { b.m = 3; } else { b.m = -3; b.a5 = thres / A; }
+    return b;
+  }
+  const double sm32 = s[K - 2], sp32 = s[K + 1];
+  const double A5 = (sm32 + sm12) + (sp12 + sp32);
+  if (!(A5 < thres)) {
+    b.m = 0;
+    const double A3m = sm32 + sm12, A30 = sm12 + sp12, A3p = sp12 + sp32;
+    b.a3[0] = A3m < thres ? 1.0 : thres / A3m;
+    b.a3[1] = A30 < thres ? 1.0 : thres / A30;
+    b.a3[2] = A3p < thres ? 1.0 : thres / A3p;
+    b.a5 = thres / A5;
+    return b;
+  }
+  b.m = 5;
+  if (R >= 7) {
+    const double A7 = A5 + (s[K - 3] + s[K + 2]);
+    if (A7 < thres) {
+      b.m = 7;
+      if (R >= 9) {
+        const double A9 = A7 + (s[K - 4] + s[K + 3]);
+        if (A9 < thres) b.m = 9;
+      }
+    }
+  }
+  return b;
+}
+
+// Linear M-cell value at point p: v points at W_0, with W_t at v[t*vs].
+template <int M>
+__device__ __forceinline__ double lin_eval(const double* v, int vs, const double* w) {
+  constexpr int H = (M - 1) / 2;
+  double acc = w[4 - H] * v[-H * vs];
+#pragma unroll
+  for (int t = -H + 1; t <= H; ++t) acc = fma(w[4 + t], v[t * vs], acc);
+  return acc;
+}
+
+// WENOZ-AO(5,3) with DF damping (Sec. 3.2) of one component, at NP points p0..p0+NP-1.
+// v points at W_0 (stride vs).
+template <int NP>
+__device__ __forceinline__ void weno_eval(const double* v, int vs, const Branch& br,
+                                          const Tables& T, int p0, double* out) {
+  double beta[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double* vk = v + (k - 2) * vs;  // sub-stencil S3_{k-1}: offsets k-2 .. k
+    const double c1 = T.cq[k][0][0] * vk[0] + T.cq[k][0][1] * vk[vs] + T.cq[k][0][2] * vk[2 * vs];
+    const double c2 = T.cq[k][1][0] * vk[0] + T.cq[k][1][1] * vk[vs] + T.cq[k][1][2] * vk[2 * vs];
+    // int_{-1}^{0} (p')^2 + (p'')^2 for p = c0 + c1 xi + c2 xi^2
+    beta[k] = c1 * (c1 - 2.0 * c2) + (16.0 / 3.0) * c2 * c2;
+  }
+  const double b5 = (beta[0] + 4.0 * beta[1] + beta[2]) * (1.0 / 6.0) + fabs(beta[0] - beta[2]);
+  const double tau = (fabs(b5 - beta[0]) + fabs(b5 - beta[1]) + fabs(b5 - beta[2])) * (1.0 / 3.0);
+  const double tau2 = tau * tau;
+  const double e5 = b5 + T.eps;
+  const double w5 = T.d5 * (1.0 + tau2 / (e5 * e5));
+  double w3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double e = beta[k] + T.eps;
+    w3[k] = T.d3[k] * (1.0 + tau2 / (e * e));
+  }
+  const double inv = 1.0 / (w5 + w3[0] + w3[1] + w3[2]);
+  const double g5 = (w5 * inv) / T.d5;
+  double g3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g3[k] = w3[k] * inv - g5 * T.d3[k];
+  const double W0 = v[0];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int p = p0 + q;
+    const double P5 = fma(br.a5, lin_eval<5>(v, vs, T.lin[1][p]) - W0, W0);
+    double P = g5 * P5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double* vk = v + (k - 2) * vs;
+      const double u = T.sub[k][p][0] * vk[0] + T.sub[k][p][1] * vk[vs] + T.sub[k][p][2] * vk[2 * vs];
+      P = fma(g3[k], fma(br.a3[k], u - W0, W0), P);
+    }
+    out[q] = P;
+  }
+}
+
+// Value of the chosen polynomial of one component at NP points p0.. (Algorithm 1).
+template <int R, int NP>
+__device__ __forceinline__ void recon_eval(const double* v, int vs, const Branch& br,
+                                           const Tables& T, int p0, double* out) {
+  if (br.m == R) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) out[q] = lin_eval<R>(v, vs, T.lin[(R - 3) / 2][p0 + q]);
+    return;
+  }
+  if (R == 3) {  // DF-damped 3rd order
+#pragma unroll
+    for (int q = 0; q < NP; ++q) out[q] = fma(br.a5, lin_eval<3>(v, vs, T.lin[0][p0 + q]) - v[0], v[0]);
+    return;
+  }
+  if (R >= 9 && br.m == 7) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) out[q] = lin_eval<(R >= 7 ? 7 : 3)>(v, vs, T.lin[2][p0 + q]);
+    return;
+  }
+  if (R >= 7 && br.m == 5) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) out[q] = lin_eval<5>(v, vs, T.lin[1][p0 + q]);
+    return;
+  }
+  if (R >= 5) weno_eval<NP>(v, vs, br, T, p0, out);
+}
+
+// Gauss-point values (tangential reconstruction, Sec. 2.1) of the order-R linear
+// branch, using the reflection symmetry of the centred stencil: the points eta and
+// -1 - eta share E = w_0 W_0 + sum e_t (W_t + W_-t) and differ in the sign of
+// O = sum o_t (W_t - W_-t).  Used for G >= 3, where it saves FMAs over G dot products.
+template <int R, int G>
+__device__ __forceinline__ void lin_gauss_sym(const double* v, int vs, const Tables& T, double* out) {
+  constexpr int K = (R - 1) / 2;
+  double S[K + 1], D[K + 1];
+#pragma unroll
+  for (int t = 1; t <= K; ++t) {
+    S[t] = v[t * vs] + v[-t * vs];
+    D[t] = v[t * vs] - v[-t * vs];
+  }
+#pragma unroll
+  for (int g = 0; g < (G + 1) / 2; ++g) {
+    double E = T.se[g][0] * v[0];
+#pragma unroll
+    for (int t = 1; t <= K; ++t) E = fma(T.se[g][t], S[t], E);
+    if (2 * g + 1 == G) {
+      out[g] = E;  // middle point
+    } else {
+      double O = T.so[g][1] * D[1];
+#pragma unroll
+      for (int t = 2; t <= K; ++t) O = fma(T.so[g][t], D[t], O);
+      out[g] = E + O;
+      out[G - 1 - g] = E - O;
+    }
+  }
+}
+
+// Tangential reconstruction at the G Gauss points (points 2..G+1 of the tables).
+template <int R, int G>
+__device__ __forceinline__ void tang_eval(const double* v, int vs, const Branch& br, const Tables& T,
+                                          double* out) {
+  if (G >= 3 && br.m == R) {
+    lin_gauss_sym<R, G>(v, vs, T, out);
+    return;
+  }
+  recon_eval<R, G>(v, vs, br, T, 2, out);
+}
+
+template <int R, int DIM>
+struct Tile {
+  static constexpr int K = (R - 1) / 2;
+  static constexpr int C = (DIM == 1) ? 3 : 4;
+  static constexpr int KT = (DIM == 2) ? K : 0;
+  static constexpr int G = (DIM == 2) ? (R == 3 ? 1 : K) : 1;
+  static constexpr int TN = (DIM == 2) ? 16 : 256;   // faces along the sweep
+  static constexpr int TT = (DIM == 2) ? 32 : 1;     // lines
+  static constexpr int NT = 256;                     // threads
+  static constexpr int NA = TN + 1 + 2 * K;          // staged cells along the sweep
+  static constexpr int NB = TT + 2 * KT;             // staged lines
+  static constexpr int NQ = TN + 1;                  // cells reconstructed along the sweep
+  static constexpr int NSN = TN + 2 * K;             // normal faces staged per line
+  static constexpr int NST = TT + 2 * K;             // tangential faces staged per column
+  static constexpr size_t smem_doubles =
+      (size_t)C * NB * NA + 2 * (size_t)C * NB * NQ + (size_t)NB * NSN + (DIM == 2 ? (size_t)NQ * NST : 0);
+};
+
+// One tile: faces a0 .. a0+TN-1 along the sweep on lines b0 .. b0+TT-1 (threadIdx.x in
+// [0, TN*TT/..) is the worker index); smem holds Tile<R, DIM>::smem_doubles doubles.
+template <int R, int DIM, int DIR>
+__device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& args, const Tables& T, int a0,
+                                           int b0, double* smem) {
+  using TL = Tile<R, DIM>;
+  constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
+  constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
+  constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
+  constexpr int NI = (DIR == 0) ? 1 : 2;  // normal momentum component
+  constexpr int TI = (DIR == 0) ? 2 : 1;  // tangential momentum component
+
+  double* sW = smem;                       // [C][NB][NA]
+  double* sQP = sW + C * NB * NA;          // [C][NB][NQ] value at xi = 0
+  double* sQM = sQP + C * NB * NQ;         // [C][NB][NQ] value at xi = -1
+  double* sSn = sQM + C * NB * NQ;         // [NB][NSN]
+  double* sSt = sSn + NB * NSN;            // [NQ][NST]
+
+  const int n = (DIR == 0) ? g.nx : g.ny;       // cells along the sweep
+  const int mlin = (DIR == 0) ? g.ny : g.nx;    // lines
+  const int tid = threadIdx.x;
+  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
+  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+
+  // ---- stage cell averages: cells a0-1-K .. a0+TN-1+K, lines b0-KT .. b0+TT+KT-1 ----
+  for (int idx = tid; idx < C * NB * NA; idx += NT) {
+    int c, bb, aa;
+    if (DIR == 0) { aa = idx % NA; bb = (idx / NA) % NB; c = idx / (NA * NB); }
+    else { bb = idx % NB; aa = (idx / NB) % NA; c = idx / (NA * NB); }
+    const int a = a0 - 1 - K + aa, b = b0 - KT + bb;
+    const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
+    sW[(c * NB + bb) * NA + aa] = fetch_w(g, args.W, c, i, j);
+  }
+  // ---- normal face strengths: faces a0-K .. a0+TN-1+K of every staged line ----
+  for (int idx = tid; idx < NB * NSN; idx += NT) {
+    int fa, bb;
+    if (DIR == 0) { fa = idx % NSN; bb = idx / NSN; }
+    else { bb = idx % NB; fa = idx / NB; }
+    const int f = face_map(a0 - K + fa, n, bcn_lo, bcn_hi);
+    const int b = wrap_or_clamp(b0 - KT + bb, mlin, bct_lo, bct_hi);
+    sSn[bb * NSN + fa] = (DIR == 0) ? __ldg(args.s_norm + (size_t)b * (g.nx + 1) + f)
+                                    : __ldg(args.s_norm + (size_t)f * g.nx + b);
+  }
+  // ---- tangential face strengths of the reconstructing cells' columns ----
+  if (DIM == 2) {
+    for (int idx = tid; idx < NQ * (NST - 1); idx += NT) {
+      int qa, fb;
+      if (DIR == 0) { qa = idx % NQ; fb = idx / NQ; }
+      else { fb = idx % (NST - 1); qa = idx / (NST - 1); }
+      const int a = wrap_or_clamp(a0 - 1 + qa, n, bcn_lo, bcn_hi);
+      const int f = face_map(b0 - K + 1 + fb, mlin, bct_lo, bct_hi);
+      sSt[qa * NST + fb] = (DIR == 0) ? __ldg(args.s_tan + (size_t)f * g.nx + a)
+                                      : __ldg(args.s_tan + (size_t)a * (g.nx + 1) + f);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 1: normal reconstruction of cells a0-1 .. a0+TN-1 on all staged lines ----
+  for (int it = tid; it < NQ * NB; it += NT) {
+    int qa, bb;
+    if (DIR == 0) { qa = it % NQ; bb = it / NQ; }
+    else { bb = it % NB; qa = it / NB; }
+    const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const double* v = sW + (c * NB + bb) * NA + qa + K;  // W_0 of this cell
+      double out[2];
+      recon_eval<R, 2>(v, 1, br, T, 0, out);
+      sQP[(c * NB + bb) * NQ + qa] = out[0];
+      sQM[(c * NB + bb) * NQ + qa] = out[1];
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: faces ----
+  for (int it = tid; it < TN * TT; it += NT) {
+    int fa, tb;
+    if (DIR == 0) { fa = it % TN; tb = it / TN; }
+    else { tb = it % TT; fa = it / TT; }
+    const int f = a0 + fa, b = b0 + tb;
+    if (f > n || b >= mlin) continue;
+    double st[2][G][C];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int qa = fa + side;  // left state: cell f-1 (plus face); right: cell f (minus face)
+      const double* Q = side == 0 ? sQP : sQM;
+      if (DIM == 2) {
+        const Branch bt = select_branch<R>(sSt + qa * NST + tb, g.thres);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const double* v = Q + (c * NB + tb + K) * NQ + qa;
+          double out[G];
+          tang_eval<R, G>(v, NQ, bt, T, out);
+#pragma unroll
+          for (int q = 0; q < G; ++q) st[side][q][c] = out[q];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) st[side][0][c] = Q[c * NQ + qa];
+      }
+    }
+    double ca[C], cb[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      ca[c] = sW[(c * NB + tb + KT) * NA + fa + K];
+      cb[c] = sW[(c * NB + tb + KT) * NA + fa + K + 1];
+    }
+    double Fs[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) Fs[c] = 0.0;
+    double ssum = 0.0;
+    bool anyfb = false;
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      double F[C], sg;
+      anyfb |= lf_point<C, NI, TI>(st[0][q], st[1][q], ca, cb, g.gamma, F, sg);
+#pragma unroll
+      for (int c = 0; c < C; ++c) Fs[c] = fma((DIM == 2) ? T.hgw[q] : 0.5, F[c], Fs[c]);
+      ssum += sg;
+    }
+    if (anyfb) atomicOr(&args.st->flags, 0x2u);
+    const double sface = (G == 1) ? ssum : ssum * (1.0 / G);
+    if (DIR == 0) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) args.F[((size_t)c * g.ny + b) * (g.nx + 1) + f] = Fs[c];
+      args.s_out[(size_t)b * (g.nx + 1) + f] = sface;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) args.F[((size_t)c * (g.ny + 1) + f) * g.nx + b] = Fs[c];
+      args.s_out[(size_t)f * g.nx + b] = sface;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace asedf

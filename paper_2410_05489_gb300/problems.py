@@ -294,3 +294,24 @@ def random_sigma(pb: Problem, seed: int, scale: float) -> Tuple[np.ndarray, np.n
 
 def zero_sigma(pb: Problem) -> Tuple[np.ndarray, np.ndarray]:
     return np.zeros(pb.sx_shape), np.zeros(pb.sy_shape)
+
+
+def batched_problems(seed: int = 20241008, n1: int = 256, n2: int = 256,
+                     n1_range=(128, 16384), n2_range=(64, 512)):
+    """The batched workload: n1 1D problems with N log-uniform in n1_range and n2 2D N x N
+    problems with N log-uniform in n2_range; random Riemann data (rho, p log-uniform
+    [0.1, 10], velocities uniform [-2, 2]; 1D: two states split at a random x in
+    [0.3, 0.7]; 2D: four quadrants split at (0.5, 0.5)); orders uniform over {3,5,7,9};
+    outflow boundaries; CFL 0.5.  Returns a list of (Problem, W)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for kind, count, (lo, hi) in ((1, n1, n1_range), (2, n2, n2_range)):
+        for _ in range(count):
+            n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+            order = int(rng.choice([3, 5, 7, 9]))
+            sub = int(rng.integers(0, 2 ** 31 - 1))
+            if kind == 1:
+                out.append(riemann_1d(n, order, sub))
+            else:
+                out.append(riemann_2d(n, order, sub))
+    return out
