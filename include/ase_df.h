@@ -204,8 +204,8 @@ void ase_df_batch_destroy(ase_df_batch* b);
  * (any pointer may be NULL). */
 ase_df_status ase_df_batch_layout(const ase_df_batch* b, int64_t* w_off, int64_t* sx_off, int64_t* sy_off);
 
-/* sigma^0 of every problem (as ase_df_prime_sigma); also resets every problem's time,
- * dt and status. */
+/* sigma^0 of every problem (as ase_df_prime_sigma), then every problem's time, dt and
+ * status are reset (as ase_df_reset with t = 0). */
 ase_df_status ase_df_batch_prime_sigma(ase_df_batch* b, const double* W, double* sx, double* sy,
                                        void* stream);
 

@@ -621,9 +621,13 @@ ase_df_status ase_df_batch_prime_sigma(ase_df_batch* b, const double* W, double*
   cudaStream_t s = (cudaStream_t)stream;
   b->last_stream = s;
   const int nthr = std::max(b->n, 8);
-  batch_reset_kernel<<<(nthr + 255) / 256, 256, 0, s>>>(b->d_counters, 8, b->d_state, b->n, 1);
+  batch_reset_kernel<<<(nthr + 255) / 256, 256, 0, s>>>(b->d_counters, 8, b->d_state, b->n, 0);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_sweeps(b, 0, s);
+  if (e == cudaSuccess) {  // then a clean status (time 0), as ase_df_reset after priming
+    batch_reset_kernel<<<(nthr + 255) / 256, 256, 0, s>>>(b->d_counters, 8, b->d_state, b->n, 1);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return bcuda(b, e, "batch prime");
   return ASE_DF_OK;
 }
