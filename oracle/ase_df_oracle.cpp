@@ -93,6 +93,49 @@ static inline bool operator<=(real a, real b) { return a.v <= b.v; }
 static inline bool operator>(real a, real b) { return a.v > b.v; }
 static inline double val(real a) { return a.v; }
 static inline real sqrt_(real a) { g_ops.sqrt++; return real(std::sqrt(a.v)); }
+#elif defined(ORACLE_TAPE)
+// Reverse mode: every operation on a non-constant value appends a node (its two parents
+// and the partial derivatives) to a tape; the backward sweep accumulates adjoints from
+// the last node to the first.  Branches (comparisons, |x|, max) follow the values, so
+// the derivative is the one of the branch taken.
+struct TapeNode { int64_t a, b; double da, db; };
+static std::vector<TapeNode> g_tape;
+struct real {
+  double v;
+  int64_t id;  // -1: constant
+  real() : v(0.0), id(-1) {}
+  real(double x) : v(x), id(-1) {}
+};
+static inline real tape_op(double v, int64_t a, double da, int64_t b, double db) {
+  real r(v);
+  if (a < 0 && b < 0) return r;
+  g_tape.push_back(TapeNode{a, b, da, db});
+  r.id = (int64_t)g_tape.size() - 1;
+  return r;
+}
+static inline real tape_input(double v) {
+  real r(v);
+  g_tape.push_back(TapeNode{-1, -1, 0.0, 0.0});
+  r.id = (int64_t)g_tape.size() - 1;
+  return r;
+}
+static inline real operator+(real a, real b) { return tape_op(a.v + b.v, a.id, 1.0, b.id, 1.0); }
+static inline real operator-(real a, real b) { return tape_op(a.v - b.v, a.id, 1.0, b.id, -1.0); }
+static inline real operator-(real a) { return tape_op(-a.v, a.id, -1.0, -1, 0.0); }
+static inline real operator*(real a, real b) { return tape_op(a.v * b.v, a.id, b.v, b.id, a.v); }
+static inline real operator/(real a, real b) {
+  const double q = a.v / b.v;
+  return tape_op(q, a.id, 1.0 / b.v, b.id, -q / b.v);
+}
+static inline real& operator+=(real& a, real b) { a = a + b; return a; }
+static inline bool operator<(real a, real b) { return a.v < b.v; }
+static inline bool operator<=(real a, real b) { return a.v <= b.v; }
+static inline bool operator>(real a, real b) { return a.v > b.v; }
+static inline double val(real a) { return a.v; }
+static inline real sqrt_(real a) {
+  const double s = std::sqrt(a.v);
+  return tape_op(s, a.id, 0.5 / s, -1, 0.0);
+}
 #else
 typedef double real;
 static inline double val(real a) { return a; }
@@ -443,13 +486,13 @@ struct Grid {
     return bc == BC_PERIODIC ? wrap(g, ny) : clampi(g, 0, ny);
   }
   // Conservative value of component c of (possibly ghost) cell (i, j).
-  real W(const double* Wd, int c, int64_t i, int64_t j) const {
+  real W(const real* Wd, int c, int64_t i, int64_t j) const {
     if (i < 0 && p->bc[0] == BC_INFLOW_BAND) {
       double yc = p->y0 + ((double)j + 0.5) * dy;
       if (yc > p->inflow_lo && yc < p->inflow_hi) return inflow_cons(c);
     }
     int64_t ii = cell_x(i), jj = cell_y(j);
-    return real(Wd[((int64_t)c * ny + jj) * nx + ii]);
+    return Wd[((int64_t)c * ny + jj) * nx + ii];
   }
   real inflow_cons(int c) const {
     double rho = p->inflow[0], u = p->inflow[1], v = p->inflow[2], pr = p->inflow[3];
@@ -460,10 +503,10 @@ struct Grid {
     if (p->ndim == 2 && c == 2) return real(rho * v);
     return real(E);
   }
-  double sx(const double* s, int64_t f, int64_t j) const {
+  real sx(const real* s, int64_t f, int64_t j) const {
     return s[cell_y(j) * (nx + 1) + face_x(f)];
   }
-  double sy(const double* s, int64_t i, int64_t g) const {
+  real sy(const real* s, int64_t i, int64_t g) const {
     return s[face_y(g) * nx + cell_x(i)];
   }
 };
@@ -486,7 +529,7 @@ Grid make_grid(const OracleParams* p) {
 // face i-1/2).  Fills out[c] for all components; returns the branch of component 0
 // (the branch does not depend on the component).
 // ---------------------------------------------------------------------------------
-int normal_recon(const Grid& g, const double* Wd, const double* sig_n, int dir, int64_t i,
+int normal_recon(const Grid& g, const real* Wd, const real* sig_n, int dir, int64_t i,
                  int64_t j, bool to_right, real* out) {
   const int r = g.p->order;
   const int k = (r - 1) / 2;
@@ -498,10 +541,10 @@ int normal_recon(const Grid& g, const double* Wd, const double* sig_n, int dir, 
     // face between stencil cells m-1 and m (mirrored: between -m+1 and -m)
     if (dir == 0) {
       int64_t f = to_right ? i + m : i - m + 1;
-      sig[m + 3] = real(g.sx(sig_n, f, j));
+      sig[m + 3] = g.sx(sig_n, f, j);
     } else {
       int64_t f = to_right ? j + m : j - m + 1;
-      sig[m + 3] = real(g.sy(sig_n, i, f));
+      sig[m + 3] = g.sy(sig_n, i, f);
     }
   }
   int branch = 0;
@@ -551,8 +594,8 @@ void to_face_frame(real* q, int dir, int C) {
 // tangential reconstruction at the Gauss points and the Gauss-point fluxes.
 // ---------------------------------------------------------------------------------
 // Faces f in [f_lo, f_hi] on lines b in [b_lo, b_hi] (the whole grid: [0, n] x [0, m-1]).
-void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const double* sy_in,
-                 int dir, double* Fout, double* sig_out, int64_t* hist, int64_t f_lo, int64_t f_hi,
+void face_fluxes(const Grid& g, const real* Wd, const real* sx_in, const real* sy_in,
+                 int dir, real* Fout, real* sig_out, int64_t* hist, int64_t f_lo, int64_t f_hi,
                  int64_t b_lo, int64_t b_hi) {
   const int r = g.p->order;
   const int k = (r - 1) / 2;
@@ -567,8 +610,8 @@ void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const dou
   // extents: along the sweep (normal) n cells, across (tangential) m lines
   const int64_t n = (dir == 0) ? g.nx : g.ny;
   const int64_t mlines = (dir == 0) ? g.ny : g.nx;
-  const double* sig_n = (dir == 0) ? sx_in : sy_in;  // normal-direction strengths
-  const double* sig_t = (dir == 0) ? sy_in : sx_in;  // tangential-direction strengths
+  const real* sig_n = (dir == 0) ? sx_in : sy_in;  // normal-direction strengths
+  const real* sig_t = (dir == 0) ? sy_in : sx_in;  // tangential-direction strengths
 
   // Pass 1: normal reconstructions of cells a = f_lo-1..f_hi (index a-f_lo+1) on lines
   // b = b_lo-kt..b_hi+kt (index b-b_lo+kt), to the "plus" face (QP) and "minus" face (QM).
@@ -613,8 +656,8 @@ void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const dou
         for (int m = -3; m <= 4; ++m) {
           sigt[m + 3] = real(0.0);
           if (m < -k + 1 || m > k) continue;
-          if (dir == 0) sigt[m + 3] = real(g.sy(sig_t, a, b + m));
-          else sigt[m + 3] = real(g.sx(sig_t, b + m, a));
+          if (dir == 0) sigt[m + 3] = g.sy(sig_t, a, b + m);
+          else sigt[m + 3] = g.sx(sig_t, b + m, a);
         }
         int brt = tangential_recon(g, Q, sigt, G, eta, state);
         hist[brt]++;
@@ -642,11 +685,11 @@ void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const dou
       }
       real sface = ssum / real((double)G);  // reading G8
       if (dir == 0) {
-        for (int c = 0; c < C; ++c) Fout[((int64_t)c * g.ny + b) * (g.nx + 1) + f] = val(Fsum[c]);
-        sig_out[b * (g.nx + 1) + f] = val(sface);
+        for (int c = 0; c < C; ++c) Fout[((int64_t)c * g.ny + b) * (g.nx + 1) + f] = Fsum[c];
+        sig_out[b * (g.nx + 1) + f] = sface;
       } else {
-        for (int c = 0; c < C; ++c) Fout[((int64_t)c * (g.ny + 1) + f) * g.nx + b] = val(Fsum[c]);
-        sig_out[f * g.nx + b] = val(sface);
+        for (int c = 0; c < C; ++c) Fout[((int64_t)c * (g.ny + 1) + f) * g.nx + b] = Fsum[c];
+        sig_out[f * g.nx + b] = sface;
       }
     }
   }
@@ -655,14 +698,14 @@ void face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const dou
 // Sec. 2.1, Eq. (2.3): L = -(1/|Omega|) sum over faces |l| * (Gauss-averaged flux . n).
 // Rows row_lo..row_hi of L (all rows: 0..ny-1); sigma_out and the face fluxes are
 // written for the faces those rows need.
-int residual(const OracleParams* p, const double* W, const double* sx_in, const double* sy_in,
-             double* L, double* sx_out, double* sy_out, double* Fx_out, double* Fy_out,
+int residual(const OracleParams* p, const real* W, const real* sx_in, const real* sy_in,
+             real* L, real* sx_out, real* sy_out, real* Fx_out, real* Fy_out,
              int64_t* hist, int64_t row_lo, int64_t row_hi) {
   Grid g = make_grid(p);
   const int C = g.C;
   const int64_t nx = g.nx, ny = g.ny;
-  std::vector<double> Fx((size_t)(C * ny * (nx + 1)));
-  std::vector<double> Fy;
+  std::vector<real> Fx((size_t)(C * ny * (nx + 1)));
+  std::vector<real> Fy;
   face_fluxes(g, W, sx_in, sy_in, 0, Fx.data(), sx_out, hist, 0, nx, row_lo, row_hi);
   if (p->ndim == 2) {
     Fy.resize((size_t)(C * (ny + 1) * nx));
@@ -671,19 +714,40 @@ int residual(const OracleParams* p, const double* W, const double* sx_in, const 
   for (int c = 0; c < C; ++c)
     for (int64_t j = row_lo; j <= row_hi; ++j)
       for (int64_t i = 0; i < nx; ++i) {
-        real dFx = real(Fx[((int64_t)c * ny + j) * (nx + 1) + i + 1]) -
-                   real(Fx[((int64_t)c * ny + j) * (nx + 1) + i]);
+        real dFx = Fx[((int64_t)c * ny + j) * (nx + 1) + i + 1] - Fx[((int64_t)c * ny + j) * (nx + 1) + i];
         real Lv = -(dFx / real(g.dx));
         if (p->ndim == 2) {
-          real dFy = real(Fy[((int64_t)c * (ny + 1) + j + 1) * nx + i]) -
-                     real(Fy[((int64_t)c * (ny + 1) + j) * nx + i]);
+          real dFy = Fy[((int64_t)c * (ny + 1) + j + 1) * nx + i] - Fy[((int64_t)c * (ny + 1) + j) * nx + i];
           Lv = Lv - dFy / real(g.dy);
         }
-        L[((int64_t)c * ny + j) * nx + i] = val(Lv);
+        L[((int64_t)c * ny + j) * nx + i] = Lv;
       }
-  if (Fx_out) std::memcpy(Fx_out, Fx.data(), Fx.size() * sizeof(double));
-  if (Fy_out && p->ndim == 2) std::memcpy(Fy_out, Fy.data(), Fy.size() * sizeof(double));
+  if (Fx_out) std::copy(Fx.begin(), Fx.end(), Fx_out);
+  if (Fy_out && p->ndim == 2) std::copy(Fy.begin(), Fy.end(), Fy_out);
   return 0;
+}
+
+// Array sizes of a problem: W, sigma_x, sigma_y, face fluxes x / y.
+struct Sizes { int64_t w, sx, sy, fx, fy; };
+Sizes sizes_of(const OracleParams* p) {
+  const int C = (p->ndim == 1) ? 3 : 4;
+  const int64_t nx = p->nx, ny = (p->ndim == 1) ? 1 : p->ny;
+  Sizes z;
+  z.w = C * nx * ny;
+  z.sx = ny * (nx + 1);
+  z.sy = (p->ndim == 2) ? (ny + 1) * nx : 1;
+  z.fx = C * ny * (nx + 1);
+  z.fy = (p->ndim == 2) ? C * (ny + 1) * nx : 1;
+  return z;
+}
+std::vector<real> to_real(const double* a, int64_t n) {
+  std::vector<real> v((size_t)n);
+  for (int64_t i = 0; i < n; ++i) v[(size_t)i] = real(a[i]);
+  return v;
+}
+void to_double(const std::vector<real>& v, double* a) {
+  if (!a) return;
+  for (size_t i = 0; i < v.size(); ++i) a[i] = val(v[i]);
 }
 
 // Largest wave speed sum over the cells: max((|u|+c)/dx + (|v|+c)/dy); also reports
@@ -731,7 +795,16 @@ int oracle_residual(const OracleParams* p, const double* W, const double* sx_in,
                     double* Fx, double* Fy, int64_t* hist) {
   int64_t h[BR_COUNT] = {0};
   const int64_t ny = (p->ndim == 1) ? 1 : p->ny;
-  int rc = residual(p, W, sx_in, sy_in, L, sx_out, sy_out, Fx, Fy, h, 0, ny - 1);
+  const Sizes z = sizes_of(p);
+  std::vector<real> w = to_real(W, z.w), sxi = to_real(sx_in, z.sx), syi = to_real(sy_in, z.sy);
+  std::vector<real> l((size_t)z.w), sxo((size_t)z.sx), syo((size_t)z.sy), fx((size_t)z.fx), fy((size_t)z.fy);
+  int rc = residual(p, w.data(), sxi.data(), syi.data(), l.data(), sxo.data(), syo.data(), fx.data(), fy.data(),
+                    h, 0, ny - 1);
+  to_double(l, L);
+  to_double(sxo, sx_out);
+  if (p->ndim == 2) to_double(syo, sy_out);
+  to_double(fx, Fx);
+  if (p->ndim == 2) to_double(fy, Fy);
   if (hist) for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[b];
   return rc;
 }
@@ -745,7 +818,15 @@ int oracle_residual_rows(const OracleParams* p, const double* W, const double* s
   const int64_t ny = (p->ndim == 1) ? 1 : p->ny;
   if (row_lo < 0 || row_hi >= ny || row_lo > row_hi) return -1;
   int64_t h[BR_COUNT] = {0};
-  return residual(p, W, sx_in, sy_in, L, sx_out, sy_out, nullptr, nullptr, h, row_lo, row_hi);
+  const Sizes z = sizes_of(p);
+  std::vector<real> w = to_real(W, z.w), sxi = to_real(sx_in, z.sx), syi = to_real(sy_in, z.sy);
+  std::vector<real> l = to_real(L, z.w), sxo = to_real(sx_out, z.sx), syo = to_real(sy_out, z.sy);
+  int rc = residual(p, w.data(), sxi.data(), syi.data(), l.data(), sxo.data(), syo.data(), nullptr, nullptr, h,
+                    row_lo, row_hi);
+  to_double(l, L);
+  to_double(sxo, sx_out);
+  if (p->ndim == 2) to_double(syo, sy_out);
+  return rc;
 }
 
 // CFL time step dt = cfl / max((|u|+c)/dx + (|v|+c)/dy); returns -1 if a cell average
@@ -773,8 +854,8 @@ const int kRepairPasses = 8;
 // Reading G21b.  Stage update of every cell from the Gauss-averaged face fluxes Fx, Fy
 // of the stage, then the first-order repair passes.  Returns false if a cell is still
 // non-physical afterwards.
-bool stage_update(const Grid& g, int stage, real dt, const double* Wn, const double* Ws,
-                  const double* Fx, const double* Fy, double* sx_out, double* sy_out, double* Wout,
+bool stage_update(const Grid& g, int stage, real dt, const real* Wn, const real* Ws,
+                  const real* Fx, const real* Fy, real* sx_out, real* sy_out, real* Wout,
                   int64_t* hist) {
   const int C = g.C;
   const int64_t nx = g.nx, ny = g.ny;
@@ -791,7 +872,7 @@ bool stage_update(const Grid& g, int stage, real dt, const double* Wn, const dou
   };
   auto physical = [&](int64_t i, int64_t j) {
     real q[4];
-    for (int c = 0; c < C; ++c) q[c] = real(Wout[((int64_t)c * ny + j) * nx + i]);
+    for (int c = 0; c < C; ++c) q[c] = Wout[((int64_t)c * ny + j) * nx + i];
     return primitives(q, C, g.p->gamma).ok;
   };
   // update of cell (i, j); in a repair pass the faces next to a marked cell take the
@@ -834,7 +915,7 @@ bool stage_update(const Grid& g, int stage, real dt, const double* Wn, const dou
       real Lv = -((Fa[0][1][c] - Fa[0][0][c]) / real(g.dx));
       if (ndir == 2) Lv = Lv - (Fa[1][1][c] - Fa[1][0][c]) / real(g.dy);
       const int64_t w = ((int64_t)c * ny + j) * nx + i;
-      Wout[w] = val(rk_combine(stage, dt, real(Wn[w]), real(Ws[w]), Lv));
+      Wout[w] = rk_combine(stage, dt, Wn[w], Ws[w], Lv);
     }
     return any_first;
   };
@@ -872,24 +953,60 @@ bool stage_update(const Grid& g, int stage, real dt, const double* Wn, const dou
       if (physical(i, j)) continue;
       for (int c = 0; c < C; ++c) {
         const int64_t w = ((int64_t)c * ny + j) * nx + i;
-        Wout[w] = val(rk_combine(stage, dt, real(Wn[w]), real(Ws[w]), real(0.0)));
+        Wout[w] = rk_combine(stage, dt, Wn[w], Ws[w], real(0.0));
       }
       const int64_t e = ((int64_t)(C - 1) * ny + j) * nx + i;
-      if (!physical(i, j) && Wout[j * nx + i] > 0.0 && std::isfinite(Wout[e])) {
+      if (!physical(i, j) && val(Wout[j * nx + i]) > 0.0 && std::isfinite(val(Wout[e]))) {
         // pressure at the rounding level of E: p := 1e-13 of the kinetic energy density
-        real rho = real(Wout[j * nx + i]), mm = real(0.0);
+        real rho = Wout[j * nx + i], mm = real(0.0);
         for (int c = 1; c < C - 1; ++c) {
-          real m = real(Wout[((int64_t)c * ny + j) * nx + i]);
+          real m = Wout[((int64_t)c * ny + j) * nx + i];
           mm = mm + m * m;
         }
         real ke = real(0.5) * mm / rho;
-        real big = rmax(ke, rabs(real(Wout[e])));
-        Wout[e] = val(ke + real(1e-13) * big / real(g.p->gamma - 1.0));
+        real big = rmax(ke, rabs(Wout[e]));
+        Wout[e] = ke + real(1e-13) * big / real(g.p->gamma - 1.0);
       }
       if (hist) hist[BR_FROZEN]++;
       if (!physical(i, j)) ok = false;
     }
   return ok;
+}
+
+// One SSP-RK3 step (Sec. 2.3) on real arrays, in place: w holds W^n on entry and W^{n+1}
+// on exit; sx / sy hold sigma^n on entry and the last stage's sigma on exit.
+bool step_real(const OracleParams* p, std::vector<real>& w, std::vector<real>& sx, std::vector<real>& sy,
+               real dt, int64_t* hist) {
+  Grid g = make_grid(p);
+  const Sizes z = sizes_of(p);
+  const int64_t ny = g.ny;
+  int64_t h[BR_COUNT] = {0};
+  std::vector<real> Wn(w), W1((size_t)z.w), W2((size_t)z.w), L((size_t)z.w);
+  std::vector<real> sxa((size_t)z.sx), sya((size_t)z.sy), sxb((size_t)z.sx), syb((size_t)z.sy);
+  std::vector<real> Fx((size_t)z.fx), Fy((size_t)z.fy);
+  bool ok = true;
+  // stage 1
+  residual(p, Wn.data(), sx.data(), sy.data(), L.data(), sxa.data(), sya.data(), Fx.data(), Fy.data(), h, 0, ny - 1);
+  ok &= stage_update(g, 1, dt, Wn.data(), Wn.data(), Fx.data(), Fy.data(), sxa.data(), sya.data(), W1.data(), h);
+  // stage 2
+  residual(p, W1.data(), sxa.data(), sya.data(), L.data(), sxb.data(), syb.data(), Fx.data(), Fy.data(), h, 0,
+           ny - 1);
+  ok &= stage_update(g, 2, dt, Wn.data(), W1.data(), Fx.data(), Fy.data(), sxb.data(), syb.data(), W2.data(), h);
+  // stage 3: its sigma becomes sigma^{n+1}
+  residual(p, W2.data(), sxb.data(), syb.data(), L.data(), sx.data(), sy.data(), Fx.data(), Fy.data(), h, 0,
+           ny - 1);
+  ok &= stage_update(g, 3, dt, Wn.data(), W2.data(), Fx.data(), Fy.data(), sx.data(), sy.data(), w.data(), h);
+  if (hist) for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[b];
+  return ok;
+}
+
+// sigma^0 (reading G7) on real arrays.
+void prime_real(const OracleParams* p, const std::vector<real>& w, std::vector<real>& sx, std::vector<real>& sy) {
+  const Sizes z = sizes_of(p);
+  const int64_t ny = (p->ndim == 1) ? 1 : p->ny;
+  std::vector<real> L((size_t)z.w), zx((size_t)z.sx, real(0.0)), zy((size_t)z.sy, real(0.0));
+  int64_t h[BR_COUNT] = {0};
+  residual(p, w.data(), zx.data(), zy.data(), L.data(), sx.data(), sy.data(), nullptr, nullptr, h, 0, ny - 1);
 }
 
 }  // namespace
@@ -903,44 +1020,28 @@ extern "C" {
 // average is non-physical at the start or stays non-physical after a stage.
 double oracle_step(const OracleParams* p, double* W, double* sx, double* sy, double dt,
                    int64_t* hist) {
-  Grid g = make_grid(p);
-  const int64_t nW = (int64_t)g.C * g.nx * g.ny;
-  const int64_t nsx = g.ny * (g.nx + 1);
-  const int64_t nsy = (p->ndim == 2) ? (g.ny + 1) * g.nx : 1;
-  const int64_t nFx = (int64_t)g.C * g.ny * (g.nx + 1);
-  const int64_t nFy = (p->ndim == 2) ? (int64_t)g.C * (g.ny + 1) * g.nx : 1;
   if (!(dt > 0.0)) {
     dt = oracle_cfl_dt(p, W);
     if (dt < 0.0) return dt;
   }
-  std::vector<double> Wn(W, W + nW), W1((size_t)nW), W2((size_t)nW), L((size_t)nW);
-  std::vector<double> sxa((size_t)nsx), sya((size_t)nsy), sxb((size_t)nsx), syb((size_t)nsy);
-  std::vector<double> Fx((size_t)nFx), Fy((size_t)nFy);
-  const real rdt = real(dt);
-  bool ok = true;
-  // stage 1
-  oracle_residual(p, Wn.data(), sx, sy, L.data(), sxa.data(), sya.data(), Fx.data(), Fy.data(), hist);
-  ok &= stage_update(g, 1, rdt, Wn.data(), Wn.data(), Fx.data(), Fy.data(), sxa.data(), sya.data(),
-                     W1.data(), hist);
-  // stage 2
-  oracle_residual(p, W1.data(), sxa.data(), sya.data(), L.data(), sxb.data(), syb.data(), Fx.data(),
-                  Fy.data(), hist);
-  ok &= stage_update(g, 2, rdt, Wn.data(), W1.data(), Fx.data(), Fy.data(), sxb.data(), syb.data(),
-                     W2.data(), hist);
-  // stage 3
-  oracle_residual(p, W2.data(), sxb.data(), syb.data(), L.data(), sx, sy, Fx.data(), Fy.data(), hist);
-  ok &= stage_update(g, 3, rdt, Wn.data(), W2.data(), Fx.data(), Fy.data(), sx, sy, W, hist);
+  const Sizes z = sizes_of(p);
+  std::vector<real> w = to_real(W, z.w), sxv = to_real(sx, z.sx), syv = to_real(sy ? sy : W, z.sy);
+  if (!sy) std::fill(syv.begin(), syv.end(), real(0.0));
+  const bool ok = step_real(p, w, sxv, syv, real(dt), hist);
+  to_double(w, W);
+  to_double(sxv, sx);
+  if (p->ndim == 2) to_double(syv, sy);
   return ok ? dt : -dt;
 }
 
 // sigma^0 (reading G7): the sigma of a residual evaluated with sigma_in = 0.
 int oracle_prime_sigma(const OracleParams* p, const double* W, double* sx, double* sy) {
-  Grid g = make_grid(p);
-  const int64_t nW = (int64_t)g.C * g.nx * g.ny;
-  const int64_t nsx = g.ny * (g.nx + 1);
-  const int64_t nsy = (p->ndim == 2) ? (g.ny + 1) * g.nx : 1;
-  std::vector<double> L((size_t)nW), zx((size_t)nsx, 0.0), zy((size_t)nsy, 0.0);
-  return oracle_residual(p, W, zx.data(), zy.data(), L.data(), sx, sy, nullptr, nullptr, nullptr);
+  const Sizes z = sizes_of(p);
+  std::vector<real> w = to_real(W, z.w), sxv((size_t)z.sx), syv((size_t)z.sy);
+  prime_real(p, w, sxv, syv);
+  to_double(sxv, sx);
+  if (p->ndim == 2) to_double(syv, sy);
+  return 0;
 }
 
 // One-dimensional ASE-DF reconstruction of one cell (Algorithm 1 capped at r), for
@@ -1018,3 +1119,90 @@ void oracle_reset_op_counts() { g_ops = {0, 0, 0, 0}; }
 #endif
 
 }  // extern "C"
+
+#ifdef ORACLE_TAPE
+namespace {
+
+std::vector<real> tape_inputs(const double* a, int64_t n) {
+  std::vector<real> v((size_t)n);
+  for (int64_t i = 0; i < n; ++i) v[(size_t)i] = tape_input(a[i]);
+  return v;
+}
+
+// adjoint accumulation from the seeds (id, weight)
+std::vector<double> backward(const std::vector<std::pair<int64_t, double>>& seeds) {
+  std::vector<double> adj(g_tape.size(), 0.0);
+  for (auto& sd : seeds)
+    if (sd.first >= 0) adj[(size_t)sd.first] += sd.second;
+  for (int64_t i = (int64_t)g_tape.size() - 1; i >= 0; --i) {
+    const double a = adj[(size_t)i];
+    if (a == 0.0) continue;
+    const TapeNode& n = g_tape[(size_t)i];
+    if (n.a >= 0) adj[(size_t)n.a] += n.da * a;
+    if (n.b >= 0) adj[(size_t)n.b] += n.db * a;
+  }
+  return adj;
+}
+
+void gather(const std::vector<real>& in, const std::vector<double>& adj, double* out) {
+  if (!out) return;
+  for (size_t i = 0; i < in.size(); ++i) out[i] += (in[i].id >= 0) ? adj[(size_t)in[i].id] : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Reverse-mode vector-Jacobian product of one residual evaluation (L, sigma_out) =
+// R(W, sigma_in): accumulates Wbar += (dL/dW)^T Lbar + (dsigma_out/dW)^T sigbar_out and
+// the same for sigma_in.  Returns the tape length.
+int64_t oracle_residual_vjp(const OracleParams* p, const double* W, const double* sx_in, const double* sy_in,
+                            const double* Lbar, const double* sxbar_out, const double* sybar_out, double* Wbar,
+                            double* sxbar_in, double* sybar_in) {
+  g_tape.clear();
+  const Sizes z = sizes_of(p);
+  const int64_t ny = (p->ndim == 1) ? 1 : p->ny;
+  std::vector<real> w = tape_inputs(W, z.w), sxi = tape_inputs(sx_in, z.sx), syi = tape_inputs(sy_in, z.sy);
+  std::vector<real> L((size_t)z.w), sxo((size_t)z.sx), syo((size_t)z.sy);
+  int64_t h[BR_COUNT] = {0};
+  residual(p, w.data(), sxi.data(), syi.data(), L.data(), sxo.data(), syo.data(), nullptr, nullptr, h, 0, ny - 1);
+  std::vector<std::pair<int64_t, double>> seeds;
+  for (int64_t i = 0; i < z.w; ++i) seeds.push_back({L[(size_t)i].id, Lbar[i]});
+  if (sxbar_out)
+    for (int64_t i = 0; i < z.sx; ++i) seeds.push_back({sxo[(size_t)i].id, sxbar_out[i]});
+  if (sybar_out && p->ndim == 2)
+    for (int64_t i = 0; i < z.sy; ++i) seeds.push_back({syo[(size_t)i].id, sybar_out[i]});
+  std::vector<double> adj = backward(seeds);
+  gather(w, adj, Wbar);
+  gather(sxi, adj, sxbar_in);
+  if (p->ndim == 2) gather(syi, adj, sybar_in);
+  const int64_t n = (int64_t)g_tape.size();
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return n;
+}
+
+// Reverse mode through sigma^0 = prime(W0) and nsteps SSP-RK3 steps of fixed dt:
+// Wbar0 += (dW_final/dW0)^T Wbar_final.  Returns the tape length (or -1 if a step went
+// non-physical).
+int64_t oracle_run_vjp(const OracleParams* p, const double* W0, int32_t nsteps, double dt, const double* Wbar_final,
+                       double* Wbar0) {
+  g_tape.clear();
+  const Sizes z = sizes_of(p);
+  std::vector<real> w0 = tape_inputs(W0, z.w);
+  std::vector<real> w(w0), sx((size_t)z.sx), sy((size_t)z.sy);
+  prime_real(p, w, sx, sy);
+  bool ok = true;
+  for (int32_t k = 0; k < nsteps; ++k) ok &= step_real(p, w, sx, sy, real(dt), nullptr);
+  std::vector<std::pair<int64_t, double>> seeds;
+  for (int64_t i = 0; i < z.w; ++i) seeds.push_back({w[(size_t)i].id, Wbar_final[i]});
+  std::vector<double> adj = backward(seeds);
+  gather(w0, adj, Wbar0);
+  const int64_t n = (int64_t)g_tape.size();
+  g_tape.clear();
+  g_tape.shrink_to_fit();
+  return ok ? n : -1;
+}
+
+}  // extern "C"
+#endif

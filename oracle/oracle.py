@@ -21,6 +21,7 @@ _SRC = os.path.join(_HERE, "ase_df_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libasedf_oracle.so")
 _LIB_COUNT = os.path.join(_BUILD, "libasedf_oracle_count.so")
+_LIB_TAPE = os.path.join(_BUILD, "libasedf_oracle_tape.so")
 _lock = threading.Lock()
 
 BRANCHES = ("lin9", "lin7", "lin5", "weno_df", "lin3", "df3", "first_order", "repaired", "frozen")
@@ -38,7 +39,7 @@ def _compile(out: str, extra=()) -> None:
 def build(force: bool = False) -> None:
     """Compile the oracle libraries (plain and op-counting) if missing or stale."""
     with _lock:
-        for out, extra in ((_LIB, ()), (_LIB_COUNT, ("-DORACLE_COUNT_OPS",))):
+        for out, extra in ((_LIB, ()), (_LIB_COUNT, ("-DORACLE_COUNT_OPS",)), (_LIB_TAPE, ("-DORACLE_TAPE",))):
             if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
                 _compile(out, extra)
 
@@ -86,14 +87,19 @@ def _setup(lib):
     return lib
 
 
-def _lib(counting: bool = False):
-    key = "count" if counting else "plain"
+def _lib(counting: bool = False, tape: bool = False):
+    key = "count" if counting else ("tape" if tape else "plain")
     if key not in _libs:
         build()
-        lib = _setup(ctypes.CDLL(_LIB_COUNT if counting else _LIB))
+        lib = _setup(ctypes.CDLL(_LIB_COUNT if counting else (_LIB_TAPE if tape else _LIB)))
         if counting:
             lib.oracle_op_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
             lib.oracle_reset_op_counts.argtypes = []
+        if tape:
+            lib.oracle_residual_vjp.argtypes = [ctypes.POINTER(_Params)] + [_P] * 9
+            lib.oracle_residual_vjp.restype = ctypes.c_int64
+            lib.oracle_run_vjp.argtypes = [ctypes.POINTER(_Params), _P, ctypes.c_int32, ctypes.c_double, _P, _P]
+            lib.oracle_run_vjp.restype = ctypes.c_int64
         _libs[key] = lib
     return _libs[key]
 
@@ -265,3 +271,30 @@ def op_counts_residual(pb, W, sx, sy):
     out = (ctypes.c_longlong * 4)()
     lib.oracle_op_counts(out)
     return tuple(int(v) for v in out)
+
+
+def residual_vjp(pb, W, sx, sy, Lbar, sxbar_out=None, sybar_out=None):
+    """Reverse-mode VJP of (L, sigma_out) = R(W, sigma_in) by the oracle's tape:
+    -> (Wbar, sxbar_in, sybar_in)."""
+    W, sx, sy, Lbar = _f64(W), _f64(sx), _f64(sy), _f64(Lbar)
+    Wbar = np.zeros(pb.state_shape)
+    sxb = np.zeros(pb.sx_shape)
+    syb = np.zeros(pb.sy_shape)
+    sxo = None if sxbar_out is None else _f64(sxbar_out)
+    syo = None if sybar_out is None else _f64(sybar_out)
+    p = _params(pb)
+    _lib(tape=True).oracle_residual_vjp(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), _ptr(Lbar), _ptr(sxo),
+                                        _ptr(syo), _ptr(Wbar), _ptr(sxb), _ptr(syb))
+    return Wbar, sxb, syb
+
+
+def run_vjp(pb, W0, nsteps: int, dt: float, Wbar_final):
+    """Reverse mode through sigma^0 = prime(W0) and nsteps fixed-dt SSP-RK3 steps:
+    -> dJ/dW0 for J with dJ/dW_final = Wbar_final."""
+    W0, Wbf = _f64(W0), _f64(Wbar_final)
+    Wbar0 = np.zeros(pb.state_shape)
+    p = _params(pb)
+    n = _lib(tape=True).oracle_run_vjp(ctypes.byref(p), _ptr(W0), int(nsteps), float(dt), _ptr(Wbf), _ptr(Wbar0))
+    if n < 0:
+        raise FloatingPointError("non-physical state in the taped run")
+    return Wbar0
