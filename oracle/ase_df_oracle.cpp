@@ -59,6 +59,9 @@
 //       convex combination of physical states); where rounding of a near-vacuum
 //       pressure still leaves p <= 0, E is raised to give p = 1e-13 of the kinetic
 //       energy density.  Not conservative at that cell.
+//   G23 reverse mode (the tape build): the derivative of the scheme on the branch the
+//       forward takes; at a kink of |x| or max(a, b) whose argument is within a relative
+//       2^-40 of it, the symmetric subgradient (0 for |x|, 1/2 each for max).
 //
 // Data layout: W is [C][ny][nx] (C = 3 in 1D: rho, rho u, E; C = 4 in 2D: rho, rho u,
 // rho v, E), sigma_x is [ny][nx+1] (x-face f sits between cells f-1 and f), sigma_y is
@@ -143,6 +146,28 @@ static inline real sqrt_(real a) { return std::sqrt(a); }
 #endif
 static inline real rabs(real a) { return val(a) < 0.0 ? -a : a; }
 static inline real rmax(real a, real b) { return val(a) < val(b) ? b : a; }
+
+// Kinks (reading G23).  |x| and max(a, b) have no derivative at x = 0 and a = b.  Where
+// the argument lies within a relative 2^-40 of the kink (|x| <= 2^-40 scale, resp.
+// |a - b| <= 2^-40 (|a| + |b|)) its side is decided by rounding, so the reverse mode
+// takes the symmetric subgradient there: 0 for |x|, one half to each operand for max.
+// Values are those of rabs / rmax.
+const double kKink = 9.094947017729282e-13;  // 2^-40
+#ifdef ORACLE_TAPE
+static inline real kabs(real a, double scale) {
+  const real r = rabs(a);
+  if (std::fabs(val(a)) <= kKink * scale) return tape_op(val(r), a.id, 0.0, -1, 0.0);
+  return r;
+}
+static inline real kmax(real a, real b) {
+  if (std::fabs(val(a) - val(b)) <= kKink * (std::fabs(val(a)) + std::fabs(val(b))))
+    return tape_op(val(rmax(a, b)), a.id, 0.5, b.id, 0.5);
+  return rmax(a, b);
+}
+#else
+static inline real kabs(real a, double) { return rabs(a); }
+static inline real kmax(real a, real b) { return rmax(a, b); }
+#endif
 
 // ---------------------------------------------------------------------------------
 // Problem description.  Its own copy; the Python wrapper fills it field by field.
@@ -283,9 +308,11 @@ void weno_ao53_df(const real* Wm, const real* alpha, int npts, const double* xi,
   // smoothness indicators (reading G6: undamped polynomials) and the simple beta5
   real beta[3];
   for (int k = 0; k < 3; ++k) beta[k] = beta3(a1[k], a2[k]);
-  real beta5 = (beta[0] + real(4.0) * beta[1] + beta[2]) / real(6.0) + rabs(beta[0] - beta[2]);
+  real beta5 = (beta[0] + real(4.0) * beta[1] + beta[2]) / real(6.0) +
+               kabs(beta[0] - beta[2], val(beta[0]) + val(beta[2]));
   // tau_Z (reading G5)
-  real tau = (rabs(beta5 - beta[0]) + rabs(beta5 - beta[1]) + rabs(beta5 - beta[2])) / real(3.0);
+  real tau = (kabs(beta5 - beta[0], val(beta5) + val(beta[0])) + kabs(beta5 - beta[1], val(beta5) + val(beta[1])) +
+              kabs(beta5 - beta[2], val(beta5) + val(beta[2]))) / real(3.0);
   if (beta_out) {
     beta_out[0] = beta[0]; beta_out[1] = beta[1]; beta_out[2] = beta[2];
     beta_out[3] = beta5; beta_out[4] = tau;
@@ -416,7 +443,7 @@ void phys_flux(const real* q, const Prim& s, int C, real* F) {
 
 // Sec. 3.1, discontinuity strength of one Gauss point (readings G9).
 real sigma_point(const Prim& L, const Prim& R, int C) {
-  real dp = rabs(L.p - R.p);
+  real dp = kabs(L.p - R.p, val(L.p) + val(R.p));
   real s = dp / L.p + dp / R.p;
   real dmn = L.un / L.c - R.un / R.c;
   s += dmn * dmn;
@@ -447,7 +474,7 @@ bool lf_flux_point(const real* qL, const real* qR, const real* cL, const real* c
   real FL[4], FR[4];
   phys_flux(a, L, C, FL);
   phys_flux(b, R, C, FR);
-  real lam = rmax(rabs(L.un) + L.c, rabs(R.un) + R.c);
+  real lam = kmax(kabs(L.un, val(L.c)) + L.c, kabs(R.un, val(R.c)) + R.c);
   for (int c = 0; c < C; ++c)
     F[c] = real(0.5) * (FL[c] + FR[c]) - real(0.5) * lam * (b[c] - a[c]);
   *sigma = fallback ? real(kSigmaBig) : sigma_point(L, R, C);

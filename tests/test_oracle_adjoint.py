@@ -140,3 +140,25 @@ def test_run_vjp_matches_central_differences(oracle, r):
         fd = (J(W0 + h * d)[0] - J(W0 - h * d)[0]) / (2 * h)
         ad = float(np.sum(G * d))
         assert abs(fd - ad) <= 1e-6 * abs(fd) + 1e-9, (k, fd, ad)
+
+
+def test_kinks_take_the_symmetric_subgradient(oracle):
+    """Reading G23.  On the Sod tube at t = 0 the velocity is exactly zero and the
+    Gauss-point pressures of the constant regions agree to rounding, so |u| in the
+    Lax-Friedrichs speed and |p_L - p_R| in sigma sit on their kinks; a central
+    difference sees the symmetric subgradient (0) there, and so must the tape."""
+    pb, W = P.sod(80, 5)
+    sx, sy = oracle.prime_sigma(pb, W)
+    rng = np.random.default_rng(7)
+    Lbar = rng.standard_normal(pb.state_shape)
+    _, sxo, _, _, _, _ = oracle.residual(pb, W, sx, sy)
+    sxb = np.where(sxo < 1e29, rng.standard_normal(pb.sx_shape), 0.0)
+    Wbar, _, _ = oracle.residual_vjp(pb, W, sx, sy, Lbar, sxb)
+    for k in range(3):
+        dW = W * rng.uniform(-1.0, 1.0, W.shape)
+        h = 1e-7
+        Jp, _ = _objective(oracle, pb, W + h * dW, sx, sy, Lbar, sxb, np.zeros(pb.sy_shape))
+        Jm, _ = _objective(oracle, pb, W - h * dW, sx, sy, Lbar, sxb, np.zeros(pb.sy_shape))
+        fd = (Jp - Jm) / (2 * h)
+        ad = float(np.sum(Wbar * dW))
+        assert abs(fd - ad) <= 1e-6 * abs(fd) + 1e-8 * np.sum(np.abs(Wbar * dW)), (k, fd, ad)
