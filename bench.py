@@ -333,6 +333,8 @@ def run_ours(args, world, rank, local):
     }
     if not args.no_batched:
         out["batched"] = batched_bench(A, torch, args)
+    if not args.no_adjoint:
+        out["adjoint"] = adjoint_bench(A, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_sample(args.order)
     if rank == 0:
@@ -384,6 +386,99 @@ def batched_bench(A, torch, args):
         "speedup": round(ms_1 / ms_b, 3),
         "schedule": tune.get("schedule"),
         "nonphysical_problems": int(((flags & 1) != 0).sum()),
+    }
+
+
+def adjoint_bench(A, torch, args):
+    """The adjoint workload: vortex 256^2 with a seeded 1% density perturbation, order 7,
+    50 SSP-RK3 steps at the t = 0 CFL dt, checkpoints every 10 steps, J = sum rho_final^2.
+    Times the taped forward (with checkpoint copies), the checkpointed backward, the plain
+    forward (ase_df_run), and one residual adjoint against one residual."""
+    import numpy as np
+
+    from paper_2410_05489_gb300.adjoint import rollout
+
+    n, order, nsteps, every = 256, 7, 50, 10
+    pb, W0 = P.isentropic_vortex(n, order)
+    rng = np.random.default_rng(1)
+    W0 = W0.copy()
+    W0[0] = W0[0] * (1.0 + 0.01 * rng.uniform(-1.0, 1.0, W0[0].shape))
+    s = A.Solver(pb, W0)
+    # the t = 0 CFL dt, from the library's own CFL step
+    probe = A.Solver(pb, W0)
+    probe.step(0.0)
+    dt = probe.status()[1]
+    probe.close()
+    W0d = torch.as_tensor(W0, dtype=torch.float64, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def one():
+        W = W0d.clone().requires_grad_(True)
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record()
+        Wf = rollout(s, W, nsteps, dt, every=every)
+        J = (Wf[0] ** 2).sum()
+        e1.record()
+        (G,) = torch.autograd.grad(J, [W])
+        e2.record()
+        e2.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), G
+
+    for _ in range(2):
+        one()
+    fw, bw = [], []
+    for _ in range(3):
+        f_, b_, G = one()
+        fw.append(f_)
+        bw.append(b_)
+    fwd_ms, bwd_ms = min(fw), min(bw)
+    # plain forward: the same steps as graph replays, no checkpoints
+    s.set_state(W0)
+    s.run(nsteps, dt)
+    torch.cuda.synchronize()
+    plain = []
+    for _ in range(3):
+        s.set_state(W0)
+        e0, e1 = ev(), ev()
+        e0.record()
+        s.run(nsteps, dt)
+        e1.record()
+        e1.synchronize()
+        plain.append(e0.elapsed_time(e1))
+    plain_ms = min(plain)
+    # one residual adjoint vs one residual (same inputs)
+    s.set_state(W0)
+    L, sxo, syo = s.residual()
+    Lbar = torch.ones_like(L)
+    Wb, sxb, syb = s.residual_adjoint(s.W, s.sx, s.sy, Lbar)
+    reps = 20
+    torch.cuda.synchronize()
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record()
+    for _ in range(reps):
+        A.ase_df_residual(s.ctx, s.W, s.sx, s.sy, L, sxo, syo)
+    e1.record()
+    for _ in range(reps):
+        A.ase_df_residual_adjoint(s.ctx, s.W, s.sx, s.sy, Lbar, None, None, Wb, sxb, syb)
+    e2.record()
+    e2.synchronize()
+    res_ms, adj_ms = e0.elapsed_time(e1) / reps, e1.elapsed_time(e2) / reps
+    _, marked, _ = A.ase_df_get_repair_stats(s.ctx)
+    s.close()
+    return {
+        "workload": "isentropic vortex 256^2 periodic, rho x (1 + 0.01 U[-1,1]) per cell (seed 1), order 7, "
+                    "50 SSP-RK3 steps at the t=0 CFL dt, checkpoints every 10 steps, J = sum rho_final^2",
+        "dt": dt,
+        "forward_ms": round(fwd_ms, 3),
+        "backward_ms": round(bwd_ms, 3),
+        "plain_forward_ms": round(plain_ms, 3),
+        "backward_over_forward": round(bwd_ms / fwd_ms, 3),
+        "gradient_over_plain_forward": round((fwd_ms + bwd_ms) / plain_ms, 3),
+        "residual_ms": round(res_ms, 4),
+        "residual_adjoint_ms": round(adj_ms, 4),
+        "residual_adjoint_over_residual": round(adj_ms / res_ms, 3),
+        "grad_norm": float(torch.linalg.vector_norm(G)),
+        "repaired_cells": marked,
     }
 
 
@@ -442,6 +537,7 @@ def main():
     ap.add_argument("--ref-n", type=int, default=96)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -131,6 +131,42 @@ ase_df_status ase_df_step(ase_df_ctx* ctx, double* W, double* sx, double* sy, do
 ase_df_status ase_df_run(ase_df_ctx* ctx, double* W, double* sx, double* sy, double dt,
                          int32_t nsteps, void* stream);
 
+/* Adjoint (vector-Jacobian product) of one residual evaluation
+ * (L, sigma_out) = R(W, sigma_in) of ase_df_residual:
+ *   Wbar     += (dL/dW)^T Lbar + (dsigma_out/dW)^T sigma_bar_out
+ *   sxbar_in += (dL/dsx_in)^T Lbar + (dsigma_out/dsx_in)^T sigma_bar_out   (same for y)
+ * The derivative is that of the scheme as defined, taken on the branch the forward
+ * evaluation takes: Algorithm 1's branch choice (Sec. 3) is held fixed; linear
+ * reconstructions have constant weights; on the WENOZ-AO(5,3) fallback (Sec. 3.2) the
+ * WENO-Z weights (beta, tau_Z, |.| piecewise) and the DF factors alpha = sigma_thres / A
+ * of Eq. (3.2) are differentiated; the Lax-Friedrichs flux of Sec. 2.3 takes the
+ * derivative of the larger wave speed; sigma of Sec. 3.1 is differentiated as written;
+ * a Gauss point that took the first-order states passes its adjoint to the two cell
+ * averages (its sigma, 1e30, is constant).
+ * Arrays are device pointers in the layouts of ase_df_residual: W, Lbar, Wbar
+ * [C][ny][nx]; sx_*, sxbar_* [ny][nx+1]; sy_*, sybar_* [ny+1][nx] (NULL in 1D).  Lbar,
+ * sxbar_out and sybar_out may be NULL (zero adjoint); sxbar_in and sybar_in may be NULL
+ * (that adjoint is not formed).  Outputs are accumulated, not overwritten; they must not
+ * alias the inputs.  The first call allocates the context's adjoint scratch (about
+ * (4r + 12) C doubles per cell in 2D); ASE_DF_E_NOMEM if that fails.  Deterministic: the
+ * kernels gather, without atomics. */
+ase_df_status ase_df_residual_adjoint(ase_df_ctx* ctx, const double* W, const double* sx_in,
+                                      const double* sy_in, const double* Lbar, const double* sxbar_out,
+                                      const double* sybar_out, double* Wbar, double* sxbar_in,
+                                      double* sybar_in, void* stream);
+
+/* Adjoint of one ase_df_step of fixed dt > 0 (Sec. 2.3, SSP-RK3 in Shu-Osher form, each
+ * stage consuming the sigma of the stage before).  W, sx, sy hold W^n and sigma^n (as
+ * passed to that step; read only).  On entry Wbar = dJ/dW^{n+1} and sxbar/sybar =
+ * dJ/dsigma^{n+1} (the third stage's sigma_out); on exit they hold dJ/dW^n and
+ * dJ/dsigma^n.  The step's first two stages are recomputed on the device (the same
+ * launches as ase_df_step, so the stage states are bit-identical) and three residual
+ * adjoints run backwards.  The positivity repair of ase_df_step is not differentiated:
+ * if a recomputed stage needed it, the step's repaired-cell count grows
+ * (ase_df_get_repair_stats) and the result is the adjoint of the unrepaired update. */
+ase_df_status ase_df_step_adjoint(ase_df_ctx* ctx, const double* W, const double* sx, const double* sy,
+                                  double dt, double* Wbar, double* sxbar, double* sybar, void* stream);
+
 /* Synchronises the stream of the last call and reads the device status word (ASE_DF_FLAG_*),
  * the last dt and the time t.  Returns ASE_DF_E_NONPHYSICAL if that bit is set. */
 ase_df_status ase_df_get_status(ase_df_ctx* ctx, uint32_t* flags, double* last_dt, double* t);

@@ -69,6 +69,8 @@ def _load():
         "ase_df_copy_face_fluxes": ([CTX, _VP, _VP, _VP], _c.c_int),
         "ase_df_step": ([CTX, _VP, _VP, _VP, _c.c_double, _VP], _c.c_int),
         "ase_df_run": ([CTX, _VP, _VP, _VP, _c.c_double, _c.c_int32, _VP], _c.c_int),
+        "ase_df_residual_adjoint": ([CTX, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _c.c_int),
+        "ase_df_step_adjoint": ([CTX, _VP, _VP, _VP, _c.c_double, _VP, _VP, _VP, _VP], _c.c_int),
         "ase_df_get_status": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)], _c.c_int),
         "ase_df_reset": ([CTX, _c.c_double, _VP], _c.c_int),
         "ase_df_get_repair_stats": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_uint64),
@@ -154,6 +156,18 @@ def ase_df_step(ctx, W, sx, sy, dt: float = 0.0, stream=None) -> None:
 
 def ase_df_run(ctx, W, sx, sy, dt: float, nsteps: int, stream=None) -> None:
     _check(ctx, _load().ase_df_run(ctx, _ptr(W), _ptr(sx), _ptr(sy), float(dt), int(nsteps), _stream(stream)))
+
+
+def ase_df_residual_adjoint(ctx, W, sx_in, sy_in, Lbar, sxbar_out, sybar_out, Wbar, sxbar_in, sybar_in,
+                            stream=None) -> None:
+    _check(ctx, _load().ase_df_residual_adjoint(ctx, _ptr(W), _ptr(sx_in), _ptr(sy_in), _ptr(Lbar), _ptr(sxbar_out),
+                                                _ptr(sybar_out), _ptr(Wbar), _ptr(sxbar_in), _ptr(sybar_in),
+                                                _stream(stream)))
+
+
+def ase_df_step_adjoint(ctx, W, sx, sy, dt: float, Wbar, sxbar, sybar, stream=None) -> None:
+    _check(ctx, _load().ase_df_step_adjoint(ctx, _ptr(W), _ptr(sx), _ptr(sy), float(dt), _ptr(Wbar), _ptr(sxbar),
+                                            _ptr(sybar), _stream(stream)))
 
 
 def ase_df_get_status(ctx) -> Tuple[int, float, float]:
@@ -244,6 +258,22 @@ class Solver:
         syo = torch.empty_like(sy)
         ase_df_residual(self.ctx, W, sx, self._sy(sy), L, sxo, self._sy(syo))
         return L, sxo, syo
+
+    def residual_adjoint(self, W, sx, sy, Lbar=None, sxbar_out=None, sybar_out=None, Wbar=None, sxbar_in=None,
+                         sybar_in=None):
+        """Accumulates the residual's vector-Jacobian product into Wbar, sxbar_in, sybar_in
+        (zero tensors are made for the ones not given) and returns them."""
+        Wbar = torch.zeros_like(W) if Wbar is None else Wbar
+        sxbar_in = torch.zeros_like(sx) if sxbar_in is None else sxbar_in
+        sybar_in = torch.zeros_like(sy) if sybar_in is None else sybar_in
+        ase_df_residual_adjoint(self.ctx, W, sx, self._sy(sy), Lbar, sxbar_out, self._sy(sybar_out), Wbar, sxbar_in,
+                                self._sy(sybar_in))
+        return Wbar, sxbar_in, sybar_in
+
+    def step_adjoint(self, W, sx, sy, dt: float, Wbar, sxbar, sybar) -> None:
+        """In place: (Wbar, sxbar, sybar) from the adjoint of W^{n+1}, sigma^{n+1} to that
+        of W^n, sigma^n for the step of fixed dt from (W, sx, sy)."""
+        ase_df_step_adjoint(self.ctx, W, sx, self._sy(sy), dt, Wbar, sxbar, self._sy(sybar))
 
     def face_fluxes(self):
         pb = self.pb

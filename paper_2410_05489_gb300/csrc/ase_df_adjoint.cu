@@ -1,0 +1,857 @@
+// Hand-written adjoint (vector-Jacobian product) of the ASE-DF residual of one sweep
+// direction, sm_103a, FP64.  Compiled once per scheme order (ASE_DF_ORDER).
+//
+// The forward residual of one direction is, per face f of line b,
+//   Q_s(line l)   = normal reconstruction of the cell of side s on line l (Sec. 3)
+//   q_s,g         = tangential reconstruction of Q_s at Gauss point g (Sec. 2.1)
+//   F_f           = sum_g (eta_g / 2) LF2(q_L,g, q_R,g)    (Sec. 2.3)
+//   sigma_f       = (1/G) sum_g sigma(q_L,g, q_R,g)          (Sec. 3.1)
+//   L(i)          = -(F_{i+1} - F_i) / dx   (+ the other direction)
+// The adjoint runs it backwards in deterministic kernels (every output element is
+// written by one thread; no atomics):
+//   K1 face kernel: recomputes the tile like the forward sweep, forms
+//      Fbar_f = (Lbar(f) - Lbar(f-1)) / dx, back-propagates through the Gauss sum, the
+//      Lax-Friedrichs flux (|.| and max taken piecewise, on the branch of the forward
+//      value), sigma_out and the tangential reconstruction of each side.  It writes, per
+//      face, side and tangential offset t, the adjoint of Q_s(line b+t) (Tbar); the
+//      adjoint of the two cell averages where a Gauss point took the first-order states
+//      (Cbar); and the sigma_in adjoints of the tangential branch (Stb).
+//   K2 normal kernel: per reconstructing cell (a, l) gathers the adjoints of its plus
+//      face value (face a+1) and minus face value (face a) from Tbar and back-propagates
+//      through the normal reconstruction: the adjoint of each stencil cell (Nbar) and
+//      the sigma_in adjoints of the normal branch (Snb).
+//   K3 gather: per cell, sums the Nbar and Cbar entries of every stencil position that
+//      the boundary maps onto it (periodic wrap, zero-gradient clamp; inflow ghost cells
+//      are constants) into Wbar.
+//   K4 / K5 gathers: per sigma_in entry (normal / tangential faces), sum Snb / Stb over
+//      the stencil positions that read it.
+// Branch decisions (Algorithm 1) are recomputed from the same sigma_in and held fixed;
+// at a kink of |x| or max whose argument is within a relative 2^-40 of it, the
+// symmetric subgradient is taken (kKink below).
+// Within a branch the reconstruction is differentiated as defined: constant weights on
+// the linear branches; on the WENOZ-AO(5,3) branch the WENO-Z weights (beta, tau_Z, |.|
+// piecewise) and the DF factors alpha = sigma_thres / A of Eq. (3.2), whose derivative
+// -alpha^2 / sigma_thres carries the adjoint to the face strengths summed in A.
+
+#include <algorithm>
+#include <cuda_runtime.h>
+
+#include "ase_df_adjoint.cuh"
+#include "ase_df_sweep_body.cuh"
+
+#ifndef ASE_DF_ORDER
+#error "ASE_DF_ORDER must be defined"
+#endif
+
+namespace asedf {
+namespace {
+
+// Kinks: |x| and max(a, b) have no derivative at x = 0 and a = b.  Where the argument is
+// within a relative 2^-40 of the kink its side is decided by rounding (it differs
+// between two correct evaluations, and between the two sides of a central difference),
+// so the adjoint takes the symmetric subgradient there: 0 for |x|, one half to each
+// operand of max.
+constexpr double kKink = 9.094947017729282e-13;  // 2^-40
+
+// d|x|/dx with that rule; scale > 0 is the size x is compared with
+__device__ __forceinline__ double dabs(double x, double scale) {
+  if (fabs(x) <= kKink * scale) return 0.0;
+  return (x < 0.0) ? -1.0 : 1.0;
+}
+
+// ---------------------------------------------------------------------------------
+// reconstruction VJPs.  Stencil values v[t*vs] (t = -K..K); vbc points at the adjoint
+// of W_0 in a unit-stride array; ab[0..2] accumulate the adjoints of alpha of S3_{-1},
+// S3_0, S3_1 and ab[3] that of alpha of S5 (or of S3_0 for the DF-damped order 3).
+// ---------------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void lin_vjp(const double* w, double pb, double* vbc) {
+  constexpr int H = (M - 1) / 2;
+#pragma unroll
+  for (int t = -H; t <= H; ++t) vbc[t] = fma(w[4 + t], pb, vbc[t]);
+}
+
+// WENOZ-AO(5,3) with DF damping (Sec. 3.2); pb[q] is the adjoint of the value at point
+// p0+q.
+template <int NP>
+__device__ void weno_vjp(const double* v, int vs, const Branch& br, const Tables& T, int p0, const double* pb,
+                         double* vbc, double* ab) {
+  double c1[3], c2[3], beta[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double* vk = v + (k - 2) * vs;
+    c1[k] = T.cq[k][0][0] * vk[0] + T.cq[k][0][1] * vk[vs] + T.cq[k][0][2] * vk[2 * vs];
+    c2[k] = T.cq[k][1][0] * vk[0] + T.cq[k][1][1] * vk[vs] + T.cq[k][1][2] * vk[2 * vs];
+    beta[k] = c1[k] * (c1[k] - 2.0 * c2[k]) + (16.0 / 3.0) * c2[k] * c2[k];
+  }
+  const double s02 = dabs(beta[0] - beta[2], beta[0] + beta[2]);
+  const double b5 = (beta[0] + 4.0 * beta[1] + beta[2]) * (1.0 / 6.0) + fabs(beta[0] - beta[2]);
+  double sk[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sk[k] = dabs(b5 - beta[k], b5 + beta[k]);
+  const double tau = (fabs(b5 - beta[0]) + fabs(b5 - beta[1]) + fabs(b5 - beta[2])) * (1.0 / 3.0);
+  const double e5 = b5 + T.eps;
+  const double w5 = T.d5 * (1.0 + tau * tau / (e5 * e5));
+  double e[3], w3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    e[k] = beta[k] + T.eps;
+    w3[k] = T.d3[k] * (1.0 + tau * tau / (e[k] * e[k]));
+  }
+  const double inv = 1.0 / (w5 + w3[0] + w3[1] + w3[2]);
+  const double g5 = w5 * inv / T.d5;
+  double g3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g3[k] = w3[k] * inv - g5 * T.d3[k];
+  const double W0 = v[0];
+  // P = g5 P5 + sum_k g3_k P3_k,  P5 = W0 + a5 (L5 - W0),  P3_k = W0 + a3_k (u_k - W0)
+  double gb5 = 0.0, gb3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int p = p0 + q;
+    const double L5 = lin_eval<5>(v, vs, T.lin[1][p]);
+    gb5 = fma(pb[q], fma(br.a5, L5 - W0, W0), gb5);
+    const double pb5 = pb[q] * g5;
+    ab[3] = fma(pb5, L5 - W0, ab[3]);
+    lin_vjp<5>(T.lin[1][p], br.a5 * pb5, vbc);
+    vbc[0] = fma(1.0 - br.a5, pb5, vbc[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double* vk = v + (k - 2) * vs;
+      const double u = T.sub[k][p][0] * vk[0] + T.sub[k][p][1] * vk[vs] + T.sub[k][p][2] * vk[2 * vs];
+      gb3[k] = fma(pb[q], fma(br.a3[k], u - W0, W0), gb3[k]);
+      const double pb3 = pb[q] * g3[k];
+      ab[k] = fma(pb3, u - W0, ab[k]);
+      const double a = br.a3[k] * pb3;
+      vbc[k - 2] = fma(T.sub[k][p][0], a, vbc[k - 2]);
+      vbc[k - 1] = fma(T.sub[k][p][1], a, vbc[k - 1]);
+      vbc[k] = fma(T.sub[k][p][2], a, vbc[k]);
+      vbc[0] = fma(1.0 - br.a3[k], pb3, vbc[0]);
+    }
+  }
+  // g3_k = w3_k inv - g5 d3_k,  g5 = w5 inv / d5,  inv = 1 / (w5 + sum w3)
+  double wb3[3], invb = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    wb3[k] = gb3[k] * inv;
+    invb = fma(gb3[k], w3[k], invb);
+    gb5 -= gb3[k] * T.d3[k];
+  }
+  double wb5 = gb5 * inv / T.d5;
+  invb += gb5 * w5 / T.d5;
+  const double Sb = -invb * inv * inv;
+  wb5 += Sb;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) wb3[k] += Sb;
+  // w = d (1 + tau^2 / (beta + eps)^2)
+  double taub = wb5 * T.d5 * 2.0 * tau / (e5 * e5);
+  double b5b = -wb5 * T.d5 * 2.0 * tau * tau / (e5 * e5 * e5);
+  double betab[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    taub += wb3[k] * T.d3[k] * 2.0 * tau / (e[k] * e[k]);
+    betab[k] = -wb3[k] * T.d3[k] * 2.0 * tau * tau / (e[k] * e[k] * e[k]);
+  }
+  // tau = (|b5 - beta_0| + |b5 - beta_1| + |b5 - beta_2|) / 3
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    b5b += taub * sk[k] * (1.0 / 3.0);
+    betab[k] -= taub * sk[k] * (1.0 / 3.0);
+  }
+  // b5 = (beta_0 + 4 beta_1 + beta_2) / 6 + |beta_0 - beta_2|
+  betab[0] += b5b * (1.0 / 6.0 + s02);
+  betab[1] += b5b * (4.0 / 6.0);
+  betab[2] += b5b * (1.0 / 6.0 - s02);
+  // beta = c1^2 - 2 c1 c2 + (16/3) c2^2
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double c1b = betab[k] * (2.0 * c1[k] - 2.0 * c2[k]);
+    const double c2b = betab[k] * (-2.0 * c1[k] + (32.0 / 3.0) * c2[k]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) vbc[k - 2 + j] += T.cq[k][0][j] * c1b + T.cq[k][1][j] * c2b;
+  }
+}
+
+// VJP of recon_eval<R, NP> (points p0 .. p0+NP-1).
+template <int R, int NP>
+__device__ __forceinline__ void recon_vjp(const double* v, int vs, const Branch& br, const Tables& T, int p0,
+                                          const double* pb, double* vbc, double* ab) {
+  if (br.m == R) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) lin_vjp<R>(T.lin[(R - 3) / 2][p0 + q], pb[q], vbc);
+    return;
+  }
+  if (R == 3) {  // DF-damped order 3: W0 + a (lin3 - W0)
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const double l3 = lin_eval<3>(v, vs, T.lin[0][p0 + q]);
+      ab[3] = fma(pb[q], l3 - v[0], ab[3]);
+      lin_vjp<3>(T.lin[0][p0 + q], br.a5 * pb[q], vbc);
+      vbc[0] = fma(1.0 - br.a5, pb[q], vbc[0]);
+    }
+    return;
+  }
+  if (R >= 9 && br.m == 7) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) lin_vjp<(R >= 7 ? 7 : 3)>(T.lin[2][p0 + q], pb[q], vbc);
+    return;
+  }
+  if (R >= 7 && br.m == 5) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) lin_vjp<5>(T.lin[1][p0 + q], pb[q], vbc);
+    return;
+  }
+  if (R >= 5) weno_vjp<NP>(v, vs, br, T, p0, pb, vbc, ab);
+}
+
+// Adjoints of the four face strengths sigma_{-3/2}, sigma_{-1/2}, sigma_{1/2}, sigma_{3/2}
+// of a stencil (sb[0..3]) from the alpha adjoints ab.  alpha = thres / A where
+// A >= thres (Eq. 3.2), so d alpha / d A = -alpha^2 / thres; alpha = 1 elsewhere.
+template <int R>
+__device__ __forceinline__ void sigma_vjp(const Branch& br, const double* ab, double thres, double* sb) {
+  sb[0] = sb[1] = sb[2] = sb[3] = 0.0;
+  if (R == 3) {
+    if (br.m == -3) {
+      const double Ab = -ab[3] * br.a5 * br.a5 / thres;  // A = sigma_{-1/2} + sigma_{1/2}
+      sb[1] = Ab;
+      sb[2] = Ab;
+    }
+    return;
+  }
+  if (br.m != 0) return;
+  const double A5b = -ab[3] * br.a5 * br.a5 / thres;
+  double A3b[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) A3b[k] = (br.a3[k] < 1.0) ? -ab[k] * br.a3[k] * br.a3[k] / thres : 0.0;
+  // A3_{-1} = s_{-3/2} + s_{-1/2}, A3_0 = s_{-1/2} + s_{1/2}, A3_1 = s_{1/2} + s_{3/2}, A5 = all four
+  sb[0] = A3b[0] + A5b;
+  sb[1] = A3b[0] + A3b[1] + A5b;
+  sb[2] = A3b[1] + A3b[2] + A5b;
+  sb[3] = A3b[2] + A5b;
+}
+
+// ---------------------------------------------------------------------------------
+// Lax-Friedrichs point VJP (the derivative of lf_point)
+// ---------------------------------------------------------------------------------
+struct SidePrim {
+  double rho, u, w, p, c, E;
+};
+
+template <int C, int NI, int TI>
+__device__ __forceinline__ SidePrim side_prim(const double* q, double gamma) {
+  SidePrim s;
+  s.rho = q[0];
+  const double ir = 1.0 / q[0];
+  s.u = q[NI] * ir;
+  s.w = (C == 4) ? q[TI] * ir : 0.0;
+  s.E = q[C - 1];
+  s.p = (gamma - 1.0) * (s.E - 0.5 * q[0] * (s.u * s.u + s.w * s.w));
+  s.c = sqrt(gamma * s.p * ir);
+  return s;
+}
+
+// Adjoints of the primitives (u, w, p, c) -> adjoint of the conservative state (+=),
+// with p = (gamma-1)(E - |m|^2 / (2 rho)), u = m_n / rho, w = m_t / rho,
+// c = sqrt(gamma p / rho).
+template <int C, int NI, int TI>
+__device__ __forceinline__ void side_back(const SidePrim& s, double gamma, double ub, double wb, double pb,
+                                          double cb, double* qb) {
+  const double ir = 1.0 / s.rho;
+  pb += cb * gamma * ir / (2.0 * s.c);
+  double rb = -cb * s.c * 0.5 * ir;
+  const double g1 = gamma - 1.0;
+  qb[C - 1] += g1 * pb;
+  qb[NI] -= g1 * pb * s.u;
+  if (C == 4) qb[TI] -= g1 * pb * s.w;
+  rb += g1 * pb * 0.5 * (s.u * s.u + s.w * s.w);
+  qb[NI] += ub * ir;
+  rb -= ub * s.u * ir;
+  if (C == 4) {
+    qb[TI] += wb * ir;
+    rb -= wb * s.w * ir;
+  }
+  qb[0] += rb;
+}
+
+// Given F2b (adjoint of 2F, the value lf_point returns) and sb (adjoint of sigma),
+// accumulates the adjoints of the two reconstructed states, or, where the point took
+// the first-order states, of the two cell averages.
+template <int C, int NI, int TI>
+__device__ void lf_point_vjp(const double* qa, const double* qb_, const double* ca, const double* cb, double gamma,
+                             const double* F2b, double sb, double* qab, double* qbb, double* cab, double* cbb) {
+  double mmL = qa[NI] * qa[NI], mmR = qb_[NI] * qb_[NI];
+  if (C == 4) {
+    mmL = fma(qa[TI], qa[TI], mmL);
+    mmR = fma(qb_[TI], qb_[TI], mmR);
+  }
+  const double prL = (gamma - 1.0) * fma(qa[C - 1], qa[0], -0.5 * mmL);
+  const double prR = (gamma - 1.0) * fma(qb_[C - 1], qb_[0], -0.5 * mmR);
+  const bool ok = (qa[0] > 0.0) && (qb_[0] > 0.0) && (prL > 0.0) && (prR > 0.0) && isfinite(prL) &&
+                  isfinite(prR);
+  double a[C], b[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    a[c] = ok ? qa[c] : ca[c];
+    b[c] = ok ? qb_[c] : cb[c];
+  }
+  double ab_[C], bb_[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) ab_[c] = bb_[c] = 0.0;
+  const SidePrim L = side_prim<C, NI, TI>(a, gamma);
+  const SidePrim R = side_prim<C, NI, TI>(b, gamma);
+  const double sL = fabs(L.u) + L.c, sR = fabs(R.u) + R.c;
+  const double lam = fmax(sL, sR);
+  // share of d lam going to the left / right speed
+  double tL = (sL < sR) ? 0.0 : 1.0;
+  if (fabs(sL - sR) <= kKink * (sL + sR)) tL = 0.5;
+  const double tR = 1.0 - tL;
+  // 2F = F(a) + F(b) - lam (b - a)
+  double lamb = 0.0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    lamb -= F2b[c] * (b[c] - a[c]);
+    ab_[c] += lam * F2b[c];
+    bb_[c] -= lam * F2b[c];
+  }
+  // F(q) = (m_n, m_n u + p, m_n w, u (E + p)) in the face frame
+  double uLb = F2b[NI] * a[NI] + F2b[C - 1] * (L.E + L.p);
+  double uRb = F2b[NI] * b[NI] + F2b[C - 1] * (R.E + R.p);
+  double pLb = F2b[NI] + F2b[C - 1] * L.u;
+  double pRb = F2b[NI] + F2b[C - 1] * R.u;
+  double wLb = 0.0, wRb = 0.0, cLb = 0.0, cRb = 0.0;
+  ab_[NI] += F2b[0] + F2b[NI] * L.u;
+  bb_[NI] += F2b[0] + F2b[NI] * R.u;
+  if (C == 4) {
+    ab_[NI] += F2b[TI] * L.w;
+    bb_[NI] += F2b[TI] * R.w;
+    wLb += F2b[TI] * a[NI];
+    wRb += F2b[TI] * b[NI];
+  }
+  ab_[C - 1] += F2b[C - 1] * L.u;
+  bb_[C - 1] += F2b[C - 1] * R.u;
+  // lam = max(|u_L| + c_L, |u_R| + c_R), piecewise
+  uLb += tL * lamb * dabs(L.u, L.c);
+  cLb += tL * lamb;
+  uRb += tR * lamb * dabs(R.u, R.c);
+  cRb += tR * lamb;
+  // sigma = |pL - pR| (1/pL + 1/pR) + (uL/cL - uR/cR)^2 + (wL/cL - wR/cR)^2; constant
+  // (1e30) at a first-order point
+  if (ok && sb != 0.0) {
+    const double dp = L.p - R.p;
+    const double sg = dabs(dp, L.p + R.p);
+    const double adp = fabs(dp);
+    const double h = 1.0 / L.p + 1.0 / R.p;
+    pLb += sb * (sg * h - adp / (L.p * L.p));
+    pRb += sb * (-sg * h - adp / (R.p * R.p));
+    const double dmn = L.u / L.c - R.u / R.c;
+    uLb += sb * 2.0 * dmn / L.c;
+    uRb -= sb * 2.0 * dmn / R.c;
+    cLb -= sb * 2.0 * dmn * L.u / (L.c * L.c);
+    cRb += sb * 2.0 * dmn * R.u / (R.c * R.c);
+    if (C == 4) {
+      const double dmt = L.w / L.c - R.w / R.c;
+      wLb += sb * 2.0 * dmt / L.c;
+      wRb -= sb * 2.0 * dmt / R.c;
+      cLb -= sb * 2.0 * dmt * L.w / (L.c * L.c);
+      cRb += sb * 2.0 * dmt * R.w / (R.c * R.c);
+    }
+  }
+  side_back<C, NI, TI>(L, gamma, uLb, wLb, pLb, cLb, ab_);
+  side_back<C, NI, TI>(R, gamma, uRb, wRb, pRb, cRb, bb_);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    if (ok) {
+      qab[c] += ab_[c];
+      qbb[c] += bb_[c];
+    } else {
+      cab[c] += ab_[c];
+      cbb[c] += bb_[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// boundary preimages
+// ---------------------------------------------------------------------------------
+// Cells x in [xlo, xhi] that the ghost map (periodic wrap / clamp) sends to cell i.
+__device__ __forceinline__ int cell_preimages(int i, int n, int bl, int bh, int xlo, int xhi, int* xs) {
+  constexpr int cap = 16;
+  int cnt = 0;
+  if (i >= xlo && i <= xhi) xs[cnt++] = i;
+  if (bl == BC_PERIODIC) {
+    for (int x = i - n; x >= xlo && cnt < cap; x -= n) xs[cnt++] = x;
+  } else if (i == 0) {
+    for (int x = -1; x >= xlo && cnt < cap; --x) xs[cnt++] = x;
+  }
+  if (bh == BC_PERIODIC) {
+    for (int x = i + n; x <= xhi && cnt < cap; x += n) xs[cnt++] = x;
+  } else if (i == n - 1) {
+    for (int x = n; x <= xhi && cnt < cap; ++x) xs[cnt++] = x;
+  }
+  return cnt;
+}
+
+// Faces f in [flo, fhi] that face_map sends to face e (0 <= e <= n).
+__device__ __forceinline__ int face_preimages(int e, int n, int bl, int bh, int flo, int fhi, int* fs) {
+  constexpr int cap = 16;
+  int cnt = 0;
+  if (e >= flo && e <= fhi) fs[cnt++] = e;
+  if (bl == BC_PERIODIC) {
+    if (e < n)
+      for (int f = e - n; f >= flo && cnt < cap; f -= n) fs[cnt++] = f;
+  } else if (e == 0) {
+    for (int f = -1; f >= flo && cnt < cap; --f) fs[cnt++] = f;
+  }
+  if (bh == BC_PERIODIC) {
+    if (e < n)
+      for (int f = e + n; f <= fhi && cnt < cap; f += n)
+        if (f > n) fs[cnt++] = f;
+  } else if (e == n) {
+    for (int f = n + 1; f <= fhi && cnt < cap; ++f) fs[cnt++] = f;
+  }
+  return cnt;
+}
+
+// ---------------------------------------------------------------------------------
+// K1: face kernel
+// ---------------------------------------------------------------------------------
+template <int R, int DIM, int DIR>
+__global__ void __launch_bounds__(Tile<R, DIM>::NT, 1)
+adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const __grid_constant__ Tables T) {
+  using TL = Tile<R, DIM>;
+  constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
+  constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
+  constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
+  constexpr int NI = (DIR == 0) ? 1 : 2;
+  constexpr int TI = (DIR == 0) ? 2 : 1;
+  constexpr int NTAP = 2 * KT + 1;
+
+  extern __shared__ double smem[];
+  double* sW = smem;
+  double* sQP = sW + C * NB * NA;
+  double* sQM = sQP + C * NB * NQ;
+  double* sSn = sQM + C * NB * NQ;
+  double* sSt = sSn + NB * NSN;
+
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const int a0 = blockIdx.x * TN, b0 = blockIdx.y * TT;
+  const int tid = threadIdx.x;
+  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
+  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+
+  // ---- stage the tile as the forward sweep does ----
+  for (int idx = tid; idx < C * NB * NA; idx += NT) {
+    int c, bb, ai;
+    if (DIR == 0) { ai = idx % NA; bb = (idx / NA) % NB; c = idx / (NA * NB); }
+    else { bb = idx % NB; ai = (idx / NB) % NA; c = idx / (NA * NB); }
+    const int a = a0 - 1 - K + ai, b = b0 - KT + bb;
+    const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
+    sW[(c * NB + bb) * NA + ai] = fetch_w(g, args.W, c, i, j);
+  }
+  for (int idx = tid; idx < NB * NSN; idx += NT) {
+    const int fa = idx % NSN, bb = idx / NSN;
+    const int f = face_map(a0 - K + fa, n, bcn_lo, bcn_hi);
+    const int b = wrap_or_clamp(b0 - KT + bb, mlin, bct_lo, bct_hi);
+    sSn[bb * NSN + fa] = (DIR == 0) ? args.s_norm[(size_t)b * (g.nx + 1) + f] : args.s_norm[(size_t)f * g.nx + b];
+  }
+  if (DIM == 2) {
+    for (int idx = tid; idx < NQ * (NST - 1); idx += NT) {
+      const int qa = idx % NQ, fb = idx / NQ;
+      const int a = wrap_or_clamp(a0 - 1 + qa, n, bcn_lo, bcn_hi);
+      const int f = face_map(b0 - K + 1 + fb, mlin, bct_lo, bct_hi);
+      sSt[qa * NST + fb] = (DIR == 0) ? args.s_tan[(size_t)f * g.nx + a] : args.s_tan[(size_t)a * (g.nx + 1) + f];
+    }
+  }
+  __syncthreads();
+  for (int it = tid; it < NQ * NB; it += NT) {
+    const int qa = it % NQ, bb = it / NQ;
+    const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const double* v = sW + (c * NB + bb) * NA + qa + K;
+      double out[2];
+      recon_eval<R, 2>(v, 1, br, T, 0, out);
+      sQP[(c * NB + bb) * NQ + qa] = out[0];
+      sQM[(c * NB + bb) * NQ + qa] = out[1];
+    }
+  }
+  __syncthreads();
+
+  // ---- per face: recompute the Gauss-point states, back-propagate ----
+  const size_t nfaces = (size_t)(n + 1) * mlin;
+  const double fscale = aa.lscale * aa.inv_h;
+  for (int it = tid; it < TN * TT; it += NT) {
+    int fa, tb;
+    if (DIR == 0) { fa = it % TN; tb = it / TN; }
+    else { tb = it % TT; fa = it / TT; }
+    const int f = a0 + fa, b = b0 + tb;
+    if (f > n || b >= mlin) continue;
+    const size_t face = (size_t)b * (n + 1) + f;
+    // F_f enters L of cell f with +1/h and L of cell f-1 with -1/h
+    double Fb[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      double lb = 0.0;
+      if (aa.Lbar) {
+        if (f < n)
+          lb += (DIR == 0) ? aa.Lbar[((size_t)c * g.ny + b) * g.nx + f] : aa.Lbar[((size_t)c * g.ny + f) * g.nx + b];
+        if (f >= 1)
+          lb -= (DIR == 0) ? aa.Lbar[((size_t)c * g.ny + b) * g.nx + f - 1]
+                           : aa.Lbar[((size_t)c * g.ny + f - 1) * g.nx + b];
+      }
+      Fb[c] = lb * fscale;
+    }
+    double sbar = 0.0;
+    if (aa.sbar_out)
+      sbar = ((DIR == 0) ? aa.sbar_out[(size_t)b * (g.nx + 1) + f] : aa.sbar_out[(size_t)f * g.nx + b]) * (1.0 / G);
+    double st[2][G][C];
+    Branch bt[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int qa = fa + side;
+      const double* Q = side == 0 ? sQP : sQM;
+      if (DIM == 2) {
+        bt[side] = select_branch<R>(sSt + qa * NST + tb, g.thres);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          double out[G];
+          recon_eval<R, G>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt[side], T, 2, out);
+#pragma unroll
+          for (int q = 0; q < G; ++q) st[side][q][c] = out[q];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) st[side][0][c] = Q[c * NQ + qa];
+      }
+    }
+    double ca[C], cb[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      ca[c] = sW[(c * NB + tb + KT) * NA + fa + K];
+      cb[c] = sW[(c * NB + tb + KT) * NA + fa + K + 1];
+    }
+    double stb[2][G][C], cab[C], cbb[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      cab[c] = cbb[c] = 0.0;
+#pragma unroll
+      for (int q = 0; q < G; ++q) stb[0][q][c] = stb[1][q][c] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      double F2b[C];
+      const double hw = (DIM == 2) ? T.hgw[q] : 0.5;
+#pragma unroll
+      for (int c = 0; c < C; ++c) F2b[c] = hw * Fb[c];
+      lf_point_vjp<C, NI, TI>(st[0][q], st[1][q], ca, cb, g.gamma, F2b, sbar, stb[0][q], stb[1][q], cab, cbb);
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int qa = fa + side;
+      const double* Q = side == 0 ? sQP : sQM;
+      double ab[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        double vb[NTAP];
+#pragma unroll
+        for (int t = 0; t < NTAP; ++t) vb[t] = 0.0;
+        if (DIM == 2) {
+          double pb[G];
+#pragma unroll
+          for (int q = 0; q < G; ++q) pb[q] = stb[side][q][c];
+          recon_vjp<R, G>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt[side], T, 2, pb, vb + KT, ab);
+        } else {
+          vb[0] = stb[side][0][c];
+        }
+#pragma unroll
+        for (int t = 0; t < NTAP; ++t) aa.Tbar[((size_t)((side * NTAP + t) * C + c)) * nfaces + face] = vb[t];
+      }
+      if (DIM == 2) {
+        double sb[4];
+        sigma_vjp<R>(bt[side], ab, g.thres, sb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) aa.Stb[(size_t)(side * 4 + q) * nfaces + face] = sb[q];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      aa.Cbar[(size_t)c * nfaces + face] = cab[c];
+      aa.Cbar[(size_t)(C + c) * nfaces + face] = cbb[c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// K2: normal VJP per reconstructing cell (a in [-1, n], line l in [-KT, m+KT))
+// ---------------------------------------------------------------------------------
+template <int R, int DIM, int DIR>
+__global__ void __launch_bounds__(256) adj_normal_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa,
+                                                         const __grid_constant__ Tables T) {
+  constexpr int K = (R - 1) / 2, C = (DIM == 1) ? 3 : 4, KT = (DIM == 2) ? K : 0;
+  constexpr int NTAP = 2 * KT + 1, NS = 2 * K + 1;
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
+  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+  const size_t nfaces = (size_t)(n + 1) * mlin;
+  const int na = n + 2, nl = mlin + 2 * KT;
+  const size_t nitems = (size_t)na * nl;
+  for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(it % na) - 1;
+    const int l = (int)(it / na) - KT;
+    // adjoints of the plus (xi = 0) and minus (xi = -1) values of cell (a, l): the
+    // plus value is the left state of face a+1, the minus value the right state of face
+    // a, each read by the tangential stencils of the face lines b = l - t
+    double QPb[C], QMb[C];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < C; ++c) QPb[c] = QMb[c] = 0.0;
+#pragma unroll
+    for (int t = -KT; t <= KT; ++t) {
+      const int b = l - t;
+      if (b < 0 || b >= mlin) continue;
+      if (a + 1 <= n) {
+        const size_t face = (size_t)b * (n + 1) + (a + 1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) QPb[c] += aa.Tbar[((size_t)((0 * NTAP + t + KT) * C + c)) * nfaces + face];
+        any = true;
+      }
+      if (a >= 0) {
+        const size_t face = (size_t)b * (n + 1) + a;
+#pragma unroll
+        for (int c = 0; c < C; ++c) QMb[c] += aa.Tbar[((size_t)((1 * NTAP + t + KT) * C + c)) * nfaces + face];
+        any = true;
+      }
+    }
+    double* out = aa.Nbar + it;  // [m][c][item]
+    if (!any) {
+#pragma unroll
+      for (int m = 0; m < NS; ++m)
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[((size_t)(m * C + c)) * nitems] = 0.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) aa.Snb[(size_t)q * nitems + it] = 0.0;
+      continue;
+    }
+    // branch of cell (a, l) from the normal faces of its (mapped) line
+    double s[2 * K];
+    const int lm = wrap_or_clamp(l, mlin, bct_lo, bct_hi);
+#pragma unroll
+    for (int q = 0; q < 2 * K; ++q) {
+      const int f = face_map(a - K + 1 + q, n, bcn_lo, bcn_hi);
+      s[q] = (DIR == 0) ? args.s_norm[(size_t)lm * (g.nx + 1) + f] : args.s_norm[(size_t)f * g.nx + lm];
+    }
+    const Branch br = select_branch<R>(s, g.thres);
+    double ab[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      double v[NS], vb[NS];
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        const int x = a - K + m;
+        v[m] = (DIR == 0) ? fetch_w(g, args.W, c, x, l) : fetch_w(g, args.W, c, l, x);
+        vb[m] = 0.0;
+      }
+      const double pb[2] = {QPb[c], QMb[c]};
+      recon_vjp<R, 2>(v + K, 1, br, T, 0, pb, vb + K, ab);
+#pragma unroll
+      for (int m = 0; m < NS; ++m) out[((size_t)(m * C + c)) * nitems] = vb[m];
+    }
+    double sb[4];
+    sigma_vjp<R>(br, ab, g.thres, sb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) aa.Snb[(size_t)q * nitems + it] = sb[q];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// K3: gather into Wbar (per interior cell)
+// ---------------------------------------------------------------------------------
+template <int R, int DIM, int DIR>
+__global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, const AdjArgs aa) {
+  constexpr int K = (R - 1) / 2, C = (DIM == 1) ? 3 : 4, KT = (DIM == 2) ? K : 0;
+  constexpr int NS = 2 * K + 1;
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
+  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+  const size_t nfaces = (size_t)(n + 1) * mlin;
+  const int na = n + 2;
+  const size_t nitems = (size_t)na * (mlin + 2 * KT);
+  const size_t ncell = (size_t)g.nx * g.ny;
+  for (size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x; cell < ncell;
+       cell += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(cell % g.nx), cj = (int)(cell / g.nx);
+    const int i = (DIR == 0) ? ci : cj;  // along the sweep
+    const int j = (DIR == 0) ? cj : ci;  // line
+    int xs[16], ls[16];
+    const int nxs = cell_preimages(i, n, bcn_lo, bcn_hi, -K - 1, n + K, xs);
+    int nls = 1;
+    ls[0] = j;
+    if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
+    double acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.0;
+    for (int il = 0; il < nls; ++il) {
+      const int l = ls[il];
+      for (int ix = 0; ix < nxs; ++ix) {
+        const int x = xs[ix];
+        // inflow ghost cells hold the constant inflow state
+        const int gi = (DIR == 0) ? x : l, gj = (DIR == 0) ? l : x;
+        if (gi < 0 && g.bc[0] == BC_INFLOW_BAND && gj >= g.band_j0 && gj <= g.band_j1) continue;
+#pragma unroll
+        for (int m = 0; m < NS; ++m) {
+          const int a = x - (m - K);
+          if (a < -1 || a > n) continue;
+          const size_t item = (size_t)(l + KT) * na + (a + 1);
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[c] += aa.Nbar[((size_t)(m * C + c)) * nitems + item];
+        }
+        // first-order states: face x+1 has this cell on its left, face x on its right
+        if (l >= 0 && l < mlin) {
+          if (x + 1 >= 0 && x + 1 <= n) {
+            const size_t face = (size_t)l * (n + 1) + (x + 1);
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] += aa.Cbar[(size_t)c * nfaces + face];
+          }
+          if (x >= 0 && x <= n) {
+            const size_t face = (size_t)l * (n + 1) + x;
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] += aa.Cbar[(size_t)(C + c) * nfaces + face];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) aa.Wbar[(size_t)c * ncell + cell] += acc[c];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// K4: gather of the normal-face sigma_in adjoints (per entry of this direction's
+// normal sigma array)
+// ---------------------------------------------------------------------------------
+template <int R, int DIM, int DIR>
+__global__ void __launch_bounds__(256) adj_gather_sn_kernel(const GridInfo g, const AdjArgs aa) {
+  constexpr int K = (R - 1) / 2, KT = (DIM == 2) ? K : 0;
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
+  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+  const int na = n + 2;
+  const size_t nitems = (size_t)na * (mlin + 2 * KT);
+  const size_t nent = (size_t)(n + 1) * mlin;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nent;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int e, j;
+    if (DIR == 0) { e = (int)(idx % (g.nx + 1)); j = (int)(idx / (g.nx + 1)); }  // sx[j][e]
+    else { j = (int)(idx % g.nx); e = (int)(idx / g.nx); }                       // sy[e][j]
+    int fs[16], ls[16];
+    const int nfs = face_preimages(e, n, bcn_lo, bcn_hi, -2, n + 2, fs);
+    int nls = 1;
+    ls[0] = j;
+    if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
+    double acc = 0.0;
+    for (int il = 0; il < nls; ++il) {
+      const size_t row = (size_t)(ls[il] + KT) * na;
+      for (int k = 0; k < nfs; ++k) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int a = fs[k] + 1 - q;  // the cell whose stencil face q (face a-1+q) is f
+          if (a < -1 || a > n) continue;
+          acc += aa.Snb[(size_t)q * nitems + row + (a + 1)];
+        }
+      }
+    }
+    aa.sbar_norm[idx] += acc;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// K5: gather of the tangential-face sigma_in adjoints (2D)
+// ---------------------------------------------------------------------------------
+template <int R, int DIR>
+__global__ void __launch_bounds__(256) adj_gather_st_kernel(const GridInfo g, const AdjArgs aa) {
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
+  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+  const size_t nfaces = (size_t)(n + 1) * mlin;
+  const size_t nent = (size_t)(mlin + 1) * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nent;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int te, i;
+    if (DIR == 0) { i = (int)(idx % g.nx); te = (int)(idx / g.nx); }            // sy[te][i]
+    else { te = (int)(idx % (g.nx + 1)); i = (int)(idx / (g.nx + 1)); }         // sx[i][te]
+    int xs[16], tfs[16];
+    const int nxs = cell_preimages(i, n, bcn_lo, bcn_hi, -1, n, xs);
+    const int ntf = face_preimages(te, mlin, bct_lo, bct_hi, -1, mlin + 1, tfs);
+    double acc = 0.0;
+    for (int side = 0; side < 2; ++side) {
+      for (int ix = 0; ix < nxs; ++ix) {
+        const int f = xs[ix] + 1 - side;  // the face whose side-`side` column is x
+        if (f < 0 || f > n) continue;
+        for (int k = 0; k < ntf; ++k) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int b = tfs[k] + 1 - q;
+            if (b < 0 || b >= mlin) continue;
+            acc += aa.Stb[(size_t)(side * 4 + q) * nfaces + (size_t)b * (n + 1) + f];
+          }
+        }
+      }
+    }
+    aa.sbar_tan[idx] += acc;
+  }
+}
+
+inline int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)); }
+
+template <int R, int DIM, int DIR>
+cudaError_t adj_launch(const GridInfo& g, const SweepArgs& a, const AdjArgs& aa, const Tables& t, cudaStream_t s) {
+  using TL = Tile<R, DIM>;
+  const size_t smem = TL::smem_doubles * sizeof(double);
+  auto k1 = adj_face_kernel<R, DIM, DIR>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int m = (DIR == 0) ? g.ny : g.nx;
+  dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
+  k1<<<grid, TL::NT, smem, s>>>(g, a, aa, t);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t nitems = (size_t)(n + 2) * (m + 2 * TL::KT);
+  adj_normal_kernel<R, DIM, DIR><<<grid_for(nitems), 256, 0, s>>>(g, a, aa, t);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  adj_gather_w_kernel<R, DIM, DIR><<<grid_for((size_t)g.nx * g.ny), 256, 0, s>>>(g, aa);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (aa.sbar_norm) {
+    adj_gather_sn_kernel<R, DIM, DIR><<<grid_for((size_t)(n + 1) * m), 256, 0, s>>>(g, aa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (DIM == 2 && aa.sbar_tan) {
+    adj_gather_st_kernel<R, DIR><<<grid_for((size_t)(m + 1) * n), 256, 0, s>>>(g, aa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+#define ASE_DF_CAT2(a, b) a##b
+#define ASE_DF_CAT(a, b) ASE_DF_CAT2(a, b)
+
+cudaError_t ASE_DF_CAT(launch_adjoint_r, ASE_DF_ORDER)(int dim, int dir, const GridInfo& g, const SweepArgs& a,
+                                                       const AdjArgs& aa, const Tables& t, cudaStream_t s) {
+  constexpr int R = ASE_DF_ORDER;
+  if (dim == 1) return adj_launch<R, 1, 0>(g, a, aa, t, s);
+  if (dir == 0) return adj_launch<R, 2, 0>(g, a, aa, t, s);
+  return adj_launch<R, 2, 1>(g, a, aa, t, s);
+}
+
+}  // namespace asedf

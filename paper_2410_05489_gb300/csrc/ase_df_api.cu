@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ase_df.h"
+#include "ase_df_adjoint.cuh"
 #include "ase_df_internal.cuh"
 
 using namespace asedf;
@@ -28,6 +30,10 @@ struct ase_df_ctx {
   double *zsx, *zsy;        // zero sigma (priming)
   unsigned char* mark;      // per-cell marks of the positivity repair
   DevState* st;
+  // adjoint scratch (allocated by the first adjoint call)
+  double* adj;              // per-direction kernel scratch (adj_scratch_doubles)
+  double *Ab1, *Ab2, *Abn;  // stage adjoints of the SSP-RK3 step adjoint
+  double *s0bx, *s0by, *s1bx, *s1by, *s2bx, *s2by;  // sigma adjoints of the stages
   // CUDA graph of one step (ase_df_run)
   cudaGraphExec_t graph_exec;
   double* g_W;
@@ -226,7 +232,8 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
 void ase_df_destroy(ase_df_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  double* ptrs[] = {c->Fx, c->Fy, c->W1, c->W2, c->sxa, c->sya, c->sxb, c->syb, c->zsx, c->zsy};
+  double* ptrs[] = {c->Fx,  c->Fy,  c->W1,   c->W2,   c->sxa,  c->sya,  c->sxb,  c->syb,  c->zsx, c->zsy,
+                    c->adj, c->Ab1, c->Ab2,  c->Abn,  c->s0bx, c->s0by, c->s1bx, c->s1by, c->s2bx, c->s2by};
   for (double* q : ptrs)
     if (q) cudaFree(q);
   if (c->st) cudaFree(c->st);
@@ -452,6 +459,151 @@ ase_df_status ase_df_run(ase_df_ctx* c, double* W, double* sx, double* sy, doubl
     cudaError_t e = cudaGraphLaunch(c->graph_exec, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
   }
+  return ASE_DF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------------
+static ase_df_status ensure_adjoint(ase_df_ctx* c) {
+  if (c->adj) return ASE_DF_OK;
+  const GridInfo& g = c->g;
+  size_t nadj = adj_scratch_doubles(c->dim, c->p.order, g.nx, g.ny);
+  if (c->dim == 2) nadj = std::max(nadj, adj_scratch_doubles(c->dim, c->p.order, g.ny, g.nx));
+  const size_t nW = (size_t)c->C * g.nx * g.ny;
+  const size_t nsx = (size_t)g.ny * (g.nx + 1);
+  const size_t nsy = (c->dim == 2) ? (size_t)(g.ny + 1) * g.nx : 1;
+  struct { double** ptr; size_t n; } allocs[] = {
+    {&c->adj, nadj}, {&c->Ab1, nW}, {&c->Ab2, nW}, {&c->Abn, nW}, {&c->s0bx, nsx}, {&c->s0by, nsy},
+    {&c->s1bx, nsx}, {&c->s1by, nsy}, {&c->s2bx, nsx}, {&c->s2by, nsy},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc((void**)a.ptr, a.n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& b : allocs) {
+        if (*b.ptr) cudaFree(*b.ptr);
+        *b.ptr = nullptr;
+      }
+      return fail(c, ASE_DF_E_NOMEM, "device allocation of %zu bytes of adjoint scratch failed", a.n * sizeof(double));
+    }
+  }
+  return ASE_DF_OK;
+}
+
+// Wbar += J_W^T (lscale Lbar) + ..., sbi += J_sigma^T ... for both directions.
+static cudaError_t residual_adjoint(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
+                                    const double* Lbar, double lscale, const double* sbo_x, const double* sbo_y,
+                                    double* Wbar, double* sbi_x, double* sbi_y, cudaStream_t s) {
+  const GridInfo& g = c->g;
+  const int K = c->K, KT = (c->dim == 2) ? K : 0, C = c->C;
+  for (int dir = 0; dir < c->dim; ++dir) {
+    const size_t n = (dir == 0) ? g.nx : g.ny, m = (dir == 0) ? g.ny : g.nx;
+    const size_t nf = (n + 1) * m, ni = (n + 2) * (m + 2 * KT);
+    AdjArgs aa;
+    aa.Lbar = Lbar;
+    aa.lscale = lscale;
+    aa.sbar_out = (dir == 0) ? sbo_x : sbo_y;
+    aa.Tbar = c->adj;
+    aa.Cbar = aa.Tbar + (size_t)2 * (2 * KT + 1) * C * nf;
+    aa.Stb = aa.Cbar + (size_t)2 * C * nf;
+    aa.Nbar = aa.Stb + (c->dim == 2 ? 8 * nf : 0);
+    aa.Snb = aa.Nbar + (size_t)(2 * K + 1) * C * ni;
+    aa.Wbar = Wbar;
+    aa.sbar_norm = (dir == 0) ? sbi_x : sbi_y;
+    aa.sbar_tan = (c->dim == 2) ? ((dir == 0) ? sbi_y : sbi_x) : nullptr;
+    aa.inv_h = (dir == 0) ? c->inv_dx : c->inv_dy;
+    SweepArgs a;
+    a.W = W;
+    a.s_norm = (dir == 0) ? sx : sy;
+    a.s_tan = (dir == 0) ? sy : sx;
+    a.F = nullptr;
+    a.s_out = nullptr;
+    a.st = c->st;
+    cudaError_t e;
+    switch (c->p.order) {
+      case 3: e = launch_adjoint_r3(c->dim, dir, g, a, aa, c->tab, s); break;
+      case 5: e = launch_adjoint_r5(c->dim, dir, g, a, aa, c->tab, s); break;
+      case 7: e = launch_adjoint_r7(c->dim, dir, g, a, aa, c->tab, s); break;
+      default: e = launch_adjoint_r9(c->dim, dir, g, a, aa, c->tab, s); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+extern "C" {
+
+ase_df_status ase_df_residual_adjoint(ase_df_ctx* c, const double* W, const double* sx_in, const double* sy_in,
+                                      const double* Lbar, const double* sxbar_out, const double* sybar_out,
+                                      double* Wbar, double* sxbar_in, double* sybar_in, void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx_in, sy_in);
+  if (r != ASE_DF_OK) return r;
+  if (!Wbar) return fail(c, ASE_DF_E_INVAL, "Wbar is NULL");
+  if (Wbar == W || Wbar == Lbar || (sxbar_in && (sxbar_in == sx_in || sxbar_in == sxbar_out)) ||
+      (c->dim == 2 && sybar_in && (sybar_in == sy_in || sybar_in == sybar_out)))
+    return fail(c, ASE_DF_E_INVAL, "adjoint outputs must not alias the inputs");
+  if ((r = ensure_adjoint(c)) != ASE_DF_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  cudaError_t e = residual_adjoint(c, W, sx_in, sy_in, Lbar, 1.0, sxbar_out, c->dim == 2 ? sybar_out : nullptr,
+                                   Wbar, sxbar_in, c->dim == 2 ? sybar_in : nullptr, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual adjoint");
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_step_adjoint(ase_df_ctx* c, const double* W, const double* sx, const double* sy, double dt,
+                                  double* Wbar, double* sxbar, double* sybar, void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx, sy);
+  if (r != ASE_DF_OK) return r;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ASE_DF_E_INVAL, "the step adjoint needs a fixed dt > 0");
+  if (!Wbar || !sxbar || (c->dim == 2 && !sybar)) return fail(c, ASE_DF_E_INVAL, "NULL adjoint pointer");
+  if (Wbar == W || sxbar == sx || (c->dim == 2 && sybar == sy))
+    return fail(c, ASE_DF_E_INVAL, "adjoint arrays must not alias the state");
+  if ((r = ensure_adjoint(c)) != ASE_DF_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  const GridInfo& g = c->g;
+  const size_t nW = (size_t)c->C * g.nx * g.ny;
+  const size_t nsx = (size_t)g.ny * (g.nx + 1);
+  const size_t nsy = (c->dim == 2) ? (size_t)(g.ny + 1) * g.nx : 0;
+  double* sybar_ = (c->dim == 2) ? sybar : nullptr;
+  double* s0by = (c->dim == 2) ? c->s0by : nullptr;
+  double* s1by = (c->dim == 2) ? c->s1by : nullptr;
+  double* s2by = (c->dim == 2) ? c->s2by : nullptr;
+  cudaError_t e;
+  // stages 1 and 2 of the forward step: W1, sigma1 (sxa, sya), W2, sigma2 (sxb, syb)
+  if ((e = face_fluxes(c, W, sx, sy, c->sxa, c->sya, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 1 sweep");
+  if ((e = combine(c, 1, W, W, c->W1, dt, s, c->sxa, c->sya)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 1 combine");
+  if ((e = face_fluxes(c, c->W1, c->sxa, c->sya, c->sxb, c->syb, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 2 sweep");
+  if ((e = combine(c, 2, W, c->W1, c->W2, dt, s, c->sxb, c->syb)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 2 combine");
+  // stage 3: W^{n+1} = W^n / 3 + 2/3 W2 + 2/3 dt L(W2, sigma2), sigma3 = sigma_out(W2, sigma2)
+  e = launch_axpby(c->Abn, 1.0 / 3.0, Wbar, 0.0, nullptr, nW, s);
+  if (e == cudaSuccess) e = launch_axpby(c->Ab2, 2.0 / 3.0, Wbar, 0.0, nullptr, nW, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->s2bx, 0, nsx * sizeof(double), s);
+  if (e == cudaSuccess && nsy) e = cudaMemsetAsync(c->s2by, 0, nsy * sizeof(double), s);
+  if (e == cudaSuccess)
+    e = residual_adjoint(c, c->W2, c->sxb, c->syb, Wbar, 2.0 / 3.0 * dt, sxbar, sybar_, c->Ab2, c->s2bx, s2by, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 3");
+  // stage 2: W2 = 3/4 W^n + 1/4 W1 + 1/4 dt L(W1, sigma1), sigma2 = sigma_out(W1, sigma1)
+  e = launch_axpby(c->Abn, 1.0, c->Abn, 0.75, c->Ab2, nW, s);
+  if (e == cudaSuccess) e = launch_axpby(c->Ab1, 0.25, c->Ab2, 0.0, nullptr, nW, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->s1bx, 0, nsx * sizeof(double), s);
+  if (e == cudaSuccess && nsy) e = cudaMemsetAsync(c->s1by, 0, nsy * sizeof(double), s);
+  if (e == cudaSuccess)
+    e = residual_adjoint(c, c->W1, c->sxa, c->sya, c->Ab2, 0.25 * dt, c->s2bx, s2by, c->Ab1, c->s1bx, s1by, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 2");
+  // stage 1: W1 = W^n + dt L(W^n, sigma^n), sigma1 = sigma_out(W^n, sigma^n)
+  e = launch_axpby(c->Abn, 1.0, c->Abn, 1.0, c->Ab1, nW, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->s0bx, 0, nsx * sizeof(double), s);
+  if (e == cudaSuccess && nsy) e = cudaMemsetAsync(c->s0by, 0, nsy * sizeof(double), s);
+  if (e == cudaSuccess) e = residual_adjoint(c, W, sx, sy, c->Ab1, dt, c->s1bx, s1by, c->Abn, c->s0bx, s0by, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 1");
+  e = cudaMemcpyAsync(Wbar, c->Abn, nW * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sxbar, c->s0bx, nsx * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && nsy) e = cudaMemcpyAsync(sybar, c->s0by, nsy * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint: copy out");
   return ASE_DF_OK;
 }
 

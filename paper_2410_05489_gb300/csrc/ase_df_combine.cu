@@ -21,6 +21,7 @@
 
 #include <cuda_runtime.h>
 
+#include "ase_df_adjoint.cuh"
 #include "ase_df_combine_body.cuh"
 
 namespace asedf {
@@ -62,6 +63,13 @@ __global__ void state_kernel(DevState* st, int op, double t) {
   }
 }
 
+// out = a x + b y (the linear combinations of the SSP-RK3 adjoint)
+__global__ void __launch_bounds__(256) axpby_kernel(double* out, double a, const double* x, double b,
+                                                    const double* y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = y ? fma(b, y[i], a * x[i]) : a * x[i];
+}
+
 int grid_for(size_t n, int threads) {
   size_t b = (n + threads - 1) / threads;
   const size_t cap = 152 * 8;
@@ -97,6 +105,12 @@ cudaError_t launch_max_speed(int dim, const GridInfo& g, const SpeedArgs& a, cud
   const size_t ncell = (size_t)g.nx * g.ny;
   if (dim == 1) max_speed_kernel<1><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
   else max_speed_kernel<2><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y, size_t n,
+                         cudaStream_t s) {
+  axpby_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, a, x, b, y, n);
   return cudaGetLastError();
 }
 
