@@ -273,6 +273,13 @@ const char* ase_df_batch_last_error(const ase_df_batch* b);
  * *fma_per_s (flops = 2x).  Synchronises the device. */
 ase_df_status ase_df_fp64_fma_rate(double* fma_per_s);
 
+/* Check of the face kernel's own FP64 reciprocal and reciprocal square root (an FP32
+ * approximation refined by one third-order Newton-Raphson step; the paper has no
+ * counterpart): for the n device doubles x[i] writes out[4i .. 4i+3] = (own 1/x, CUDA's
+ * 1/x, own 1/sqrt(x), CUDA's rsqrt(x)).  out holds 4n device doubles.  Asynchronous on
+ * stream. */
+ase_df_status ase_df_check_recip(const double* x, double* out, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

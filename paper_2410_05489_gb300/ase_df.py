@@ -77,6 +77,7 @@ def _load():
                                      _c.POINTER(_c.c_uint64)], _c.c_int),
         "ase_df_last_error": ([CTX], _c.c_char_p),
         "ase_df_fp64_fma_rate": ([_c.POINTER(_c.c_double)], _c.c_int),
+        "ase_df_check_recip": ([_VP, _VP, _c.c_int64, _VP], _c.c_int),
         "ase_df_profile_enable": ([CTX, _c.c_int32], _c.c_int),
         "ase_df_profile_read": ([CTX, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64)], _c.c_int),
     }
@@ -208,6 +209,10 @@ def ase_df_profile_read(ctx):
     n = (_c.c_int64 * 5)()
     _check(ctx, _load().ase_df_profile_read(ctx, ms, n))
     return list(ms), list(n)
+
+
+def ase_df_check_recip(x, out, stream=None) -> None:
+    _check(None, _load().ase_df_check_recip(_ptr(x), _ptr(out), int(x.numel()), _stream(stream)))
 
 
 def ase_df_fp64_fma_rate() -> float:

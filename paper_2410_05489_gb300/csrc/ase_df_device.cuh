@@ -12,6 +12,73 @@ namespace {
 
 constexpr double kSigmaBig = 1e30;  // sigma of a Gauss point that took first-order states
 
+// ---------------------------------------------------------------------------------
+// FP64-pipe economy.  This part issues FP64 at 2 lanes per cycle per SM and the face
+// kernel is bound by that pipe, so comparisons whose outcome the bit patterns fix run
+// as integer operations, and the reciprocal and reciprocal square root of the flux
+// start from an FP32 approximation (XU pipe) refined by one FP64 step of order three.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// x > 0 and finite: sign bit clear, not +0, exponent field not all ones (so false for
+// NaN, +-0, negative values and +inf), as (x > 0 && isfinite(x)).
+__device__ __forceinline__ bool pos_finite(double x) {
+  const long long b = dbits(x);
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
+
+// a < t for a threshold t > 0: non-negative values (and +NaN) order like their bit
+// patterns, and negative values (and -0) have the sign bit set and compare below.
+// Equals (a < t) except for a NaN with the sign bit set.
+__device__ __forceinline__ bool lt_pos(double a, double t) { return dbits(a) < dbits(t); }
+
+// max of two non-negative values, by bit pattern
+__device__ __forceinline__ double max_nonneg(double a, double b) { return dbits(a) < dbits(b) ? b : a; }
+
+// 1/x for x > 0 with biased exponent in [3, 2044] (otherwise the division).  Seed: the
+// FP32 reciprocal approximation of the leading 23 mantissa bits (x scaled into [1, 2)),
+// relative error below 2^-22.  Then one step of the third-order Newton-Raphson
+// (Householder) iteration for 1/x: with e = 1 - x y0, 1/x = y0 / (1 - e) =
+// y0 (1 + e + e^2 + ...), so y1 = y0 + y0 (e + e^2), error O(e^3) < 2^-64 before the
+// final rounding.
+__device__ __forceinline__ double rcp_pos(double x) {
+  const long long b = dbits(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (b <= 0 || ex < 3 || ex > 2044) return 1.0 / x;
+  const unsigned fb = 0x3f800000u | (unsigned)((b >> 29) & 0x7fffff);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__uint_as_float(fb)));
+  // r ~ 1/m in [1/2, 1]; 1/x = r 2^(1023 - ex)
+  const unsigned rb = __float_as_uint(r);
+  const long long er = (long long)((rb >> 23) & 0xffu) - 127 + 1023 + (1023 - ex);
+  const double y0 = __longlong_as_double((er << 52) | ((long long)(rb & 0x7fffffu) << 29));
+  const double e = fma(-x, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+
+// 1/sqrt(x) for x > 0 normal and finite (otherwise rsqrt()).  Seed: the FP32 rsqrt
+// approximation of x scaled by an even power of two into [1, 4).  Then one third-order
+// step: with r = 1 - x y0^2, 1/sqrt(x) = y0 (1 - r)^(-1/2) = y0 (1 + r/2 + 3 r^2 / 8 + ...),
+// so y1 = y0 + y0 r (1/2 + 3 r / 8), error O(r^3) < 2^-62 before rounding.
+__device__ __forceinline__ double rsqrt_pos(double x) {
+  const long long b = dbits(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (b <= 0 || ex < 1 || ex > 2046) return rsqrt(x);
+  const int e = ex - 1023;   // x = 1.f 2^e
+  const int par = e & 1;     // e = 2k + par
+  const int k = (e - par) >> 1;
+  const unsigned fb = ((unsigned)(127 + par) << 23) | (unsigned)((b >> 29) & 0x7fffff);
+  float sf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(__uint_as_float(fb)));
+  // sf ~ 1/sqrt(m) in [1/2, 1]; 1/sqrt(x) = sf 2^-k
+  const unsigned sb = __float_as_uint(sf);
+  const long long es = (long long)((sb >> 23) & 0xffu) - 127 + 1023 - k;
+  const double y0 = __longlong_as_double((es << 52) | ((long long)(sb & 0x7fffffu) << 29));
+  const double h = x * y0;
+  const double r = fma(-h, y0, 1.0);
+  return fma(y0 * r, fma(r, 0.375, 0.5), y0);
+}
+
 __device__ __forceinline__ int wrap_or_clamp(int i, int n, int bc_lo, int bc_hi) {
   if (i < 0) {
     if (bc_lo == BC_PERIODIC) { int m = i % n; return m < 0 ? m + n : m; }
@@ -65,8 +132,7 @@ __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, con
   }
   double prL = gm1 * fma(qa[C - 1], qa[0], -0.5 * mmL);
   double prR = gm1 * fma(qb[C - 1], qb[0], -0.5 * mmR);
-  const bool ok = (qa[0] > 0.0) && (qb[0] > 0.0) && (prL > 0.0) && (prR > 0.0) && isfinite(prL) &&
-                  isfinite(prR);
+  const bool ok = pos_finite(qa[0]) && pos_finite(qb[0]) && pos_finite(prL) && pos_finite(prR);
   double a[C], b[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -85,16 +151,16 @@ __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, con
   }
   const double rr = a[0] * b[0];
   const double pp = prL * prR;
-  const double inv = 1.0 / (rr * pp);
+  const double inv = rcp_pos(rr * pp);
   const double irr = pp * inv;       // 1 / (rho_l rho_r)
   const double irL = b[0] * irr;     // 1 / rho_l
   const double irR = a[0] * irr;     // 1 / rho_r
   const double unL = a[NI] * irL, unR = b[NI] * irR;
   const double pL = prL * irL, pR = prR * irR;
   const double c2L = gamma * pL * irL, c2R = gamma * pR * irR;
-  const double icL = rsqrt(c2L), icR = rsqrt(c2R);
+  const double icL = rsqrt_pos(c2L), icR = rsqrt_pos(c2R);
   const double cL = c2L * icL, cR = c2R * icR;
-  const double lam = fmax(fabs(unL) + cL, fabs(unR) + cR);
+  const double lam = max_nonneg(fabs(unL) + cL, fabs(unR) + cR);
   double FL[C], FR[C];
   FL[0] = a[NI];
   FR[0] = b[NI];

@@ -32,28 +32,28 @@ __device__ __forceinline__ Branch select_branch(const double* s, double thres) {
   const double sm12 = s[K - 1], sp12 = s[K];  // sigma_{-1/2}, sigma_{1/2}
   if (R == 3) {
     const double A = sm12 + sp12;
-    if (A < thres) { b.m = 3; } else { b.m = -3; b.a5 = thres / A; }
+    if (lt_pos(A, thres)) { b.m = 3; } else { b.m = -3; b.a5 = thres / A; }
     return b;
   }
   const double sm32 = s[K - 2], sp32 = s[K + 1];
   const double A5 = (sm32 + sm12) + (sp12 + sp32);
-  if (!(A5 < thres)) {
+  if (!lt_pos(A5, thres)) {
     b.m = 0;
     const double A3m = sm32 + sm12, A30 = sm12 + sp12, A3p = sp12 + sp32;
-    b.a3[0] = A3m < thres ? 1.0 : thres / A3m;
-    b.a3[1] = A30 < thres ? 1.0 : thres / A30;
-    b.a3[2] = A3p < thres ? 1.0 : thres / A3p;
+    b.a3[0] = lt_pos(A3m, thres) ? 1.0 : thres / A3m;
+    b.a3[1] = lt_pos(A30, thres) ? 1.0 : thres / A30;
+    b.a3[2] = lt_pos(A3p, thres) ? 1.0 : thres / A3p;
     b.a5 = thres / A5;
     return b;
   }
   b.m = 5;
   if (R >= 7) {
     const double A7 = A5 + (s[K - 3] + s[K + 2]);
-    if (A7 < thres) {
+    if (lt_pos(A7, thres)) {
       b.m = 7;
       if (R >= 9) {
         const double A9 = A7 + (s[K - 4] + s[K + 3]);
-        if (A9 < thres) b.m = 9;
+        if (lt_pos(A9, thres)) b.m = 9;
       }
     }
   }
