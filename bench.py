@@ -353,7 +353,7 @@ def batched_bench(A, torch, args):
     bt.run(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ksteps = max(2, args.steps // 4)
+    ksteps = max(2, min(10, args.steps // 4))
     e0.record()
     bt.run(ksteps)
     e1.record()
@@ -526,10 +526,159 @@ def run_reference(args, world, rank):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------------
+# --suite: every configuration of the workload list, GPU and CPU oracle side by side
+# ----------------------------------------------------------------------------------
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_rows_parallel(O, pb, W, sx, sy, threads):
+    """One residual evaluation by the oracle with the rows split over `threads` host
+    threads (each runs the serial code on its rows; the C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    blocks = [b for b in np.array_split(np.arange(pb.nyc), threads) if len(b)]
+    with ThreadPoolExecutor(len(blocks)) as ex:
+        list(ex.map(lambda b: O.residual_rows(pb, W, sx, sy, int(b[0]), int(b[-1])), blocks))
+
+
+def _cpu_rates(O, pb, W, sx, sy, cores):
+    t0 = time.perf_counter()
+    O.residual(pb, W, sx, sy)
+    t1 = time.perf_counter()
+    _oracle_rows_parallel(O, pb, W, sx, sy, cores)
+    t2 = time.perf_counter()
+    return ({"value": round(pb.ncells / (t1 - t0) / 1e6, 4), "cores": 1},
+            {"value": round(pb.ncells / (t2 - t1) / 1e6, 4), "cores": cores})
+
+
+def suite_bench(args):
+    """GPU throughput, roofline fraction and the CPU oracle (one core and all cores) for
+    the Sod tube, the vortex at orders 5/7/9, the jet, the batched set and the adjoint."""
+    import torch
+
+    from oracle import oracle as O
+    from paper_2410_05489_gb300 import ase_df as A
+    from paper_2410_05489_gb300 import build
+
+    build.build()
+    O.build()
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    cores = _cores()
+    rows = []
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # Sod: 200 cells, r = 5, to t = 0.2 (the whole run, CFL steps)
+    pb, W0 = P.sod(200, 5)
+    t0 = time.perf_counter()
+    _, _, _, t_end, nsteps = O.run(pb, W0, t_end=0.2)
+    cpu_s = time.perf_counter() - t0
+    s = A.Solver(pb, W0, t_end=0.2)
+    s.run(nsteps)
+    torch.cuda.synchronize()
+    s.set_state(W0)
+    e0, e1 = ev(), ev()
+    e0.record()
+    s.run(nsteps)
+    e1.record()
+    e1.synchronize()
+    gms = e0.elapsed_time(e1)
+    flags, _, t_gpu = s.status()
+    s.close()
+    rows.append({"config": "Sod 1D, 200 cells, r=5, to t=0.2 (%d CFL steps)" % nsteps,
+                 "gpu": {"value": round(pb.ncells * 3 * nsteps / (gms * 1e-3) / 1e6, 3), "ms_run": round(gms, 3),
+                         "t_end": t_gpu, "flags": flags,
+                         "note": "launch-bound: 200 cells per stage; the whole run is one graph per step"},
+                 "cpu_1core": {"value": round(pb.ncells * 3 * nsteps / cpu_s / 1e6, 4), "cores": 1},
+                 "cpu_all_cores": {"value": None, "cores": cores, "note": "one row: nothing to split"}})
+
+    # vortex 1024^2 at r = 5, 7, 9 (GPU), oracle on 256^2
+    for r in (5, 7, 9):
+        pb, W0 = P.isentropic_vortex(1024, r)
+        ms, prof, flags = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush, profile=True)
+        value = pb.ncells * 3 * args.steps / (ms * 1e-3) / 1e6
+        sweep_ms, sweep_n = prof[0][0] + prof[0][1], prof[1][0] + prof[1][1]
+        faces = 0.5 * ((pb.nx + 1) * pb.ny + (pb.ny + 1) * pb.nx)
+        achieved = algorithmic_flops_per_face(2, r) * faces / (sweep_ms / sweep_n * 1e-3) / 1e12
+        peak = 2.0 * 2.0 * n_sm * 2070.0e6 / 1e12
+        pbc, Wc = P.isentropic_vortex(256, r)
+        c1, ca = _cpu_rates(O, pbc, Wc, *P.zero_sigma(pbc), cores)
+        rows.append({"config": "vortex 2D 1024^2, r=%d (oracle: one stage at 256^2)" % r,
+                     "gpu": {"value": round(value, 3), "ms_per_step": round(ms / args.steps, 4), "flags": flags},
+                     "roofline_frac": round(achieved / peak, 4), "hbm_frac":
+                         round(value * 1e6 * HBM_BYTES_PER_CELL_STAGE_2D / 1e9 / 6694.8, 5),
+                     "cpu_1core": c1, "cpu_all_cores": ca})
+
+    # jet 1600 x 800, r = 9: 20 CFL steps from t = 0
+    pb, W0 = P.high_mach_jet(1600, 800, 9)
+    ms, _, flags = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush)
+    value = pb.ncells * 3 * args.steps / (ms * 1e-3) / 1e6
+    sx, sy = P.zero_sigma(pb)
+    lo, hi = 368, 431
+    t0 = time.perf_counter()
+    O.residual_rows(pb, W0, sx, sy, lo, hi)
+    band = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _oracle_rows_parallel(O, pb, W0, sx, sy, cores)
+    full = time.perf_counter() - t0
+    rows.append({"config": "jet 2D 1600x800, r=9, %d CFL steps after %d warm-up steps from t=0" % (args.steps, args.warmup),
+                 "gpu": {"value": round(value, 3), "ms_per_step": round(ms / args.steps, 4), "flags": flags},
+                 "cpu_1core": {"value": round(pb.nx * (hi - lo + 1) / band / 1e6, 4), "cores": 1,
+                               "sample": "one stage of rows %d..%d of the initial state, sigma = 0" % (lo, hi)},
+                 "cpu_all_cores": {"value": round(pb.ncells / full / 1e6, 4), "cores": cores,
+                                   "sample": "one stage of the whole initial state, sigma = 0"}})
+
+    # batched set (GPU) and a seeded subset of it (oracle, one CFL step per problem)
+    b = batched_bench(A, torch, args)
+    probs = P.batched_problems()[:16]
+    t0 = time.perf_counter()
+    for pb, W in probs:
+        O.step(pb, W, *O.prime_sigma(pb, W))
+    one = time.perf_counter() - t0
+    from concurrent.futures import ThreadPoolExecutor
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(min(cores, len(probs))) as ex:
+        list(ex.map(lambda pw: O.step(pw[0], pw[1], *O.prime_sigma(pw[0], pw[1])), probs))
+    allc = time.perf_counter() - t0
+    sub_cells = sum(pb.ncells for pb, _ in probs)
+    rows.append({"config": "batched: 512 problems, 18.0 M cells (oracle: the first 16 problems, priming + one step)",
+                 "gpu": {"value": b["value"], "ms_per_step": b["ms_per_step"],
+                         "one_problem_per_launch": b["one_problem_per_launch"], "speedup": b["speedup"]},
+                 "cpu_1core": {"value": round(sub_cells * 4 / one / 1e6, 4), "cores": 1},
+                 "cpu_all_cores": {"value": round(sub_cells * 4 / allc / 1e6, 4), "cores": min(cores, len(probs))}})
+
+    # adjoint: GPU ratios, and the oracle tape's reverse/forward ratio on a 32^2 sample
+    a = adjoint_bench(A, torch, args)
+    pb, W0 = P.isentropic_vortex(32, 7)
+    W0 = W0.copy()
+    W0[0] *= 1.0 + 0.01 * np.random.default_rng(1).uniform(-1.0, 1.0, W0[0].shape)
+    dt = O.cfl_dt(pb, W0)
+    t0 = time.perf_counter()
+    Wf = O.run(pb, W0, nsteps=2, dt=dt)[0]
+    fwd = time.perf_counter() - t0
+    Wbf = np.zeros_like(Wf)
+    Wbf[0] = 2.0 * Wf[0]
+    t0 = time.perf_counter()
+    O.run_vjp(pb, W0, 2, dt, Wbf)
+    rev = time.perf_counter() - t0
+    rows.append({"config": "adjoint: vortex 256^2 + 1% density noise, r=7, 50 steps, checkpoints every 10",
+                 "gpu": {k: a[k] for k in ("forward_ms", "backward_ms", "plain_forward_ms", "backward_over_forward",
+                                           "gradient_over_plain_forward", "residual_adjoint_over_residual")},
+                 "cpu_1core": {"tape_over_forward": round(rev / fwd, 2), "cores": 1,
+                               "sample": "oracle tape (reverse mode incl. taping) vs plain oracle, 32^2, 2 steps"}})
+    print(json.dumps({"suite": rows, "cores": cores}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=N_GRID)
@@ -538,11 +687,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--suite", action="store_true",
+                    help="measure every workload configuration (GPU and CPU oracle) instead of the headline line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.suite:
+        if rank == 0:
+            suite_bench(args)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)
