@@ -201,6 +201,14 @@ double Zq(int q, double xi) {
   return p - mean;
 }
 
+// dZ_q / dxi = q xi^(q-1) (the mean is a constant).
+double Zq_d(int q, double xi) {
+  if (q == 0) return 0.0;
+  double p = (double)q;
+  for (int i = 0; i < q - 1; ++i) p *= xi;
+  return p;
+}
+
 // ---------------------------------------------------------------------------------
 // Coefficient tables of Sec. 3.2-3.4 as the paper prints them (with readings G2-G4).
 // Row q-1 gives W_xq = (sum_m num[m+4] * W_m) / den, m = -4..4.
@@ -256,6 +264,13 @@ real eval_linear(const CoefRow* rows, int nrows, const real* Wm, double xi) {
   return P;
 }
 
+// dP/dxi of the same polynomial.
+real eval_linear_d(const CoefRow* rows, int nrows, const real* Wm, double xi) {
+  real P = real(0.0);
+  for (int q = 1; q <= nrows; ++q) P += coef(rows[q - 1], Wm) * real(Zq_d(q, xi));
+  return P;
+}
+
 // Sec. 3.1, Eq. (3.2): DF factor of a stencil from the summed face strengths A.
 real df_alpha(real A, double thres) {
   if (A < real(thres)) return real(1.0);  // reading G12
@@ -296,7 +311,7 @@ const double kEps = 1e-6;
 // force_linear_weights replaces the normalised nonlinear weights by the linear ones
 // (used only by the tests of the AO identity).
 void weno_ao53_df(const real* Wm, const real* alpha, int npts, const double* xi, real* out,
-                  bool force_linear_weights, real* beta_out) {
+                  bool force_linear_weights, real* beta_out, real* dout = nullptr) {
   real a1[3], a2[3];
   for (int k = 0; k < 3; ++k) {
     a1[k] = coef(kS3[k][0], Wm);
@@ -349,6 +364,18 @@ void weno_ao53_df(const real* Wm, const real* alpha, int npts, const double* xi,
     real P = wb5 * inner;
     for (int k = 0; k < 3; ++k) P += wb3[k] * P3[k];
     out[p] = P;
+    if (dout) {  // the weights do not depend on xi: the same combination of the derivatives
+      real dP3[3];
+      for (int k = 0; k < 3; ++k)
+        dP3[k] = alpha[k] * (a1[k] * real(Zq_d(1, x)) + a2[k] * real(Zq_d(2, x)));
+      real dP5 = alpha[3] * (b[0] * real(Zq_d(1, x)) + b[1] * real(Zq_d(2, x)) +
+                             b[2] * real(Zq_d(3, x)) + b[3] * real(Zq_d(4, x)));
+      real dinner = dP5 / real(d5);
+      for (int k = 0; k < 3; ++k) dinner = dinner - (real(d3[k]) / real(d5)) * dP3[k];
+      real dP = wb5 * dinner;
+      for (int k = 0; k < 3; ++k) dP += wb3[k] * dP3[k];
+      dout[p] = dP;
+    }
   }
 }
 
@@ -363,21 +390,24 @@ enum {
 // Algorithm 1 capped at the scheme order r (reading G13) for one cell and one
 // component.  Wm[m+4] = W_m (m = -k..k, others unused), sig[m+3] = sigma_{m-1/2}.
 // Evaluates the chosen polynomial at npts points xi[] into out[]; returns the branch.
+// dout (optional) receives dP/dxi of the chosen polynomial at the same points.
 int ase_df_reconstruct(int r, const real* Wm, const real* sig, double thres, int npts,
-                       const double* xi, real* out) {
+                       const double* xi, real* out, real* dout = nullptr) {
   StencilSums A = stencil_sums(sig);
   if (r == 3) {  // reading G20
     real a = df_alpha(A.s30, thres);
     real a1 = coef(kS3[1][0], Wm), a2 = coef(kS3[1][1], Wm);
-    for (int p = 0; p < npts; ++p)
+    for (int p = 0; p < npts; ++p) {
       out[p] = Wm[4] + a * (a1 * real(Zq(1, xi[p])) + a2 * real(Zq(2, xi[p])));
+      if (dout) dout[p] = a * (a1 * real(Zq_d(1, xi[p])) + a2 * real(Zq_d(2, xi[p])));
+    }
     return (A.s30 < real(thres)) ? BR_LIN3 : BR_DF3;
   }
   if (!(A.s5 < real(thres))) {
     // alpha_S5 < 1: WENOZ-AO(5,3) with DF
     real alpha[4] = {df_alpha(A.s3m, thres), df_alpha(A.s30, thres), df_alpha(A.s3p, thres),
                      df_alpha(A.s5, thres)};
-    weno_ao53_df(Wm, alpha, npts, xi, out, false, nullptr);
+    weno_ao53_df(Wm, alpha, npts, xi, out, false, nullptr, dout);
     return BR_WENO;
   }
   int m = 5;
@@ -386,7 +416,10 @@ int ase_df_reconstruct(int r, const real* Wm, const real* sig, double thres, int
     if (r >= 9 && A.s9 < real(thres)) m = 9;
   }
   const CoefRow* rows = (m == 5) ? kS5 : (m == 7) ? kS7 : kS9;
-  for (int p = 0; p < npts; ++p) out[p] = eval_linear(rows, m - 1, Wm, xi[p]);
+  for (int p = 0; p < npts; ++p) {
+    out[p] = eval_linear(rows, m - 1, Wm, xi[p]);
+    if (dout) dout[p] = eval_linear_d(rows, m - 1, Wm, xi[p]);
+  }
   return (m == 5) ? BR_LIN5 : (m == 7) ? BR_LIN7 : BR_LIN9;
 }
 
@@ -556,8 +589,10 @@ Grid make_grid(const OracleParams* p) {
 // face i-1/2).  Fills out[c] for all components; returns the branch of component 0
 // (the branch does not depend on the component).
 // ---------------------------------------------------------------------------------
+// dout (optional) receives dP/dxi of the reconstructing polynomial at that face (xi along
+// the mirrored stencil's axis when to_right is false).
 int normal_recon(const Grid& g, const real* Wd, const real* sig_n, int dir, int64_t i,
-                 int64_t j, bool to_right, real* out) {
+                 int64_t j, bool to_right, real* out, real* dout = nullptr) {
   const int r = g.p->order;
   const int k = (r - 1) / 2;
   const int s = to_right ? 1 : -1;  // mirrored stencil: W'_m = W_{-m}
@@ -583,7 +618,7 @@ int normal_recon(const Grid& g, const real* Wd, const real* sig_n, int dir, int6
       if (m < -k || m > k) continue;
       Wm[m + 4] = (dir == 0) ? g.W(Wd, c, i + s * m, j) : g.W(Wd, c, i, j + s * m);
     }
-    branch = ase_df_reconstruct(r, Wm, sig, g.p->sigma_thres, 1, &xi0, &out[c]);
+    branch = ase_df_reconstruct(r, Wm, sig, g.p->sigma_thres, 1, &xi0, &out[c], dout ? &dout[c] : nullptr);
   }
   return branch;
 }
@@ -592,16 +627,18 @@ int normal_recon(const Grid& g, const real* Wd, const real* sig_n, int dir, int6
 // tangential stencil) at the G Gauss points, with the tangential face strengths
 // sigt[m+3] of the reconstructing cell's column / row.
 int tangential_recon(const Grid& g, const real Q[9][4], const real* sigt, int G,
-                     const double* eta, real out[4][4]) {
+                     const double* eta, real out[4][4], real (*dout)[4] = nullptr) {
   const int r = g.p->order;
   const int k = (r - 1) / 2;
   int branch = 0;
   for (int c = 0; c < g.C; ++c) {
     real Wm[9];
     for (int m = -4; m <= 4; ++m) Wm[m + 4] = (m < -k || m > k) ? real(0.0) : Q[m + k][c];
-    real vals[4];
-    branch = ase_df_reconstruct(r, Wm, sigt, g.p->sigma_thres, G, eta, vals);
+    real vals[4], dvals[4];
+    branch = ase_df_reconstruct(r, Wm, sigt, g.p->sigma_thres, G, eta, vals, dout ? dvals : nullptr);
     for (int q = 0; q < G; ++q) out[q][c] = vals[q];
+    if (dout)
+      for (int q = 0; q < G; ++q) dout[q][c] = dvals[q];
   }
   return branch;
 }
@@ -1146,6 +1183,444 @@ void oracle_reset_op_counts() { g_ops = {0, 0, 0, 0}; }
 #endif
 
 }  // extern "C"
+
+#if !defined(ORACLE_TAPE) && !defined(ORACLE_COUNT_OPS)
+// =================================================================================
+// Gas-kinetic flux (Sec. 2.2 with Appendix A) and the two-stage fourth-order time
+// stepping S2O4 (Sec. 2.2): the paper's primary solver.  Plain double build only.
+//
+// At a Gauss point, in the face frame (u normal, v tangential), the time integral over
+// [0, delta] of the flux of the distribution function of Eq. (GKS flux) with the
+// physical collision time tau = 0 (reading G25) is
+//   F(delta) = c1 rho_c <u psi>_c + c2 rho_c <u (a_x^c u + a_y^c v) psi>_c
+//            + c3 rho_c <u A^c psi>_c
+//            + c4 (rho_l <u psi>_{l,u>0} + rho_r <u psi>_{r,u<0})
+//            - c2 (rho_l <u (a_x^l u + a_y^l v) psi>_{l,u>0} + rho_r <...>_{r,u<0})
+// with, for e = exp(-delta / tau_n),
+//   c1 = delta - tau_n (1 - e)      (time integral of 1 - exp(-t/tau_n))
+//   c2 = tau_n^2 (1 - e) - tau_n delta e   (of t exp(-t/tau_n))
+//   c3 = delta^2 / 2                (of t)
+//   c4 = tau_n (1 - e)              (of exp(-t/tau_n)).
+// g_l, g_r are the Maxwellians of the two reconstructed states, g_c the one of the
+// kinetic-weighted state W_c = rho_l <psi>_{l,u>0} + rho_r <psi>_{r,u<0} (Sec. 3.5), the
+// slopes a come from <a psi psi^T> = W_x / rho (Appendix A, M a = b), those of g_c from
+// the kinetic-weighted derivatives, and A^c from the compatibility condition
+// <a_x u + a_y v + A> = 0.  From F(dt) and F(dt/2) the linear-in-time flux F + t F_t
+// follows (Sec. 2.2): F = (4 F(dt/2) - F(dt)) / dt, F_t = 4 (F(dt) - 2 F(dt/2)) / dt^2.
+// tau_n = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt (reading G24: C1 = 0.01, C2 = 1).
+// =================================================================================
+namespace {
+
+const double kGksC1 = 0.01, kGksC2 = 1.0;
+
+// A monomial c u^a v^b (xi^2)^l of the particle velocity (u, v) and the internal
+// variable (xi^2 = the sum of squares of the K internal components).
+struct Mono { int a, b, l; double c; };
+typedef std::vector<Mono> Poly;
+
+// psi = (1, u, v, (u^2 + v^2 + xi^2) / 2) in 2D; (1, u, (u^2 + xi^2) / 2) in 1D.
+Poly psi(int i, int dim) {
+  if (i == 0) return {{0, 0, 0, 1.0}};
+  if (i == 1) return {{1, 0, 0, 1.0}};
+  if (dim == 2 && i == 2) return {{0, 1, 0, 1.0}};
+  if (dim == 2) return {{2, 0, 0, 0.5}, {0, 2, 0, 0.5}, {0, 0, 1, 0.5}};
+  return {{2, 0, 0, 0.5}, {0, 0, 1, 0.5}};
+}
+Poly mul(const Poly& x, const Poly& y) {
+  Poly r;
+  for (const Mono& p : x)
+    for (const Mono& q : y) r.push_back({p.a + q.a, p.b + q.b, p.l + q.l, p.c * q.c});
+  return r;
+}
+Poly mono(int a, int b) { return {{a, b, 0, 1.0}}; }
+
+// Internal degrees of freedom: gamma = (K + D + 2) / (K + D) with D = 1 or 2
+// (Sec. 2.2: K = (4 - 2 gamma) / (gamma - 1) in 2D; (3 - gamma) / (gamma - 1) in 1D).
+double internal_dof(int dim, double gamma) {
+  return (dim == 2) ? (4.0 - 2.0 * gamma) / (gamma - 1.0) : (3.0 - gamma) / (gamma - 1.0);
+}
+
+// A Maxwellian and its moments (Appendix A): <u^n> over the whole line and the two half
+// lines (from erfc), <v^n>, <xi^0>, <xi^2>, <xi^4>.
+struct Maxwell {
+  double rho, U, V, lam;
+  double u[9], up[9], un[9], v[9], xi[3];
+};
+
+Maxwell maxwell(const double* W, int dim, double gamma) {
+  const double K = internal_dof(dim, gamma);
+  Maxwell m;
+  m.rho = W[0];
+  m.U = W[1] / W[0];
+  m.V = (dim == 2) ? W[2] / W[0] : 0.0;
+  const double E = W[dim + 1];
+  const double p = (gamma - 1.0) * (E - 0.5 * m.rho * (m.U * m.U + m.V * m.V));
+  m.lam = m.rho / (2.0 * p);  // p = rho / (2 lambda)
+  const double l = m.lam;
+  m.u[0] = 1.0;
+  m.u[1] = m.U;
+  m.v[0] = 1.0;
+  m.v[1] = m.V;
+  m.up[0] = 0.5 * std::erfc(-std::sqrt(l) * m.U);
+  m.un[0] = 0.5 * std::erfc(std::sqrt(l) * m.U);
+  const double h = 0.5 * std::exp(-l * m.U * m.U) / std::sqrt(M_PI * l);
+  m.up[1] = m.U * m.up[0] + h;
+  m.un[1] = m.U * m.un[0] - h;
+  for (int n = 0; n + 2 < 9; ++n) {
+    const double s = (n + 1) / (2.0 * l);
+    m.u[n + 2] = m.U * m.u[n + 1] + s * m.u[n];
+    m.up[n + 2] = m.U * m.up[n + 1] + s * m.up[n];
+    m.un[n + 2] = m.U * m.un[n + 1] + s * m.un[n];
+    m.v[n + 2] = m.V * m.v[n + 1] + s * m.v[n];
+  }
+  m.xi[0] = 1.0;
+  m.xi[1] = K / (2.0 * l);
+  m.xi[2] = (K + 2.0) / (2.0 * l) * m.xi[1];
+  return m;
+}
+
+// <poly> of a Maxwellian over all velocities (region 0), u > 0 (1) or u < 0 (-1).
+double moment(const Poly& p, const Maxwell& m, int region) {
+  const double* u = (region == 0) ? m.u : (region > 0) ? m.up : m.un;
+  double s = 0.0;
+  for (const Mono& t : p) s += t.c * u[t.a] * m.v[t.b] * m.xi[t.l];
+  return s;
+}
+
+// x = M^{-1} b for n <= 4 by Gaussian elimination with partial pivoting.
+void solve_small(int n, double M[4][4], const double* b, double* x) {
+  double A[4][5];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) A[i][j] = M[i][j];
+    A[i][n] = b[i];
+  }
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    for (int j = 0; j <= n; ++j) std::swap(A[c][j], A[piv][j]);
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[r][c] / A[c][c];
+      for (int j = c; j <= n; ++j) A[r][j] -= f * A[c][j];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double t = A[i][n];
+    for (int j = i + 1; j < n; ++j) t -= A[i][j] * x[j];
+    x[i] = t / A[i][i];
+  }
+}
+
+// Coefficients a of (dg/dx)/g = a . psi from the derivative dW of the conservative
+// variables: <psi psi^T> a = dW / rho (Appendix A).
+void slope(const Maxwell& m, int dim, const double* dW, double* a) {
+  const int n = dim + 2;
+  double M[4][4], b[4];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) M[i][j] = moment(mul(psi(i, dim), psi(j, dim)), m, 0);
+    b[i] = dW[i] / m.rho;
+  }
+  solve_small(n, M, b, a);
+}
+
+// rho <u^su v^sv (a . psi) psi_i> over a region, i = 0..n-1.
+void slope_flux(const Maxwell& m, int dim, int su, int sv, const double* a, int region, double* out) {
+  const int n = dim + 2;
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += a[j] * moment(mul(mono(su, sv), mul(psi(j, dim), psi(i, dim))), m, region);
+    out[i] = m.rho * s;
+  }
+}
+
+// The GKS flux at one Gauss point (face frame): left / right states, their normal (x)
+// and tangential (y, 2D) derivatives; dt of the step.  Writes F (value at t_n) and F_t.
+void gks_point(int dim, double gamma, const double* Wl, const double* Wlx, const double* Wly,
+               const double* Wr, const double* Wrx, const double* Wry, double dt, double* F,
+               double* Ft) {
+  const int n = dim + 2;
+  const Maxwell gl = maxwell(Wl, dim, gamma), gr = maxwell(Wr, dim, gamma);
+  double alx[4] = {0, 0, 0, 0}, aly[4] = {0, 0, 0, 0}, arx[4] = {0, 0, 0, 0}, ary[4] = {0, 0, 0, 0};
+  slope(gl, dim, Wlx, alx);
+  slope(gr, dim, Wrx, arx);
+  if (dim == 2) {
+    slope(gl, dim, Wly, aly);
+    slope(gr, dim, Wry, ary);
+  }
+  // kinetic-weighted equilibrium state and its derivatives (Sec. 3.5)
+  double Wc[4], Wcx[4], Wcy[4] = {0, 0, 0, 0}, t1[4], t2[4];
+  for (int i = 0; i < n; ++i)
+    Wc[i] = gl.rho * moment(psi(i, dim), gl, 1) + gr.rho * moment(psi(i, dim), gr, -1);
+  slope_flux(gl, dim, 0, 0, alx, 1, t1);
+  slope_flux(gr, dim, 0, 0, arx, -1, t2);
+  for (int i = 0; i < n; ++i) Wcx[i] = t1[i] + t2[i];
+  if (dim == 2) {
+    slope_flux(gl, dim, 0, 0, aly, 1, t1);
+    slope_flux(gr, dim, 0, 0, ary, -1, t2);
+    for (int i = 0; i < n; ++i) Wcy[i] = t1[i] + t2[i];
+  }
+  const Maxwell gc = maxwell(Wc, dim, gamma);
+  double acx[4] = {0, 0, 0, 0}, acy[4] = {0, 0, 0, 0}, Ac[4] = {0, 0, 0, 0};
+  slope(gc, dim, Wcx, acx);
+  if (dim == 2) slope(gc, dim, Wcy, acy);
+  // compatibility: <a_x u + a_y v + A> = 0, i.e. <psi psi^T> A = -(<u a_x psi> + <v a_y psi>)
+  {
+    double bA[4], M[4][4];
+    slope_flux(gc, dim, 1, 0, acx, 0, t1);
+    for (int i = 0; i < n; ++i) bA[i] = -t1[i] / gc.rho;
+    if (dim == 2) {
+      slope_flux(gc, dim, 0, 1, acy, 0, t2);
+      for (int i = 0; i < n; ++i) bA[i] -= t2[i] / gc.rho;
+    }
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) M[i][j] = moment(mul(psi(i, dim), psi(j, dim)), gc, 0);
+    solve_small(n, M, bA, Ac);
+  }
+  // the five flux vectors
+  double T0[4], T1[4], T2[4], T3[4], T4[4];
+  for (int i = 0; i < n; ++i) {
+    T0[i] = gc.rho * moment(mul(mono(1, 0), psi(i, dim)), gc, 0);
+    T3[i] = gl.rho * moment(mul(mono(1, 0), psi(i, dim)), gl, 1) +
+            gr.rho * moment(mul(mono(1, 0), psi(i, dim)), gr, -1);
+  }
+  slope_flux(gc, dim, 2, 0, acx, 0, T1);
+  slope_flux(gc, dim, 1, 0, Ac, 0, T2);
+  {
+    double a1[4], a2[4];
+    slope_flux(gl, dim, 2, 0, alx, 1, a1);
+    slope_flux(gr, dim, 2, 0, arx, -1, a2);
+    for (int i = 0; i < n; ++i) T4[i] = a1[i] + a2[i];
+    if (dim == 2) {
+      double b1[4], b2[4], c1[4];
+      slope_flux(gc, dim, 1, 1, acy, 0, c1);
+      for (int i = 0; i < n; ++i) T1[i] += c1[i];
+      slope_flux(gl, dim, 1, 1, aly, 1, b1);
+      slope_flux(gr, dim, 1, 1, ary, -1, b2);
+      for (int i = 0; i < n; ++i) T4[i] += b1[i] + b2[i];
+    }
+  }
+  // numerical collision time (reading G24) and the time integrals
+  const double pl = (gamma - 1.0) * (Wl[n - 1] - 0.5 * (Wl[1] * Wl[1] + (dim == 2 ? Wl[2] * Wl[2] : 0.0)) / Wl[0]);
+  const double pr = (gamma - 1.0) * (Wr[n - 1] - 0.5 * (Wr[1] * Wr[1] + (dim == 2 ? Wr[2] * Wr[2] : 0.0)) / Wr[0]);
+  const double taun = kGksC1 * dt + kGksC2 * std::fabs((pl - pr) / (pl + pr)) * dt;
+  double Fd[2][4];
+  for (int h = 0; h < 2; ++h) {
+    const double d = (h == 0) ? dt : 0.5 * dt;
+    const double e = std::exp(-d / taun);
+    const double c1 = d - taun * (1.0 - e);
+    const double c2 = taun * taun * (1.0 - e) - taun * d * e;
+    const double c3 = 0.5 * d * d;
+    const double c4 = taun * (1.0 - e);
+    for (int i = 0; i < n; ++i) Fd[h][i] = c1 * T0[i] + c2 * T1[i] + c3 * T2[i] + c4 * T3[i] - c2 * T4[i];
+  }
+  for (int i = 0; i < n; ++i) {
+    F[i] = (4.0 * Fd[1][i] - Fd[0][i]) / dt;
+    Ft[i] = 4.0 * (Fd[0][i] - 2.0 * Fd[1][i]) / (dt * dt);
+  }
+}
+
+bool physical(const double* q, int C, double gamma) {
+  double mm = q[1] * q[1] + (C == 4 ? q[2] * q[2] : 0.0);
+  const double pr = (gamma - 1.0) * (q[C - 1] * q[0] - 0.5 * mm);
+  return q[0] > 0.0 && pr > 0.0 && std::isfinite(pr);
+}
+
+// All GKS face fluxes (value and time derivative) of one direction and sigma_out.
+void gks_face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const double* sy_in, int dir,
+                     double dt, double* Fout, double* Ftout, double* sig_out, int64_t* hist) {
+  const int r = g.p->order;
+  const int k = (r - 1) / 2;
+  const int C = g.C;
+  const int dim = g.p->ndim;
+  const bool twoD = (dim == 2);
+  const int G = twoD ? ((r == 3) ? 1 : k) : 1;
+  const int kt = twoD ? k : 0;
+  const double gamma = g.p->gamma;
+  double tq[4], wq[4], eta[4];
+  gauss_legendre01(G, tq, wq);
+  for (int q = 0; q < G; ++q) eta[q] = tq[q] - 1.0;
+  const int64_t n = (dir == 0) ? g.nx : g.ny;
+  const int64_t mlines = (dir == 0) ? g.ny : g.nx;
+  const double hn = (dir == 0) ? g.dx : g.dy, ht = (dir == 0) ? g.dy : g.dx;
+  const double* sig_n = (dir == 0) ? sx_in : sy_in;
+  const double* sig_t = (dir == 0) ? sy_in : sx_in;
+  // pass 1: value and normal derivative (d/dn, physical) of every cell at both faces
+  const int64_t na = n + 2, nb = mlines + 2 * kt;
+  std::vector<double> QP((size_t)(na * nb * C)), QM(QP.size()), DP(QP.size()), DM(QP.size());
+  for (int64_t b = -kt; b < mlines + kt; ++b)
+    for (int64_t a = -1; a <= n; ++a) {
+      const int64_t i = (dir == 0) ? a : b, j = (dir == 0) ? b : a;
+      const size_t idx = (size_t)((b + kt) * na + (a + 1));
+      double out[4], dout[4];
+      normal_recon(g, Wd, sig_n, dir, i, j, true, out, dout);
+      for (int c = 0; c < C; ++c) { QP[idx * C + c] = out[c]; DP[idx * C + c] = dout[c] / hn; }
+      normal_recon(g, Wd, sig_n, dir, i, j, false, out, dout);
+      // the mirrored polynomial runs against the axis: d/dn = -(d/dxi) / h
+      for (int c = 0; c < C; ++c) { QM[idx * C + c] = out[c]; DM[idx * C + c] = -dout[c] / hn; }
+    }
+  // pass 2: faces
+  for (int64_t b = 0; b < mlines; ++b)
+    for (int64_t f = 0; f <= n; ++f) {
+      double st[2][4][4], dn[2][4][4], dt_[2][4][4];
+      for (int side = 0; side < 2; ++side) {
+        const int64_t a = (side == 0) ? f - 1 : f;
+        const std::vector<double>& Qv = (side == 0) ? QP : QM;
+        const std::vector<double>& Dv = (side == 0) ? DP : DM;
+        if (!twoD) {
+          const size_t idx = (size_t)(a + 1);
+          for (int c = 0; c < C; ++c) {
+            st[side][0][c] = Qv[idx * C + c];
+            dn[side][0][c] = Dv[idx * C + c];
+            dt_[side][0][c] = 0.0;
+          }
+          continue;
+        }
+        double Q[9][4], D[9][4];
+        for (int t = -k; t <= k; ++t) {
+          const size_t idx = (size_t)((b + t + kt) * na + (a + 1));
+          for (int c = 0; c < C; ++c) { Q[t + k][c] = Qv[idx * C + c]; D[t + k][c] = Dv[idx * C + c]; }
+        }
+        double sigt[8];
+        for (int m = -3; m <= 4; ++m) {
+          sigt[m + 3] = 0.0;
+          if (m < -k + 1 || m > k) continue;
+          sigt[m + 3] = (dir == 0) ? g.sy(sig_t, a, b + m) : g.sx(sig_t, b + m, a);
+        }
+        double dtan[4][4];
+        const int brt = tangential_recon(g, Q, sigt, G, eta, st[side], dtan);
+        hist[brt]++;
+        for (int q = 0; q < G; ++q)
+          for (int c = 0; c < C; ++c) dt_[side][q][c] = dtan[q][c] / ht;
+        tangential_recon(g, D, sigt, G, eta, dn[side]);
+      }
+      double cL[4], cR[4];
+      for (int c = 0; c < C; ++c) {
+        cL[c] = (dir == 0) ? g.W(Wd, c, f - 1, b) : g.W(Wd, c, b, f - 1);
+        cR[c] = (dir == 0) ? g.W(Wd, c, f, b) : g.W(Wd, c, b, f);
+      }
+      to_face_frame(cL, dir, C);
+      to_face_frame(cR, dir, C);
+      double Fs[4] = {0, 0, 0, 0}, Fts[4] = {0, 0, 0, 0}, ssum = 0.0;
+      for (int q = 0; q < G; ++q) {
+        double ql[4], qr[4], qlx[4], qrx[4], qly[4], qry[4];
+        for (int c = 0; c < C; ++c) {
+          ql[c] = st[0][q][c]; qr[c] = st[1][q][c];
+          qlx[c] = dn[0][q][c]; qrx[c] = dn[1][q][c];
+          qly[c] = dt_[0][q][c]; qry[c] = dt_[1][q][c];
+        }
+        to_face_frame(ql, dir, C); to_face_frame(qr, dir, C);
+        to_face_frame(qlx, dir, C); to_face_frame(qrx, dir, C);
+        to_face_frame(qly, dir, C); to_face_frame(qry, dir, C);
+        double sg;
+        if (!(physical(ql, C, gamma) && physical(qr, C, gamma))) {  // reading G26 (as G21)
+          for (int c = 0; c < C; ++c) {
+            ql[c] = cL[c]; qr[c] = cR[c];
+            qlx[c] = qrx[c] = qly[c] = qry[c] = 0.0;
+          }
+          sg = kSigmaBig;
+          hist[BR_FIRST]++;
+        } else {
+          Prim L = primitives(ql, C, gamma), R = primitives(qr, C, gamma);
+          sg = sigma_point(L, R, C);
+        }
+        double F[4], Ft[4];
+        gks_point(dim, gamma, ql, qlx, qly, qr, qrx, qry, dt, F, Ft);
+        to_face_frame(F, dir, C);
+        to_face_frame(Ft, dir, C);
+        for (int c = 0; c < C; ++c) { Fs[c] += wq[q] * F[c]; Fts[c] += wq[q] * Ft[c]; }
+        ssum += sg;
+      }
+      const double sface = ssum / (double)G;
+      if (dir == 0) {
+        for (int c = 0; c < C; ++c) {
+          Fout[((int64_t)c * g.ny + b) * (g.nx + 1) + f] = Fs[c];
+          Ftout[((int64_t)c * g.ny + b) * (g.nx + 1) + f] = Fts[c];
+        }
+        sig_out[b * (g.nx + 1) + f] = sface;
+      } else {
+        for (int c = 0; c < C; ++c) {
+          Fout[((int64_t)c * (g.ny + 1) + f) * g.nx + b] = Fs[c];
+          Ftout[((int64_t)c * (g.ny + 1) + f) * g.nx + b] = Fts[c];
+        }
+        sig_out[f * g.nx + b] = sface;
+      }
+    }
+}
+
+// L and L_t (Sec. 2.2) of one evaluation.
+void gks_residual(const OracleParams* p, const double* W, const double* sx, const double* sy, double dt,
+                  double* L, double* Lt, double* sxo, double* syo, int64_t* hist) {
+  Grid g = make_grid(p);
+  const int C = g.C;
+  const int64_t nx = g.nx, ny = g.ny;
+  std::vector<double> Fx((size_t)(C * ny * (nx + 1))), Fxt(Fx.size()), Fy, Fyt;
+  gks_face_fluxes(g, W, sx, sy, 0, dt, Fx.data(), Fxt.data(), sxo, hist);
+  if (p->ndim == 2) {
+    Fy.resize((size_t)(C * (ny + 1) * nx));
+    Fyt.resize(Fy.size());
+    gks_face_fluxes(g, W, sx, sy, 1, dt, Fy.data(), Fyt.data(), syo, hist);
+  }
+  for (int c = 0; c < C; ++c)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i) {
+        const int64_t fx = ((int64_t)c * ny + j) * (nx + 1) + i;
+        double l = -(Fx[fx + 1] - Fx[fx]) / g.dx, lt = -(Fxt[fx + 1] - Fxt[fx]) / g.dx;
+        if (p->ndim == 2) {
+          const int64_t fy = ((int64_t)c * (ny + 1) + j) * nx + i;
+          l -= (Fy[fy + nx] - Fy[fy]) / g.dy;
+          lt -= (Fyt[fy + nx] - Fyt[fy]) / g.dy;
+        }
+        L[((int64_t)c * ny + j) * nx + i] = l;
+        Lt[((int64_t)c * ny + j) * nx + i] = lt;
+      }
+}
+
+}  // namespace
+
+extern "C" {
+
+// The GKS flux at one Gauss point in the face frame (tests).  Wly / Wry are ignored in 1D.
+void oracle_gks_point(int32_t dim, double gamma, const double* Wl, const double* Wlx, const double* Wly,
+                      const double* Wr, const double* Wrx, const double* Wry, double dt, double* F, double* Ft) {
+  gks_point(dim, gamma, Wl, Wlx, Wly, Wr, Wrx, Wry, dt, F, Ft);
+}
+
+// L and L_t of one GKS evaluation with sigma_in -> sigma_out.
+void oracle_gks_residual(const OracleParams* p, const double* W, const double* sx, const double* sy, double dt,
+                         double* L, double* Lt, double* sxo, double* syo, int64_t* hist) {
+  int64_t h[BR_COUNT] = {0};
+  gks_residual(p, W, sx, sy, dt, L, Lt, sxo, syo, h);
+  if (hist)
+    for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[b];
+}
+
+// One S2O4 step (Sec. 2.2) in place with sigma feedback (reading G27); dt <= 0 takes the
+// CFL step.  Returns the dt used, negative if a cell average ends non-physical.
+double oracle_gks_step(const OracleParams* p, double* W, double* sx, double* sy, double dt, int64_t* hist) {
+  if (!(dt > 0.0)) {
+    dt = oracle_cfl_dt(p, W);
+    if (dt < 0.0) return dt;
+  }
+  const Sizes z = sizes_of(p);
+  std::vector<double> L0((size_t)z.w), Lt0((size_t)z.w), L1((size_t)z.w), Lt1((size_t)z.w), Ws((size_t)z.w);
+  std::vector<double> sxa((size_t)z.sx), sya((size_t)z.sy, 0.0), syz((size_t)z.sy, 0.0);
+  const double* syin = (p->ndim == 2) ? sy : syz.data();
+  int64_t h[BR_COUNT] = {0};
+  gks_residual(p, W, sx, syin, dt, L0.data(), Lt0.data(), sxa.data(), sya.data(), h);
+  for (int64_t i = 0; i < z.w; ++i) Ws[(size_t)i] = W[i] + 0.5 * dt * L0[(size_t)i] + 0.125 * dt * dt * Lt0[(size_t)i];
+  gks_residual(p, Ws.data(), sxa.data(), sya.data(), dt, L1.data(), Lt1.data(), sx,
+               (p->ndim == 2) ? sy : syz.data(), h);
+  for (int64_t i = 0; i < z.w; ++i)
+    W[i] = W[i] + dt * L0[(size_t)i] + (1.0 / 6.0) * dt * dt * (Lt0[(size_t)i] + 2.0 * Lt1[(size_t)i]);
+  if (hist)
+    for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[b];
+  int bad = 0;
+  max_speed(p, W, &bad);
+  return bad ? -dt : dt;
+}
+
+}  // extern "C"
+#endif  // plain build
 
 #ifdef ORACLE_TAPE
 namespace {

@@ -95,6 +95,14 @@ def _lib(counting: bool = False, tape: bool = False):
         if counting:
             lib.oracle_op_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
             lib.oracle_reset_op_counts.argtypes = []
+        if key == "plain":
+            lib.oracle_gks_point.argtypes = [ctypes.c_int32, ctypes.c_double] + [_P] * 6 + [ctypes.c_double, _P, _P]
+            lib.oracle_gks_point.restype = None
+            lib.oracle_gks_residual.argtypes = [ctypes.POINTER(_Params), _P, _P, _P, ctypes.c_double, _P, _P, _P,
+                                                _P, _I64]
+            lib.oracle_gks_residual.restype = None
+            lib.oracle_gks_step.argtypes = [ctypes.POINTER(_Params), _P, _P, _P, ctypes.c_double, _I64]
+            lib.oracle_gks_step.restype = ctypes.c_double
         if tape:
             lib.oracle_residual_vjp.argtypes = [ctypes.POINTER(_Params)] + [_P] * 9
             lib.oracle_residual_vjp.restype = ctypes.c_int64
@@ -298,3 +306,66 @@ def run_vjp(pb, W0, nsteps: int, dt: float, Wbar_final):
     if n < 0:
         raise FloatingPointError("non-physical state in the taped run")
     return Wbar0
+
+
+# ----------------------------------------------------------------------------------
+# gas-kinetic flux and S2O4 (Sec. 2.2)
+# ----------------------------------------------------------------------------------
+def gks_point(dim: int, gamma: float, Wl, Wlx, Wly, Wr, Wrx, Wry, dt: float):
+    """GKS flux at one Gauss point, face frame: -> (F, F_t)."""
+    n = dim + 2
+    arrs = [_f64(np.asarray(a, dtype=np.float64).reshape(-1)[:n]) if a is not None else np.zeros(n)
+            for a in (Wl, Wlx, Wly, Wr, Wrx, Wry)]
+    F = np.zeros(n)
+    Ft = np.zeros(n)
+    _lib().oracle_gks_point(int(dim), float(gamma), *[_ptr(a) for a in arrs], float(dt), _ptr(F), _ptr(Ft))
+    return F, Ft
+
+
+def gks_residual(pb, W, sx, sy, dt: float):
+    """One GKS evaluation: -> (L, L_t, sx_out, sy_out, hist)."""
+    W, sx, sy = _f64(W), _f64(sx), _f64(sy)
+    L = np.empty_like(W)
+    Lt = np.empty_like(W)
+    sxo = np.empty(pb.sx_shape)
+    syo = np.zeros(pb.sy_shape)
+    hist = np.zeros(len(BRANCHES), dtype=np.int64)
+    p = _params(pb)
+    _lib().oracle_gks_residual(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), float(dt), _ptr(L), _ptr(Lt),
+                               _ptr(sxo), _ptr(syo), hist.ctypes.data_as(_I64))
+    return L, Lt, sxo, syo, hist
+
+
+def gks_step(pb, W, sx, sy, dt: float = 0.0, hist: Optional[np.ndarray] = None):
+    """One S2O4 step (CFL when dt <= 0): -> (W, sx, sy, dt used; negative if non-physical)."""
+    W, sx, sy = _f64(W).copy(), _f64(sx).copy(), _f64(sy).copy()
+    h = np.zeros(len(BRANCHES), dtype=np.int64) if hist is None else hist
+    p = _params(pb)
+    d = _lib().oracle_gks_step(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), float(dt), h.ctypes.data_as(_I64))
+    return W, sx, sy, d
+
+
+def gks_run(pb, W, t_end: float = 0.0, nsteps: int = 0, dt: float = 0.0, dt_cap: float = 0.0):
+    """S2O4 march to t_end (CFL steps, capped by dt_cap if > 0, the last one shortened) or
+    nsteps steps of dt; sigma^0 is primed.  -> (W, sx, sy, t, n)."""
+    sx, sy = prime_sigma(pb, W)
+    W = _f64(W)
+    t, n = 0.0, 0
+    while True:
+        if nsteps and n >= nsteps:
+            break
+        if t_end and t >= t_end * (1 - 1e-14):
+            break
+        h = dt if dt > 0 else cfl_dt(pb, W)
+        if h <= 0:
+            raise FloatingPointError("non-physical state at t=%g" % t)
+        if dt_cap > 0:
+            h = min(h, dt_cap)
+        if t_end and t + h > t_end:
+            h = t_end - t
+        W, sx, sy, h2 = gks_step(pb, W, sx, sy, h)
+        if h2 < 0:
+            raise FloatingPointError("non-physical state after the step at t=%g" % t)
+        t += h
+        n += 1
+    return W, sx, sy, t, n
