@@ -156,6 +156,22 @@ def sin_wave_2d(n: int, order: int) -> Tuple[Problem, np.ndarray]:
     return pb, sin_wave_2d_exact(pb, 0.0)
 
 
+def sin_wave_2d_diag(n: int, order: int) -> Tuple[Problem, np.ndarray]:
+    """The 2-D sin-wave of Table 2 (Sec. 4.2): rho = 1 + 0.2 sin(pi (x + y)), u = v = p = 1 on
+    [0,2]^2, periodic (the diagonal wave reproduces the printed Table 2 errors)."""
+    pb = Problem(ndim=2, nx=n, ny=n, x0=0.0, x1=2.0, y0=0.0, y1=2.0, order=order, gamma=1.4,
+                 bc=("periodic",) * 4)
+    return pb, sin_wave_2d_diag_exact(pb, 0.0)
+
+
+def sin_wave_2d_diag_exact(pb: Problem, t: float) -> np.ndarray:
+    def prim(x, y):
+        one = np.ones_like(x)
+        return (1.0 + 0.2 * np.sin(np.pi * (x + y - 2.0 * t)), one, one, one)
+
+    return cell_average(pb, prim)
+
+
 def sin_wave_2d_exact(pb: Problem, t: float) -> np.ndarray:
     def prim(x, y):
         one = np.ones_like(x)

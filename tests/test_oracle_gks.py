@@ -7,9 +7,9 @@
   compatibility condition together must reproduce that exactly (Jacobians here by
   central differences of the closed-form Euler fluxes, independent of kinetic theory).
 * Mirror symmetry of a Riemann-type point (x -> -x).
-* Table 1 of Sec. 4.2 (1-D sin-wave, GKS + S2O4, dt = min(CFL dt, dx^(r/4))): the printed
-  L1 errors at N = 20 and 40 are reproduced, to 2 % at orders 7 and 9 and to 15 % at
-  order 5.
+* Tables 1 and 2 of Sec. 4.2 (sin-waves, GKS + S2O4, dt = dx^(r/4)): the printed L1
+  errors are reproduced -- 1-D at N = 20 and 40 for orders 5, 7, 9 to 1 %, and the 2-D
+  diagonal wave at N = 20, order 7, to 2 %.
 * Conservation on a periodic grid.
 """
 import math
@@ -98,19 +98,29 @@ def test_mirror_symmetry(oracle):
 
 def run_sin_wave_1d(oracle, N, r):
     pb, W = P.sin_wave_1d(N, r)
-    dt = min(oracle.cfl_dt(pb, W), pb.dx ** (r / 4.0))  # dt = dx^(r/s), s = 4 (S2O4)
-    n = int(math.ceil(2.0 / dt))
+    n = int(math.ceil(2.0 / pb.dx ** (r / 4.0)))  # dt = dx^(r/s), s = 4 (S2O4), reading G28
     Wn, *_ = oracle.gks_run(pb, W, nsteps=n, dt=2.0 / n)
     ex = P.sin_wave_1d_exact(pb, 2.0)
     return np.abs(Wn[0] - ex[0]).sum() * pb.dx / 2.0
 
 
-@pytest.mark.parametrize("r,tol", [(5, 0.15), (7, 0.02), (9, 0.02)])
-def test_sin_wave_1d_reproduces_table1(oracle, golden, r, tol):
+@pytest.mark.parametrize("r", [5, 7, 9])
+def test_sin_wave_1d_reproduces_table1(oracle, golden, r):
     tab = golden("sin_wave_accuracy_tables.json")["table1_1d"]["r%d" % r]
     for k, N in enumerate((20, 40)):
         e = run_sin_wave_1d(oracle, N, r)
-        assert abs(e / tab["err"][k] - 1.0) < tol, (N, e, tab["err"][k])
+        assert abs(e / tab["err"][k] - 1.0) < 0.01, (N, e, tab["err"][k])
+
+
+def test_sin_wave_2d_reproduces_table2(oracle, golden):
+    """The diagonal wave at N = 20, order 7 (dt = dx^(7/4), below the CFL limit)."""
+    tab = golden("sin_wave_accuracy_tables.json")["table2_2d"]["r7"]
+    pb, W = P.sin_wave_2d_diag(20, 7)
+    n = int(math.ceil(2.0 / pb.dx ** (7 / 4.0)))
+    Wn, *_ = oracle.gks_run(pb, W, nsteps=n, dt=2.0 / n)
+    ex = P.sin_wave_2d_diag_exact(pb, 2.0)
+    e = np.abs(Wn[0] - ex[0]).sum() * pb.dx * pb.dy / 4.0
+    assert abs(e / tab["err"][0] - 1.0) < 0.02, (e, tab["err"][0])
 
 
 def test_periodic_conservation(oracle):
