@@ -216,6 +216,30 @@ ase_df_status ase_df_residual_noalloc(const ase_df_params* p, const double* W, c
                                       void* stream);
 
 /* ---------------------------------------------------------------------------------
+ * Gas-kinetic flux and two-stage fourth-order time stepping (Sec. 2.2 with Appendix A):
+ * the paper's primary solver.  The reconstruction (Sec. 3, Algorithm 1, the same sigma
+ * feedback) also provides the normal and tangential derivatives of each side's state at
+ * the Gauss points; the flux of the BGK distribution function of Eq. (GKS flux), with
+ * the physical collision time 0 (inviscid flow) and the numerical collision time
+ * tau_n = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt (C1 = 0.01, C2 = 1), is integrated over
+ * [0, dt] and [0, dt/2], giving the face flux F and its time derivative F_t.  A Gauss
+ * point with a non-physical state takes the two cell averages with zero derivatives
+ * (sigma 1e30, ASE_DF_FLAG_POSITIVITY).  There is no positivity repair on this path.
+ * --------------------------------------------------------------------------------- */
+
+/* One gas-kinetic evaluation for the step size dt > 0: L (as ase_df_residual) and its time
+ * derivative Lt (both [C][ny][nx]), sigma_out as ase_df_residual. */
+ase_df_status ase_df_gks_residual(ase_df_ctx* ctx, const double* W, const double* sx_in, const double* sy_in,
+                                  double dt, double* L, double* Lt, double* sx_out, double* sy_out, void* stream);
+
+/* One S2O4 step in place: W* = W^n + dt/2 L(W^n) + dt^2/8 Lt(W^n), then
+ * W^{n+1} = W^n + dt L(W^n) + dt^2/6 (Lt(W^n) + 2 Lt(W*)); each stage consumes the sigma
+ * of the stage before (sx, sy: sigma^n on entry, the second stage's on exit).  dt > 0:
+ * that step; dt <= 0: the CFL step of W^n (as ase_df_step), fixed before the first flux
+ * evaluation.  A non-physical cell average raises ASE_DF_FLAG_NONPHYSICAL. */
+ase_df_status ase_df_gks_step(ase_df_ctx* ctx, double* W, double* sx, double* sy, double dt, void* stream);
+
+/* ---------------------------------------------------------------------------------
  * Batched solves (no counterpart in the paper, whose solver advances one problem): n
  * independent problems, 1D and 2D, of mixed order, advanced together, each with its own
  * CFL dt, time and status.  Every sweep direction of every RK stage is ONE persistent

@@ -71,6 +71,8 @@ def _load():
         "ase_df_run": ([CTX, _VP, _VP, _VP, _c.c_double, _c.c_int32, _VP], _c.c_int),
         "ase_df_residual_adjoint": ([CTX, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], _c.c_int),
         "ase_df_step_adjoint": ([CTX, _VP, _VP, _VP, _c.c_double, _VP, _VP, _VP, _VP], _c.c_int),
+        "ase_df_gks_residual": ([CTX, _VP, _VP, _VP, _c.c_double, _VP, _VP, _VP, _VP, _VP], _c.c_int),
+        "ase_df_gks_step": ([CTX, _VP, _VP, _VP, _c.c_double, _VP], _c.c_int),
         "ase_df_get_status": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)], _c.c_int),
         "ase_df_reset": ([CTX, _c.c_double, _VP], _c.c_int),
         "ase_df_get_repair_stats": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_uint64),
@@ -169,6 +171,15 @@ def ase_df_residual_adjoint(ctx, W, sx_in, sy_in, Lbar, sxbar_out, sybar_out, Wb
 def ase_df_step_adjoint(ctx, W, sx, sy, dt: float, Wbar, sxbar, sybar, stream=None) -> None:
     _check(ctx, _load().ase_df_step_adjoint(ctx, _ptr(W), _ptr(sx), _ptr(sy), float(dt), _ptr(Wbar), _ptr(sxbar),
                                             _ptr(sybar), _stream(stream)))
+
+
+def ase_df_gks_residual(ctx, W, sx_in, sy_in, dt: float, L, Lt, sx_out, sy_out, stream=None) -> None:
+    _check(ctx, _load().ase_df_gks_residual(ctx, _ptr(W), _ptr(sx_in), _ptr(sy_in), float(dt), _ptr(L), _ptr(Lt),
+                                            _ptr(sx_out), _ptr(sy_out), _stream(stream)))
+
+
+def ase_df_gks_step(ctx, W, sx, sy, dt: float = 0.0, stream=None) -> None:
+    _check(ctx, _load().ase_df_gks_step(ctx, _ptr(W), _ptr(sx), _ptr(sy), float(dt), _stream(stream)))
 
 
 def ase_df_get_status(ctx) -> Tuple[int, float, float]:
@@ -279,6 +290,21 @@ class Solver:
         """In place: (Wbar, sxbar, sybar) from the adjoint of W^{n+1}, sigma^{n+1} to that
         of W^n, sigma^n for the step of fixed dt from (W, sx, sy)."""
         ase_df_step_adjoint(self.ctx, W, sx, self._sy(sy), dt, Wbar, sxbar, self._sy(sybar))
+
+    def gks_residual(self, dt: float, W=None, sx=None, sy=None):
+        """Gas-kinetic L and L_t for step size dt: -> (L, Lt, sx_out, sy_out)."""
+        W = self.W if W is None else W
+        sx = self.sx if sx is None else sx
+        sy = self.sy if sy is None else sy
+        L = torch.empty_like(W)
+        Lt = torch.empty_like(W)
+        sxo = torch.empty_like(sx)
+        syo = torch.empty_like(sy)
+        ase_df_gks_residual(self.ctx, W, sx, self._sy(sy), dt, L, Lt, sxo, self._sy(syo))
+        return L, Lt, sxo, syo
+
+    def gks_step(self, dt: float = 0.0) -> None:
+        ase_df_gks_step(self.ctx, self.W, self.sx, self._sy(self.sy), dt)
 
     def face_fluxes(self):
         pb = self.pb

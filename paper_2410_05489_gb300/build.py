@@ -3,7 +3,7 @@
     python -m paper_2410_05489_gb300.build [--verbose]
 
 Objects and the library go to paper_2410_05489_gb300/_build/.  The sweep kernel file is
-compiled once per scheme order (3, 5, 7, 9), and so is the adjoint kernel file.
+compiled once per scheme order (3, 5, 7, 9), and so are the adjoint and gas-kinetic kernel files.
 """
 from __future__ import annotations
 
@@ -25,8 +25,9 @@ def _units():
     for r in (3, 5, 7, 9):
         units.append(("ase_df_sweep.cu", "sweep_r%d.o" % r, ["-DASE_DF_ORDER=%d" % r]))
         units.append(("ase_df_adjoint.cu", "adjoint_r%d.o" % r, ["-DASE_DF_ORDER=%d" % r]))
+        units.append(("ase_df_gks.cu", "gks_r%d.o" % r, ["-DASE_DF_ORDER=%d" % r]))
     for src in ("ase_df_combine.cu", "ase_df_api.cu", "ase_df_fp64_peak.cu", "ase_df_tables.cpp",
-                "ase_df_noalloc.cu", "ase_df_batch.cu"):
+                "ase_df_noalloc.cu", "ase_df_batch.cu", "ase_df_gks_combine.cu"):
         if os.path.exists(os.path.join(CSRC, src)):
             units.append((src, os.path.splitext(src)[0] + ".o", []))
     return units

@@ -13,6 +13,7 @@
 
 #include "../../include/ase_df.h"
 #include "ase_df_adjoint.cuh"
+#include "ase_df_gks.cuh"
 #include "ase_df_internal.cuh"
 
 using namespace asedf;
@@ -22,6 +23,7 @@ struct ase_df_ctx {
   int C, K, dim;
   GridInfo g;
   Tables tab;
+  DTables dtab;             // derivative weights (gas-kinetic path)
   double dx, dy, inv_dx, inv_dy, inflow_speed;
   // device scratch owned by the context
   double *Fx, *Fy;          // face fluxes
@@ -34,6 +36,9 @@ struct ase_df_ctx {
   double* adj;              // per-direction kernel scratch (adj_scratch_doubles)
   double *Ab1, *Ab2, *Abn;  // stage adjoints of the SSP-RK3 step adjoint
   double *s0bx, *s0by, *s1bx, *s1by, *s2bx, *s2by;  // sigma adjoints of the stages
+  // gas-kinetic scratch (allocated by the first gas-kinetic call)
+  double *Fxt, *Fyt;        // time derivatives of the face fluxes
+  double *L0, *Lt0;         // L(W^n), L_t(W^n) of an S2O4 step
   // CUDA graph of one step (ase_df_run)
   cudaGraphExec_t graph_exec;
   double* g_W;
@@ -190,6 +195,7 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
   g.gamma = p.gamma;
   g.thres = p.sigma_thres;
   build_tables(p.order, p.ndim, &c->tab);
+  build_dtables(p.order, p.ndim, &c->dtab);
 
   const size_t nW = (size_t)C * g.nx * g.ny;
   const size_t nFx = (size_t)C * g.ny * (g.nx + 1);
@@ -233,7 +239,8 @@ void ase_df_destroy(ase_df_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   double* ptrs[] = {c->Fx,  c->Fy,  c->W1,   c->W2,   c->sxa,  c->sya,  c->sxb,  c->syb,  c->zsx, c->zsy,
-                    c->adj, c->Ab1, c->Ab2,  c->Abn,  c->s0bx, c->s0by, c->s1bx, c->s1by, c->s2bx, c->s2by};
+                    c->adj, c->Ab1, c->Ab2,  c->Abn,  c->s0bx, c->s0by, c->s1bx, c->s1by, c->s2bx, c->s2by,
+                    c->Fxt, c->Fyt, c->L0,   c->Lt0};
   for (double* q : ptrs)
     if (q) cudaFree(q);
   if (c->st) cudaFree(c->st);
@@ -604,6 +611,128 @@ ase_df_status ase_df_step_adjoint(ase_df_ctx* c, const double* W, const double* 
   if (e == cudaSuccess) e = cudaMemcpyAsync(sxbar, c->s0bx, nsx * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && nsy) e = cudaMemcpyAsync(sybar, c->s0by, nsy * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint: copy out");
+  return ASE_DF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// gas-kinetic path (Sec. 2.2)
+// ---------------------------------------------------------------------------------
+static ase_df_status ensure_gks(ase_df_ctx* c) {
+  if (c->Fxt) return ASE_DF_OK;
+  const GridInfo& g = c->g;
+  const size_t nW = (size_t)c->C * g.nx * g.ny;
+  const size_t nFx = (size_t)c->C * g.ny * (g.nx + 1);
+  const size_t nFy = (c->dim == 2) ? (size_t)c->C * (g.ny + 1) * g.nx : 1;
+  struct { double** ptr; size_t n; } allocs[] = {{&c->Fxt, nFx}, {&c->Fyt, nFy}, {&c->L0, nW}, {&c->Lt0, nW}};
+  for (auto& a : allocs) {
+    if (cudaMalloc((void**)a.ptr, a.n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& b : allocs) {
+        if (*b.ptr) cudaFree(*b.ptr);
+        *b.ptr = nullptr;
+      }
+      return fail(c, ASE_DF_E_NOMEM, "device allocation of %zu bytes of gas-kinetic scratch failed",
+                  a.n * sizeof(double));
+    }
+  }
+  return ASE_DF_OK;
+}
+
+static cudaError_t gks_face_fluxes(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
+                                   double* sxo, double* syo, double dt_fixed, cudaStream_t s) {
+  for (int dir = 0; dir < c->dim; ++dir) {
+    GksSweepArgs a;
+    a.W = W;
+    a.s_norm = (dir == 0) ? sx : sy;
+    a.s_tan = (dir == 0) ? sy : sx;
+    a.F = (dir == 0) ? c->Fx : c->Fy;
+    a.Ft = (dir == 0) ? c->Fxt : c->Fyt;
+    a.s_out = (dir == 0) ? sxo : syo;
+    a.st = c->st;
+    a.dt_fixed = dt_fixed;
+    a.inv_dn = (dir == 0) ? c->inv_dx : c->inv_dy;
+    a.inv_dt = (dir == 0) ? c->inv_dy : c->inv_dx;
+    cudaError_t e;
+    ProfScope prof(c, s, dir);
+    switch (c->p.order) {
+      case 3: e = launch_gks_sweep_r3(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
+      case 5: e = launch_gks_sweep_r5(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
+      case 7: e = launch_gks_sweep_r7(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
+      default: e = launch_gks_sweep_r9(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t gks_combine(ase_df_ctx* c, int stage, const double* Wn, double* out, double* Lt_out,
+                               double dt_fixed, cudaStream_t s) {
+  GksCombineArgs a;
+  a.Fx = c->Fx;
+  a.Fxt = c->Fxt;
+  a.Fy = c->Fy;
+  a.Fyt = c->Fyt;
+  a.Wn = Wn;
+  a.out = out;
+  a.Lt_out = Lt_out;
+  a.L0 = c->L0;
+  a.Lt0 = c->Lt0;
+  a.st = c->st;
+  a.inv_dx = c->inv_dx;
+  a.inv_dy = c->inv_dy;
+  a.dt_fixed = dt_fixed;
+  a.stage = stage;
+  ProfScope prof(c, s, 2);
+  return launch_gks_combine(c->dim, c->g, a, s);
+}
+
+extern "C" {
+
+ase_df_status ase_df_gks_residual(ase_df_ctx* c, const double* W, const double* sx_in, const double* sy_in, double dt,
+                                  double* L, double* Lt, double* sx_out, double* sy_out, void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx_in, sy_in);
+  if (r != ASE_DF_OK) return r;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ASE_DF_E_INVAL, "the gas-kinetic flux needs dt > 0");
+  if (!L || !Lt || !sx_out || (c->dim == 2 && !sy_out)) return fail(c, ASE_DF_E_INVAL, "NULL output pointer");
+  if (sx_out == sx_in || (c->dim == 2 && sy_out == sy_in))
+    return fail(c, ASE_DF_E_INVAL, "sigma_out must not alias sigma_in");
+  if ((r = ensure_gks(c)) != ASE_DF_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  cudaError_t e = gks_face_fluxes(c, W, sx_in, sy_in, sx_out, sy_out, dt, s);
+  if (e == cudaSuccess) e = gks_combine(c, 0, W, L, Lt, dt, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gas-kinetic residual");
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_gks_step(ase_df_ctx* c, double* W, double* sx, double* sy, double dt, void* stream) {
+  ase_df_status r = check_ptrs(c, W, sx, sy);
+  if (r != ASE_DF_OK) return r;
+  if (!std::isfinite(dt)) return fail(c, ASE_DF_E_INVAL, "dt is not finite");
+  if ((r = ensure_gks(c)) != ASE_DF_OK) return r;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  cudaError_t e = cudaSuccess;
+  const double dtf = (dt > 0.0) ? dt : 0.0;
+  if (!(dt > 0.0)) {
+    SpeedArgs sa;
+    sa.W = W;
+    sa.st = c->st;
+    sa.inv_dx = c->inv_dx;
+    sa.inv_dy = c->inv_dy;
+    ProfScope prof(c, s, 3);
+    e = launch_max_speed(c->dim, c->g, sa, s);
+  }
+  if (e == cudaSuccess) e = launch_gks_dt(c->st, dtf, c->p.cfl, c->p.t_end, c->inflow_speed, s);
+  // stage 1: W* = W^n + dt/2 L + dt^2/8 L_t, sigma -> sxa, sya
+  if (e == cudaSuccess) e = gks_face_fluxes(c, W, sx, sy, c->sxa, c->sya, dtf, s);
+  if (e == cudaSuccess) e = gks_combine(c, 1, W, c->W1, nullptr, dtf, s);
+  // stage 2: W^{n+1} from L(W^n), L_t(W^n) and L_t(W*); its sigma lands in sx, sy
+  if (e == cudaSuccess) e = gks_face_fluxes(c, c->W1, c->sxa, c->sya, sx, sy, dtf, s);
+  if (e == cudaSuccess) e = gks_combine(c, 2, W, W, nullptr, dtf, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gas-kinetic step");
   return ASE_DF_OK;
 }
 

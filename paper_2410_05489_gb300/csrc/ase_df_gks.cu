@@ -1,0 +1,591 @@
+// Gas-kinetic face kernel of the ASE-DF scheme (Sec. 2.2 with Appendix A), one sweep
+// direction, sm_103a, FP64.  Compiled once per scheme order (ASE_DF_ORDER).
+//
+// Per face the tile is staged like the Lax-Friedrichs sweep; phase 1 reconstructs every
+// cell of the band at both of its faces, value and normal derivative (Sec. 3 polynomials
+// and their derivatives); phase 2 reconstructs, per face side, the G Gauss-point values
+// and tangential derivatives from the face line-averages, and the Gauss-point normal
+// derivatives from the line-averages of the normal derivative (the same tangential
+// procedure applied to them), then evaluates the gas-kinetic flux at each Gauss point:
+//   Maxwellians g_l, g_r of the two states and their moments (erfc half-line moments),
+//   slopes a from <psi psi^T> a = W_x / rho (closed form of Appendix A), the
+//   kinetic-weighted equilibrium state g_c and its slopes, A_c from the compatibility
+//   condition, and the time integrals of the distribution function of Eq. (GKS flux)
+//   with the physical collision time 0 over [0, dt] and [0, dt/2]:
+//     F(d) = c1 T0 + c2 (T1 - T4) + c3 T2 + c4 T3,
+//     c1 = d - tn (1 - e), c2 = tn^2 (1 - e) - tn d e, c3 = d^2 / 2, c4 = tn (1 - e),
+//     e = exp(-d / tn), tn = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt  (C1 = 0.01, C2 = 1);
+//   T0 = rho_c <u psi>_c, T1 = rho_c <u (a_x^c u + a_y^c v) psi>_c, T2 = rho_c <u A^c psi>_c,
+//   T3 = rho_l <u psi>_{l,u>0} + rho_r <u psi>_{r,u<0}, T4 = the same with (a_x u + a_y v).
+//   F = (4 F(dt/2) - F(dt)) / dt and F_t = 4 (F(dt) - 2 F(dt/2)) / dt^2 (Sec. 2.2).
+// A Gauss point where either side's state is non-physical takes the two cell averages
+// with zero derivatives and sigma 1e30, as the Lax-Friedrichs path does.
+
+#include <cuda_runtime.h>
+
+#include "ase_df_gks.cuh"
+#include "ase_df_sweep_body.cuh"
+
+#ifndef ASE_DF_ORDER
+#error "ASE_DF_ORDER must be defined"
+#endif
+
+namespace asedf {
+namespace {
+
+constexpr double kGksC1 = 0.01, kGksC2 = 1.0;
+
+// ---------------------------------------------------------------------------------
+// value and d/dxi of the chosen polynomial (Algorithm 1) at NP points p0..
+// ---------------------------------------------------------------------------------
+template <int NP>
+__device__ void weno_eval_d(const double* v, int vs, const Branch& br, const Tables& T, const DTables& D, int p0,
+                            double* out, double* dout) {
+  double beta[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double* vk = v + (k - 2) * vs;
+    const double c1 = T.cq[k][0][0] * vk[0] + T.cq[k][0][1] * vk[vs] + T.cq[k][0][2] * vk[2 * vs];
+    const double c2 = T.cq[k][1][0] * vk[0] + T.cq[k][1][1] * vk[vs] + T.cq[k][1][2] * vk[2 * vs];
+    beta[k] = c1 * (c1 - 2.0 * c2) + (16.0 / 3.0) * c2 * c2;
+  }
+  const double b5 = (beta[0] + 4.0 * beta[1] + beta[2]) * (1.0 / 6.0) + fabs(beta[0] - beta[2]);
+  const double tau = (fabs(b5 - beta[0]) + fabs(b5 - beta[1]) + fabs(b5 - beta[2])) * (1.0 / 3.0);
+  const double tau2 = tau * tau;
+  const double e5 = b5 + T.eps;
+  const double w5 = T.d5 * (1.0 + tau2 / (e5 * e5));
+  double w3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double e = beta[k] + T.eps;
+    w3[k] = T.d3[k] * (1.0 + tau2 / (e * e));
+  }
+  const double inv = 1.0 / (w5 + w3[0] + w3[1] + w3[2]);
+  const double g5 = (w5 * inv) / T.d5;
+  double g3[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g3[k] = w3[k] * inv - g5 * T.d3[k];
+  const double W0 = v[0];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int p = p0 + q;
+    double P = g5 * fma(br.a5, lin_eval<5>(v, vs, T.lin[1][p]) - W0, W0);
+    double dP = g5 * br.a5 * lin_eval<5>(v, vs, D.dlin[1][p]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double* vk = v + (k - 2) * vs;
+      const double u = T.sub[k][p][0] * vk[0] + T.sub[k][p][1] * vk[vs] + T.sub[k][p][2] * vk[2 * vs];
+      const double du = D.dsub[k][p][0] * vk[0] + D.dsub[k][p][1] * vk[vs] + D.dsub[k][p][2] * vk[2 * vs];
+      P = fma(g3[k], fma(br.a3[k], u - W0, W0), P);
+      dP = fma(g3[k] * br.a3[k], du, dP);
+    }
+    out[q] = P;
+    dout[q] = dP;
+  }
+}
+
+template <int R, int NP>
+__device__ __forceinline__ void recon_eval_d(const double* v, int vs, const Branch& br, const Tables& T,
+                                             const DTables& D, int p0, double* out, double* dout) {
+  if (br.m == R) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      out[q] = lin_eval<R>(v, vs, T.lin[(R - 3) / 2][p0 + q]);
+      dout[q] = lin_eval<R>(v, vs, D.dlin[(R - 3) / 2][p0 + q]);
+    }
+    return;
+  }
+  if (R == 3) {  // DF-damped order 3: W0 + a (lin3 - W0)
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      out[q] = fma(br.a5, lin_eval<3>(v, vs, T.lin[0][p0 + q]) - v[0], v[0]);
+      dout[q] = br.a5 * lin_eval<3>(v, vs, D.dlin[0][p0 + q]);
+    }
+    return;
+  }
+  if (R >= 9 && br.m == 7) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      out[q] = lin_eval<(R >= 7 ? 7 : 3)>(v, vs, T.lin[2][p0 + q]);
+      dout[q] = lin_eval<(R >= 7 ? 7 : 3)>(v, vs, D.dlin[2][p0 + q]);
+    }
+    return;
+  }
+  if (R >= 7 && br.m == 5) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      out[q] = lin_eval<5>(v, vs, T.lin[1][p0 + q]);
+      dout[q] = lin_eval<5>(v, vs, D.dlin[1][p0 + q]);
+    }
+    return;
+  }
+  if (R >= 5) weno_eval_d<NP>(v, vs, br, T, D, p0, out, dout);
+}
+
+// ---------------------------------------------------------------------------------
+// Maxwellian moments (Appendix A)
+// ---------------------------------------------------------------------------------
+struct Maxw {
+  double rho, U, V, lam;
+  double mu[7], mv[6], mx[3];  // <u^n> (n <= 6), <v^n> (n <= 5), <xi^0>, <xi^2>, <xi^4>
+};
+
+template <int DIM>
+__device__ __forceinline__ void maxw_init(const double* W, double gamma, double K, Maxw& m) {
+  m.rho = W[0];
+  const double ir = 1.0 / W[0];
+  m.U = W[1] * ir;
+  m.V = (DIM == 2) ? W[2] * ir : 0.0;
+  const double p = (gamma - 1.0) * (W[DIM + 1] - 0.5 * m.rho * (m.U * m.U + m.V * m.V));
+  m.lam = 0.5 * m.rho / p;
+  const double h = p * ir;  // 1 / (2 lambda)
+  m.mu[0] = 1.0;
+  m.mu[1] = m.U;
+#pragma unroll
+  for (int n = 0; n < 5; ++n) m.mu[n + 2] = fma(m.U, m.mu[n + 1], (n + 1) * h * m.mu[n]);
+  m.mv[0] = 1.0;
+  m.mv[1] = m.V;
+#pragma unroll
+  for (int n = 0; n < 4; ++n) m.mv[n + 2] = (DIM == 2) ? fma(m.V, m.mv[n + 1], (n + 1) * h * m.mv[n]) : 0.0;
+  m.mx[0] = 1.0;
+  m.mx[1] = K * h;
+  m.mx[2] = (K + 2.0) * h * m.mx[1];
+}
+
+// <u^n> over u > 0 (pos) or u < 0, n <= 6
+__device__ __forceinline__ void half_moments(const Maxw& m, bool pos, double* mh) {
+  const double sl = sqrt(m.lam);
+  const double e = 0.5 * exp(-m.lam * m.U * m.U) / sqrt(3.141592653589793 * m.lam);
+  mh[0] = 0.5 * erfc(pos ? -sl * m.U : sl * m.U);
+  mh[1] = fma(m.U, mh[0], pos ? e : -e);
+  const double h = 0.5 / m.lam;
+#pragma unroll
+  for (int n = 0; n < 5; ++n) mh[n + 2] = fma(m.U, mh[n + 1], (n + 1) * h * mh[n]);
+}
+
+// <u^s v^t psi_i> and <u^s v^t psi_i psi_j> with psi = (1, u, v, (u^2+v^2+xi^2)/2) in 2D,
+// (1, u, (u^2+xi^2)/2) in 1D; mu are the u moments (full or half line).
+template <int DIM>
+__device__ __forceinline__ double mom1(int i, int s, int t, const double* mu, const Maxw& m) {
+  auto M = [&](int a, int b, int l) { return mu[a] * m.mv[b] * m.mx[l]; };
+  if (DIM == 2) {
+    if (i == 0) return M(s, t, 0);
+    if (i == 1) return M(s + 1, t, 0);
+    if (i == 2) return M(s, t + 1, 0);
+    return 0.5 * (M(s + 2, t, 0) + M(s, t + 2, 0) + M(s, t, 1));
+  }
+  if (i == 0) return M(s, 0, 0);
+  if (i == 1) return M(s + 1, 0, 0);
+  return 0.5 * (M(s + 2, 0, 0) + M(s, 0, 1));
+}
+
+template <int DIM>
+__device__ __forceinline__ double mom2(int i, int j, int s, int t, const double* mu, const Maxw& m) {
+  auto M = [&](int a, int b, int l) { return mu[a] * m.mv[b] * m.mx[l]; };
+  if (i > j) { const int x = i; i = j; j = x; }
+  if (DIM == 2) {
+    switch (i * 4 + j) {
+      case 0: return M(s, t, 0);
+      case 1: return M(s + 1, t, 0);
+      case 2: return M(s, t + 1, 0);
+      case 3: return 0.5 * (M(s + 2, t, 0) + M(s, t + 2, 0) + M(s, t, 1));
+      case 5: return M(s + 2, t, 0);
+      case 6: return M(s + 1, t + 1, 0);
+      case 7: return 0.5 * (M(s + 3, t, 0) + M(s + 1, t + 2, 0) + M(s + 1, t, 1));
+      case 10: return M(s, t + 2, 0);
+      case 11: return 0.5 * (M(s + 2, t + 1, 0) + M(s, t + 3, 0) + M(s, t + 1, 1));
+      default:
+        return 0.25 * (M(s + 4, t, 0) + M(s, t + 4, 0) + M(s, t, 2)) +
+               0.5 * (M(s + 2, t + 2, 0) + M(s + 2, t, 1) + M(s, t + 2, 1));
+    }
+  }
+  switch (i * 3 + j) {
+    case 0: return M(s, 0, 0);
+    case 1: return M(s + 1, 0, 0);
+    case 2: return 0.5 * (M(s + 2, 0, 0) + M(s, 0, 1));
+    case 4: return M(s + 2, 0, 0);
+    case 5: return 0.5 * (M(s + 3, 0, 0) + M(s + 1, 0, 1));
+    default: return 0.25 * (M(s + 4, 0, 0) + M(s, 0, 2)) + 0.5 * M(s + 2, 0, 1);
+  }
+}
+
+// out_i = rho sum_j a_j <u^s v^t psi_j psi_i>
+template <int DIM>
+__device__ __forceinline__ void slope_moments(const double* a, int s, int t, const double* mu, const Maxw& m,
+                                              double* out) {
+  constexpr int n = DIM + 2;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < n; ++j) acc = fma(a[j], mom2<DIM>(i, j, s, t, mu, m), acc);
+    out[i] = m.rho * acc;
+  }
+}
+
+// a with <psi psi^T> a = b (Appendix A closed form; b = W_x / rho)
+template <int DIM>
+__device__ __forceinline__ void solve_slope(const Maxw& m, double K, const double* b, double* a) {
+  const double l = m.lam, U = m.U, V = m.V;
+  if (DIM == 2) {
+    const double D = K + 2.0;
+    const double q = U * U + V * V + D / (2.0 * l);
+    const double R4 = 2.0 * b[3] - q * b[0], R3 = b[2] - V * b[0], R2 = b[1] - U * b[0];
+    a[3] = 4.0 * l * l / D * (R4 - 2.0 * U * R2 - 2.0 * V * R3);
+    a[2] = 2.0 * l * R3 - V * a[3];
+    a[1] = 2.0 * l * R2 - U * a[3];
+    a[0] = b[0] - U * a[1] - V * a[2] - 0.5 * a[3] * q;
+  } else {
+    const double D = K + 1.0;
+    const double q = U * U + D / (2.0 * l);
+    const double R3 = 2.0 * b[2] - q * b[0], R2 = b[1] - U * b[0];
+    a[2] = 4.0 * l * l / D * (R3 - 2.0 * U * R2);
+    a[1] = 2.0 * l * R2 - U * a[2];
+    a[0] = b[0] - U * a[1] - 0.5 * a[2] * q;
+  }
+}
+
+template <int DIM>
+__device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly, const double* Wr,
+                          const double* Wrx, const double* Wry, double gamma, double dt, double* F, double* Ft) {
+  constexpr int n = DIM + 2;
+  const double K = (DIM == 2) ? (4.0 - 2.0 * gamma) / (gamma - 1.0) : (3.0 - gamma) / (gamma - 1.0);
+  Maxw gl, gr;
+  maxw_init<DIM>(Wl, gamma, K, gl);
+  maxw_init<DIM>(Wr, gamma, K, gr);
+  double b[4], alx[4], aly[4], arx[4], ary[4];
+#pragma unroll
+  for (int i = 0; i < n; ++i) b[i] = Wlx[i] / gl.rho;
+  solve_slope<DIM>(gl, K, b, alx);
+#pragma unroll
+  for (int i = 0; i < n; ++i) b[i] = Wrx[i] / gr.rho;
+  solve_slope<DIM>(gr, K, b, arx);
+  if (DIM == 2) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) b[i] = Wly[i] / gl.rho;
+    solve_slope<DIM>(gl, K, b, aly);
+#pragma unroll
+    for (int i = 0; i < n; ++i) b[i] = Wry[i] / gr.rho;
+    solve_slope<DIM>(gr, K, b, ary);
+  }
+  double mlp[7], mrn[7];
+  half_moments(gl, true, mlp);
+  half_moments(gr, false, mrn);
+  // kinetic-weighted equilibrium state and its derivatives
+  double Wc[4], Wcx[4], Wcy[4], t1[4], t2[4];
+#pragma unroll
+  for (int i = 0; i < n; ++i) Wc[i] = gl.rho * mom1<DIM>(i, 0, 0, mlp, gl) + gr.rho * mom1<DIM>(i, 0, 0, mrn, gr);
+  slope_moments<DIM>(alx, 0, 0, mlp, gl, t1);
+  slope_moments<DIM>(arx, 0, 0, mrn, gr, t2);
+#pragma unroll
+  for (int i = 0; i < n; ++i) Wcx[i] = t1[i] + t2[i];
+  if (DIM == 2) {
+    slope_moments<DIM>(aly, 0, 0, mlp, gl, t1);
+    slope_moments<DIM>(ary, 0, 0, mrn, gr, t2);
+#pragma unroll
+    for (int i = 0; i < n; ++i) Wcy[i] = t1[i] + t2[i];
+  }
+  Maxw gc;
+  maxw_init<DIM>(Wc, gamma, K, gc);
+  double acx[4], acy[4] = {0.0, 0.0, 0.0, 0.0}, Ac[4];
+#pragma unroll
+  for (int i = 0; i < n; ++i) b[i] = Wcx[i] / gc.rho;
+  solve_slope<DIM>(gc, K, b, acx);
+  if (DIM == 2) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) b[i] = Wcy[i] / gc.rho;
+    solve_slope<DIM>(gc, K, b, acy);
+  }
+  // compatibility: <psi psi^T> A = -(<u a_x psi> + <v a_y psi>)
+  slope_moments<DIM>(acx, 1, 0, gc.mu, gc, t1);
+  if (DIM == 2) slope_moments<DIM>(acy, 0, 1, gc.mu, gc, t2);
+#pragma unroll
+  for (int i = 0; i < n; ++i) b[i] = -(t1[i] + (DIM == 2 ? t2[i] : 0.0)) / gc.rho;
+  solve_slope<DIM>(gc, K, b, Ac);
+  // flux vectors
+  double T0[4], T1[4], T2[4], T3[4], T4[4];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    T0[i] = gc.rho * mom1<DIM>(i, 1, 0, gc.mu, gc);
+    T3[i] = gl.rho * mom1<DIM>(i, 1, 0, mlp, gl) + gr.rho * mom1<DIM>(i, 1, 0, mrn, gr);
+  }
+  slope_moments<DIM>(acx, 2, 0, gc.mu, gc, T1);
+  slope_moments<DIM>(Ac, 1, 0, gc.mu, gc, T2);
+  slope_moments<DIM>(alx, 2, 0, mlp, gl, t1);
+  slope_moments<DIM>(arx, 2, 0, mrn, gr, t2);
+#pragma unroll
+  for (int i = 0; i < n; ++i) T4[i] = t1[i] + t2[i];
+  if (DIM == 2) {
+    slope_moments<DIM>(acy, 1, 1, gc.mu, gc, t1);
+#pragma unroll
+    for (int i = 0; i < n; ++i) T1[i] += t1[i];
+    slope_moments<DIM>(aly, 1, 1, mlp, gl, t1);
+    slope_moments<DIM>(ary, 1, 1, mrn, gr, t2);
+#pragma unroll
+    for (int i = 0; i < n; ++i) T4[i] += t1[i] + t2[i];
+  }
+  // numerical collision time and the time integrals over [0, dt] and [0, dt/2]
+  const double pl = 0.5 * gl.rho / gl.lam, pr = 0.5 * gr.rho / gr.lam;
+  const double taun = kGksC1 * dt + kGksC2 * fabs((pl - pr) / (pl + pr)) * dt;
+  double Fd[2][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double d = (h == 0) ? dt : 0.5 * dt;
+    const double e = exp(-d / taun);
+    const double c1 = d - taun * (1.0 - e);
+    const double c2 = taun * taun * (1.0 - e) - taun * d * e;
+    const double c3 = 0.5 * d * d;
+    const double c4 = taun * (1.0 - e);
+#pragma unroll
+    for (int i = 0; i < n; ++i) Fd[h][i] = c1 * T0[i] + c2 * (T1[i] - T4[i]) + c3 * T2[i] + c4 * T3[i];
+  }
+  const double idt = 1.0 / dt;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    F[i] = (4.0 * Fd[1][i] - Fd[0][i]) * idt;
+    Ft[i] = 4.0 * (Fd[0][i] - 2.0 * Fd[1][i]) * idt * idt;
+  }
+}
+
+// sigma of one Gauss point (Sec. 3.1) for physical states in the face frame
+template <int C, int NI, int TI>
+__device__ __forceinline__ double sigma_point(const double* qa, const double* qb, double gamma) {
+  const double ia = 1.0 / qa[0], ib = 1.0 / qb[0];
+  const double ua = qa[NI] * ia, ub = qb[NI] * ib;
+  const double wa = (C == 4) ? qa[TI] * ia : 0.0, wb = (C == 4) ? qb[TI] * ib : 0.0;
+  const double pa = (gamma - 1.0) * (qa[C - 1] - 0.5 * qa[0] * (ua * ua + wa * wa));
+  const double pb = (gamma - 1.0) * (qb[C - 1] - 0.5 * qb[0] * (ub * ub + wb * wb));
+  const double ca = sqrt(gamma * pa * ia), cb = sqrt(gamma * pb * ib);
+  const double dp = fabs(pa - pb);
+  const double dmn = ua / ca - ub / cb;
+  double s = dp / pa + dp / pb + dmn * dmn;
+  if (C == 4) {
+    const double dmt = wa / ca - wb / cb;
+    s += dmt * dmt;
+  }
+  return s;
+}
+
+template <int C>
+__device__ __forceinline__ bool gks_physical(const double* q, double gamma) {
+  double mm = q[1] * q[1];
+  if (C == 4) mm = fma(q[2], q[2], mm);
+  const double pr = (gamma - 1.0) * fma(q[C - 1], q[0], -0.5 * mm);
+  return pos_finite(q[0]) && pos_finite(pr);
+}
+
+// ---------------------------------------------------------------------------------
+// the face kernel
+// ---------------------------------------------------------------------------------
+template <int R, int DIM>
+struct GksTile {
+  using TL = Tile<R, DIM>;
+  static constexpr size_t smem_doubles = TL::smem_doubles + 2 * (size_t)TL::C * TL::NB * TL::NQ;
+};
+
+template <int R, int DIM, int DIR>
+__global__ void __launch_bounds__(Tile<R, DIM>::NT, 1)
+gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constant__ Tables T,
+                 const __grid_constant__ DTables D) {
+  using TL = Tile<R, DIM>;
+  constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
+  constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
+  constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
+  constexpr int NI = (DIR == 0) ? 1 : 2;
+  constexpr int TI = (DIR == 0) ? 2 : 1;
+
+  extern __shared__ double smem[];
+  double* sW = smem;                 // [C][NB][NA]
+  double* sQP = sW + C * NB * NA;    // values at xi = 0 / -1
+  double* sQM = sQP + C * NB * NQ;
+  double* sSn = sQM + C * NB * NQ;
+  double* sSt = sSn + NB * NSN;
+  double* sDP = sSt + (DIM == 2 ? NQ * NST : 0);  // normal derivatives (physical) at xi = 0 / -1
+  double* sDM = sDP + C * NB * NQ;
+
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const int a0 = blockIdx.x * TN, b0 = blockIdx.y * TT;
+  const int tid = threadIdx.x;
+  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
+  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
+  const double dt = args.dt_fixed > 0.0 ? args.dt_fixed : args.st->dt;
+
+  for (int idx = tid; idx < C * NB * NA; idx += NT) {
+    int c, bb, ai;
+    if (DIR == 0) { ai = idx % NA; bb = (idx / NA) % NB; c = idx / (NA * NB); }
+    else { bb = idx % NB; ai = (idx / NB) % NA; c = idx / (NA * NB); }
+    const int a = a0 - 1 - K + ai, b = b0 - KT + bb;
+    const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
+    sW[(c * NB + bb) * NA + ai] = fetch_w(g, args.W, c, i, j);
+  }
+  for (int idx = tid; idx < NB * NSN; idx += NT) {
+    const int fa = idx % NSN, bb = idx / NSN;
+    const int f = face_map(a0 - K + fa, n, bcn_lo, bcn_hi);
+    const int b = wrap_or_clamp(b0 - KT + bb, mlin, bct_lo, bct_hi);
+    sSn[bb * NSN + fa] = (DIR == 0) ? args.s_norm[(size_t)b * (g.nx + 1) + f] : args.s_norm[(size_t)f * g.nx + b];
+  }
+  if (DIM == 2) {
+    for (int idx = tid; idx < NQ * (NST - 1); idx += NT) {
+      const int qa = idx % NQ, fb = idx / NQ;
+      const int a = wrap_or_clamp(a0 - 1 + qa, n, bcn_lo, bcn_hi);
+      const int f = face_map(b0 - K + 1 + fb, mlin, bct_lo, bct_hi);
+      sSt[qa * NST + fb] = (DIR == 0) ? args.s_tan[(size_t)f * g.nx + a] : args.s_tan[(size_t)a * (g.nx + 1) + f];
+    }
+  }
+  __syncthreads();
+  // phase 1: value and normal derivative of every cell of the band at both faces
+  for (int it = tid; it < NQ * NB; it += NT) {
+    const int qa = it % NQ, bb = it / NQ;
+    const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const double* v = sW + (c * NB + bb) * NA + qa + K;
+      double out[2], dout[2];
+      recon_eval_d<R, 2>(v, 1, br, T, D, 0, out, dout);
+      sQP[(c * NB + bb) * NQ + qa] = out[0];
+      sQM[(c * NB + bb) * NQ + qa] = out[1];
+      sDP[(c * NB + bb) * NQ + qa] = dout[0] * args.inv_dn;
+      sDM[(c * NB + bb) * NQ + qa] = dout[1] * args.inv_dn;
+    }
+  }
+  __syncthreads();
+
+  for (int it = tid; it < TN * TT; it += NT) {
+    int fa, tb;
+    if (DIR == 0) { fa = it % TN; tb = it / TN; }
+    else { tb = it % TT; fa = it / TT; }
+    const int f = a0 + fa, b = b0 + tb;
+    if (f > n || b >= mlin) continue;
+    double st[2][G][C], sx_[2][G][C], sy_[2][G][C];  // value, normal and tangential derivative
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int qa = fa + side;
+      const double* Q = side == 0 ? sQP : sQM;
+      const double* Dn = side == 0 ? sDP : sDM;
+      if (DIM == 2) {
+        const Branch bt = select_branch<R>(sSt + qa * NST + tb, g.thres);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          double out[G], dout[G], nout[G];
+          recon_eval_d<R, G>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt, T, D, 2, out, dout);
+          recon_eval<R, G>(Dn + (c * NB + tb + K) * NQ + qa, NQ, bt, T, 2, nout);
+#pragma unroll
+          for (int q = 0; q < G; ++q) {
+            st[side][q][c] = out[q];
+            sy_[side][q][c] = dout[q] * args.inv_dt;
+            sx_[side][q][c] = nout[q];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          st[side][0][c] = Q[c * NQ + qa];
+          sx_[side][0][c] = Dn[c * NQ + qa];
+          sy_[side][0][c] = 0.0;
+        }
+      }
+    }
+    double ca[C], cb[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      ca[c] = sW[(c * NB + tb + KT) * NA + fa + K];
+      cb[c] = sW[(c * NB + tb + KT) * NA + fa + K + 1];
+    }
+    double Fs[C], Fts[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) Fs[c] = Fts[c] = 0.0;
+    double ssum = 0.0;
+    bool anyfb = false;
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      // face frame: (rho, m_n, m_t, E)
+      double ql[C], qr[C], qlx[C], qrx[C], qly[C], qry[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
+        ql[c] = st[0][q][src];
+        qr[c] = st[1][q][src];
+        qlx[c] = sx_[0][q][src];
+        qrx[c] = sx_[1][q][src];
+        qly[c] = sy_[0][q][src];
+        qry[c] = sy_[1][q][src];
+      }
+      double sg;
+      if (!(gks_physical<C>(ql, g.gamma) && gks_physical<C>(qr, g.gamma))) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
+          ql[c] = ca[src];
+          qr[c] = cb[src];
+          qlx[c] = qrx[c] = qly[c] = qry[c] = 0.0;
+        }
+        sg = kSigmaBig;
+        anyfb = true;
+      } else {
+        sg = sigma_point<C, 1, 2>(ql, qr, g.gamma);
+      }
+      double Fq[C], Ftq[C];
+      gks_point<DIM>(ql, qlx, qly, qr, qrx, qry, g.gamma, dt, Fq, Ftq);
+      const double w = (DIM == 2) ? T.gw[q] : 1.0;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int dst = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
+        Fs[dst] = fma(w, Fq[c], Fs[dst]);
+        Fts[dst] = fma(w, Ftq[c], Fts[dst]);
+      }
+      ssum += sg;
+    }
+    if (anyfb) atomicOr(&const_cast<DevState*>(args.st)->flags, 0x2u);
+    const double sface = (G == 1) ? ssum : ssum * (1.0 / G);
+    if (DIR == 0) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        args.F[((size_t)c * g.ny + b) * (g.nx + 1) + f] = Fs[c];
+        args.Ft[((size_t)c * g.ny + b) * (g.nx + 1) + f] = Fts[c];
+      }
+      args.s_out[(size_t)b * (g.nx + 1) + f] = sface;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        args.F[((size_t)c * (g.ny + 1) + f) * g.nx + b] = Fs[c];
+        args.Ft[((size_t)c * (g.ny + 1) + f) * g.nx + b] = Fts[c];
+      }
+      args.s_out[(size_t)f * g.nx + b] = sface;
+    }
+  }
+}
+
+template <int R, int DIM, int DIR>
+cudaError_t gks_launch(const GridInfo& g, const GksSweepArgs& a, const Tables& t, const DTables& d,
+                       cudaStream_t s) {
+  using TL = Tile<R, DIM>;
+  const size_t smem = GksTile<R, DIM>::smem_doubles * sizeof(double);
+  auto k = gks_sweep_kernel<R, DIM, DIR>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int m = (DIR == 0) ? g.ny : g.nx;
+  dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
+  k<<<grid, TL::NT, smem, s>>>(g, a, t, d);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define ASE_DF_CAT2(a, b) a##b
+#define ASE_DF_CAT(a, b) ASE_DF_CAT2(a, b)
+
+cudaError_t ASE_DF_CAT(launch_gks_sweep_r, ASE_DF_ORDER)(int dim, int dir, const GridInfo& g, const GksSweepArgs& a,
+                                                         const Tables& t, const DTables& d, cudaStream_t s) {
+  constexpr int R = ASE_DF_ORDER;
+  if (dim == 1) return gks_launch<R, 1, 0>(g, a, t, d, s);
+  if (dir == 0) return gks_launch<R, 2, 0>(g, a, t, d, s);
+  return gks_launch<R, 2, 1>(g, a, t, d, s);
+}
+
+}  // namespace asedf

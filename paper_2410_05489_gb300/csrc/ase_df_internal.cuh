@@ -38,6 +38,13 @@ struct Tables {
   double eps;        // 1e-6 (Sec. 3.2)
 };
 
+// Derivative weights (d/dxi) of the same polynomials at the same points, for the
+// gas-kinetic flux (which needs the slopes of the reconstructed states).
+struct DTables {
+  double dlin[4][kMaxPts][9];
+  double dsub[3][kMaxPts][3];
+};
+
 // Positivity repair of a stage update (the paper's transition to first order for
 // positivity): at most this many passes per RK stage.
 constexpr int kRepairPasses = 8;
@@ -131,5 +138,6 @@ cudaError_t launch_state_kernel(DevState* st, int op, double t, cudaStream_t s);
 
 // Tables of scheme order r (host, exact rational arithmetic).
 void build_tables(int r, int ndim, Tables* out);
+void build_dtables(int r, int ndim, DTables* out);
 
 }  // namespace asedf

@@ -138,7 +138,59 @@ void point_weights_ld(const std::vector<std::vector<Rat>>& inv, long double xi, 
   }
 }
 
+// Derivative weights d/dxi of the polynomial at point xi: sum_q q xi^(q-1) inv[q][i].
+void deriv_weights_rat(const std::vector<std::vector<Rat>>& inv, Rat xi, double* w) {
+  const int n = (int)inv.size();
+  for (int i = 0; i < n; ++i) {
+    Rat s = mk(0, 1);
+    Rat xp = mk(1, 1);
+    for (int q = 1; q < n; ++q) {
+      s = add(s, mul(mul(mk(q, 1), xp), inv[q][i]));
+      xp = mul(xp, xi);
+    }
+    w[i] = to_d(s);
+  }
+}
+
+void deriv_weights_ld(const std::vector<std::vector<Rat>>& inv, long double xi, double* w) {
+  const int n = (int)inv.size();
+  for (int i = 0; i < n; ++i) {
+    long double s = 0;
+    for (int q = n - 1; q >= 1; --q) s = s * xi + (long double)q * to_ld(inv[q][i]);  // Horner
+    w[i] = (double)s;
+  }
+}
+
 }  // namespace
+
+void build_dtables(int r, int ndim, DTables* D) {
+  std::memset(D, 0, sizeof(DTables));
+  const int G = (ndim == 2) ? (r == 3 ? 1 : (r - 1) / 2) : 1;
+  long double gt[4], gwt[4];
+  gauss_legendre(G, gt, gwt);
+  const int npts = 2 + G;
+  auto eval_all = [&](const std::vector<std::vector<Rat>>& inv, int p, double* w) {
+    if (p == 0) deriv_weights_rat(inv, mk(0, 1), w);
+    else if (p == 1) deriv_weights_rat(inv, mk(-1, 1), w);
+    else deriv_weights_ld(inv, gt[p - 2] - 1.0L, w);
+  };
+  for (int b = 0; b < 4; ++b) {
+    const int h = b + 1;
+    std::vector<int> offs;
+    for (int o = -h; o <= h; ++o) offs.push_back(o);
+    auto inv = moment_inverse(offs);
+    for (int p = 0; p < npts; ++p) {
+      double w[9];
+      eval_all(inv, p, w);
+      for (int i = 0; i < 2 * h + 1; ++i) D->dlin[b][p][4 - h + i] = w[i];
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    std::vector<int> offs = {k - 2, k - 1, k};
+    auto inv = moment_inverse(offs);
+    for (int p = 0; p < npts; ++p) eval_all(inv, p, D->dsub[k][p]);
+  }
+}
 
 void build_tables(int r, int ndim, Tables* T) {
   std::memset(T, 0, sizeof(Tables));
