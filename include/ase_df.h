@@ -81,6 +81,10 @@ typedef struct {
   double inflow_state[4];  /* primitive (rho, u, v, p) of an x-lo inflow band */
   double inflow_lo, inflow_hi;
   double t_end;            /* > 0: CFL steps are shortened so that t never passes t_end */
+  double gks_c1, gks_c2;   /* gas-kinetic path: tau_n = c1 dt + c2 |p_l - p_r| / (p_l + p_r) dt
+                              (Sec. 2.2); <= 0 takes 0.05 and 1.0, the values of the paper's
+                              figure captions for Configuration 3, Shu-Osher and the double Mach
+                              reflection (5.0 for c2 in its blast wave) */
 } ase_df_params;
 
 typedef struct ase_df_ctx ase_df_ctx;
@@ -221,8 +225,9 @@ ase_df_status ase_df_residual_noalloc(const ase_df_params* p, const double* W, c
  * feedback) also provides the normal and tangential derivatives of each side's state at
  * the Gauss points; the flux of the BGK distribution function of Eq. (GKS flux), with
  * the physical collision time 0 (inviscid flow) and the numerical collision time
- * tau_n = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt (C1 = 0.01, C2 = 1), is integrated over
- * [0, dt] and [0, dt/2], giving the face flux F and its time derivative F_t.  A Gauss
+ * tau_n = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt, is integrated over
+ * [0, dt] and [0, dt/2], giving the face flux F and its time derivative F_t; C1, C2 are
+ * ase_df_params.gks_c1, gks_c2.  A Gauss
  * point with a non-physical state takes the two cell averages with zero derivatives
  * (sigma 1e30, ASE_DF_FLAG_POSITIVITY).  There is no positivity repair on this path.
  * --------------------------------------------------------------------------------- */

@@ -185,6 +185,7 @@ struct OracleParams {
   int32_t bc[4];       // x-lo, x-hi, y-lo, y-hi
   double inflow[4];    // rho, u, v, p of the x-lo inflow band
   double inflow_lo, inflow_hi;  // the band is inflow_lo < y < inflow_hi
+  double gks_c1, gks_c2;        // tau_n constants of the gas-kinetic path (reading G24)
 };
 
 namespace {
@@ -1207,11 +1208,11 @@ void oracle_reset_op_counts() { g_ops = {0, 0, 0, 0}; }
 // the kinetic-weighted derivatives, and A^c from the compatibility condition
 // <a_x u + a_y v + A> = 0.  From F(dt) and F(dt/2) the linear-in-time flux F + t F_t
 // follows (Sec. 2.2): F = (4 F(dt/2) - F(dt)) / dt, F_t = 4 (F(dt) - 2 F(dt/2)) / dt^2.
-// tau_n = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt (reading G24: C1 = 0.01, C2 = 1).
+// tau_n = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt (reading G24: C1, C2 are problem
+// parameters; the paper's captions give C1 = 0.05, C2 = 1.0, and C2 = 5.0 for its blast
+// wave).
 // =================================================================================
 namespace {
-
-const double kGksC1 = 0.01, kGksC2 = 1.0;
 
 // A monomial c u^a v^b (xi^2)^l of the particle velocity (u, v) and the internal
 // variable (xi^2 = the sum of squares of the K internal components).
@@ -1336,8 +1337,8 @@ void slope_flux(const Maxwell& m, int dim, int su, int sv, const double* a, int 
 // The GKS flux at one Gauss point (face frame): left / right states, their normal (x)
 // and tangential (y, 2D) derivatives; dt of the step.  Writes F (value at t_n) and F_t.
 void gks_point(int dim, double gamma, const double* Wl, const double* Wlx, const double* Wly,
-               const double* Wr, const double* Wrx, const double* Wry, double dt, double* F,
-               double* Ft) {
+               const double* Wr, const double* Wrx, const double* Wry, double dt, double C1, double C2,
+               double* F, double* Ft) {
   const int n = dim + 2;
   const Maxwell gl = maxwell(Wl, dim, gamma), gr = maxwell(Wr, dim, gamma);
   double alx[4] = {0, 0, 0, 0}, aly[4] = {0, 0, 0, 0}, arx[4] = {0, 0, 0, 0}, ary[4] = {0, 0, 0, 0};
@@ -1402,7 +1403,7 @@ void gks_point(int dim, double gamma, const double* Wl, const double* Wlx, const
   // numerical collision time (reading G24) and the time integrals
   const double pl = (gamma - 1.0) * (Wl[n - 1] - 0.5 * (Wl[1] * Wl[1] + (dim == 2 ? Wl[2] * Wl[2] : 0.0)) / Wl[0]);
   const double pr = (gamma - 1.0) * (Wr[n - 1] - 0.5 * (Wr[1] * Wr[1] + (dim == 2 ? Wr[2] * Wr[2] : 0.0)) / Wr[0]);
-  const double taun = kGksC1 * dt + kGksC2 * std::fabs((pl - pr) / (pl + pr)) * dt;
+  const double taun = C1 * dt + C2 * std::fabs((pl - pr) / (pl + pr)) * dt;
   double Fd[2][4];
   for (int h = 0; h < 2; ++h) {
     const double d = (h == 0) ? dt : 0.5 * dt;
@@ -1524,7 +1525,8 @@ void gks_face_fluxes(const Grid& g, const double* Wd, const double* sx_in, const
           sg = sigma_point(L, R, C);
         }
         double F[4], Ft[4];
-        gks_point(dim, gamma, ql, qlx, qly, qr, qrx, qry, dt, F, Ft);
+        const double C1 = g.p->gks_c1 > 0.0 ? g.p->gks_c1 : 0.05, C2 = g.p->gks_c2 > 0.0 ? g.p->gks_c2 : 1.0;
+        gks_point(dim, gamma, ql, qlx, qly, qr, qrx, qry, dt, C1, C2, F, Ft);
         to_face_frame(F, dir, C);
         to_face_frame(Ft, dir, C);
         for (int c = 0; c < C; ++c) { Fs[c] += wq[q] * F[c]; Fts[c] += wq[q] * Ft[c]; }
@@ -1581,8 +1583,9 @@ extern "C" {
 
 // The GKS flux at one Gauss point in the face frame (tests).  Wly / Wry are ignored in 1D.
 void oracle_gks_point(int32_t dim, double gamma, const double* Wl, const double* Wlx, const double* Wly,
-                      const double* Wr, const double* Wrx, const double* Wry, double dt, double* F, double* Ft) {
-  gks_point(dim, gamma, Wl, Wlx, Wly, Wr, Wrx, Wry, dt, F, Ft);
+                      const double* Wr, const double* Wrx, const double* Wry, double dt, double c1, double c2,
+                      double* F, double* Ft) {
+  gks_point(dim, gamma, Wl, Wlx, Wly, Wr, Wrx, Wry, dt, c1, c2, F, Ft);
 }
 
 // L and L_t of one GKS evaluation with sigma_in -> sigma_out.

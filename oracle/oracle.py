@@ -53,6 +53,7 @@ class _Params(ctypes.Structure):
         ("gamma", ctypes.c_double), ("sigma_thres", ctypes.c_double), ("cfl", ctypes.c_double),
         ("bc", ctypes.c_int32 * 4), ("inflow", ctypes.c_double * 4),
         ("inflow_lo", ctypes.c_double), ("inflow_hi", ctypes.c_double),
+        ("gks_c1", ctypes.c_double), ("gks_c2", ctypes.c_double),
     ]
 
 
@@ -96,7 +97,8 @@ def _lib(counting: bool = False, tape: bool = False):
             lib.oracle_op_counts.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
             lib.oracle_reset_op_counts.argtypes = []
         if key == "plain":
-            lib.oracle_gks_point.argtypes = [ctypes.c_int32, ctypes.c_double] + [_P] * 6 + [ctypes.c_double, _P, _P]
+            lib.oracle_gks_point.argtypes = ([ctypes.c_int32, ctypes.c_double] + [_P] * 6 +
+                                             [ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P])
             lib.oracle_gks_point.restype = None
             lib.oracle_gks_residual.argtypes = [ctypes.POINTER(_Params), _P, _P, _P, ctypes.c_double, _P, _P, _P,
                                                 _P, _I64]
@@ -123,6 +125,7 @@ def _params(pb) -> _Params:
     for i in range(4):
         p.inflow[i] = pb.inflow[i]
     p.inflow_lo, p.inflow_hi = pb.inflow_lo, pb.inflow_hi
+    p.gks_c1, p.gks_c2 = pb.gks_c1, pb.gks_c2
     return p
 
 
@@ -311,14 +314,15 @@ def run_vjp(pb, W0, nsteps: int, dt: float, Wbar_final):
 # ----------------------------------------------------------------------------------
 # gas-kinetic flux and S2O4 (Sec. 2.2)
 # ----------------------------------------------------------------------------------
-def gks_point(dim: int, gamma: float, Wl, Wlx, Wly, Wr, Wrx, Wry, dt: float):
+def gks_point(dim: int, gamma: float, Wl, Wlx, Wly, Wr, Wrx, Wry, dt: float, c1: float = 0.05, c2: float = 1.0):
     """GKS flux at one Gauss point, face frame: -> (F, F_t)."""
     n = dim + 2
     arrs = [_f64(np.asarray(a, dtype=np.float64).reshape(-1)[:n]) if a is not None else np.zeros(n)
             for a in (Wl, Wlx, Wly, Wr, Wrx, Wry)]
     F = np.zeros(n)
     Ft = np.zeros(n)
-    _lib().oracle_gks_point(int(dim), float(gamma), *[_ptr(a) for a in arrs], float(dt), _ptr(F), _ptr(Ft))
+    _lib().oracle_gks_point(int(dim), float(gamma), *[_ptr(a) for a in arrs], float(dt), float(c1), float(c2),
+                            _ptr(F), _ptr(Ft))
     return F, Ft
 
 

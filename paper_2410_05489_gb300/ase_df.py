@@ -44,6 +44,7 @@ class ase_df_params(ctypes.Structure):
         ("bc", ctypes.c_int32 * 4), ("inflow_state", ctypes.c_double * 4),
         ("inflow_lo", ctypes.c_double), ("inflow_hi", ctypes.c_double),
         ("t_end", ctypes.c_double),
+        ("gks_c1", ctypes.c_double), ("gks_c2", ctypes.c_double),
     ]
 
 
@@ -103,6 +104,7 @@ def params_from_problem(pb: Problem, t_end: float = 0.0) -> ase_df_params:
         p.inflow_state[i] = pb.inflow[i]
     p.inflow_lo, p.inflow_hi = pb.inflow_lo, pb.inflow_hi
     p.t_end = t_end
+    p.gks_c1, p.gks_c2 = pb.gks_c1, pb.gks_c2
     return p
 
 

@@ -654,6 +654,8 @@ static cudaError_t gks_face_fluxes(ase_df_ctx* c, const double* W, const double*
     a.dt_fixed = dt_fixed;
     a.inv_dn = (dir == 0) ? c->inv_dx : c->inv_dy;
     a.inv_dt = (dir == 0) ? c->inv_dy : c->inv_dx;
+    a.c1 = c->p.gks_c1 > 0.0 ? c->p.gks_c1 : 0.05;
+    a.c2 = c->p.gks_c2 > 0.0 ? c->p.gks_c2 : 1.0;
     cudaError_t e;
     ProfScope prof(c, s, dir);
     switch (c->p.order) {

@@ -14,7 +14,7 @@
 //   with the physical collision time 0 over [0, dt] and [0, dt/2]:
 //     F(d) = c1 T0 + c2 (T1 - T4) + c3 T2 + c4 T3,
 //     c1 = d - tn (1 - e), c2 = tn^2 (1 - e) - tn d e, c3 = d^2 / 2, c4 = tn (1 - e),
-//     e = exp(-d / tn), tn = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt  (C1 = 0.01, C2 = 1);
+//     e = exp(-d / tn), tn = C1 dt + C2 |p_l - p_r| / (p_l + p_r) dt (C1, C2 of the problem);
 //   T0 = rho_c <u psi>_c, T1 = rho_c <u (a_x^c u + a_y^c v) psi>_c, T2 = rho_c <u A^c psi>_c,
 //   T3 = rho_l <u psi>_{l,u>0} + rho_r <u psi>_{r,u<0}, T4 = the same with (a_x u + a_y v).
 //   F = (4 F(dt/2) - F(dt)) / dt and F_t = 4 (F(dt) - 2 F(dt/2)) / dt^2 (Sec. 2.2).
@@ -32,8 +32,6 @@
 
 namespace asedf {
 namespace {
-
-constexpr double kGksC1 = 0.01, kGksC2 = 1.0;
 
 // ---------------------------------------------------------------------------------
 // value and d/dxi of the chosen polynomial (Algorithm 1) at NP points p0..
@@ -247,7 +245,8 @@ __device__ __forceinline__ void solve_slope(const Maxw& m, double K, const doubl
 
 template <int DIM>
 __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly, const double* Wr,
-                          const double* Wrx, const double* Wry, double gamma, double dt, double* F, double* Ft) {
+                          const double* Wrx, const double* Wry, double gamma, double dt, double C1, double C2,
+                          double* F, double* Ft) {
   constexpr int n = DIM + 2;
   const double K = (DIM == 2) ? (4.0 - 2.0 * gamma) / (gamma - 1.0) : (3.0 - gamma) / (gamma - 1.0);
   Maxw gl, gr;
@@ -326,7 +325,7 @@ __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly
   }
   // numerical collision time and the time integrals over [0, dt] and [0, dt/2]
   const double pl = 0.5 * gl.rho / gl.lam, pr = 0.5 * gr.rho / gr.lam;
-  const double taun = kGksC1 * dt + kGksC2 * fabs((pl - pr) / (pl + pr)) * dt;
+  const double taun = C1 * dt + C2 * fabs((pl - pr) / (pl + pr)) * dt;
   double Fd[2][4];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -526,7 +525,7 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
         sg = sigma_point<C, 1, 2>(ql, qr, g.gamma);
       }
       double Fq[C], Ftq[C];
-      gks_point<DIM>(ql, qlx, qly, qr, qrx, qry, g.gamma, dt, Fq, Ftq);
+      gks_point<DIM>(ql, qlx, qly, qr, qrx, qry, g.gamma, dt, args.c1, args.c2, Fq, Ftq);
       const double w = (DIM == 2) ? T.gw[q] : 1.0;
 #pragma unroll
       for (int c = 0; c < C; ++c) {

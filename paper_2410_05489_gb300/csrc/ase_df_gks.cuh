@@ -18,6 +18,7 @@ struct GksSweepArgs {
   const DevState* st;     // dt of the step when dt_fixed <= 0
   double dt_fixed;        // > 0: the step's dt
   double inv_dn, inv_dt;  // 1/h along the sweep and across it
+  double c1, c2;          // tau_n = c1 dt + c2 |p_l - p_r| / (p_l + p_r) dt
 };
 
 struct GksCombineArgs {

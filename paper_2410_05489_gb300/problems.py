@@ -52,6 +52,8 @@ class Problem:
     inflow: Tuple[float, float, float, float] = (0.0, 0.0, 0.0, 0.0)
     inflow_lo: float = 0.0
     inflow_hi: float = 0.0
+    gks_c1: float = 0.05   # tau_n constants of the gas-kinetic path (Sec. 2.2; the paper's
+    gks_c2: float = 1.0    # captions give 0.05 and 1.0, and c2 = 5.0 for the blast wave)
 
     @property
     def ncomp(self) -> int:

@@ -46,7 +46,8 @@ def test_params_struct_layout_matches_header():
     assert ase_df_params.bc.offset == 80
     assert ase_df_params.inflow_state.offset == 96
     assert ase_df_params.t_end.offset == 144
-    assert ctypes.sizeof(ase_df_params) == 152
+    assert ase_df_params.gks_c1.offset == 152 and ase_df_params.gks_c2.offset == 160
+    assert ctypes.sizeof(ase_df_params) == 168
 
 
 def test_init_rejects_bad_parameters_without_a_device(lib):

@@ -132,6 +132,7 @@ def test_gks_reproduces_table1_on_gpu(A, golden):
 
     tab = golden("sin_wave_accuracy_tables.json")["table1_1d"]["r9"]
     pb, W = P.sin_wave_1d(40, 9)
+    pb = pb.replace(gks_c1=0.001)  # the accuracy runs' C1
     n = int(math.ceil(2.0 / pb.dx ** (9 / 4.0)))
     s = A.Solver(pb, W)
     try:

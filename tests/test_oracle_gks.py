@@ -7,9 +7,11 @@
   compatibility condition together must reproduce that exactly (Jacobians here by
   central differences of the closed-form Euler fluxes, independent of kinetic theory).
 * Mirror symmetry of a Riemann-type point (x -> -x).
-* Tables 1 and 2 of Sec. 4.2 (sin-waves, GKS + S2O4, dt = dx^(r/4)): the printed L1
-  errors are reproduced -- 1-D at N = 20 and 40 for orders 5, 7, 9 to 1 %, and the 2-D
-  diagonal wave at N = 20, order 7, to 2 %.
+* Tables 1 and 2 of Sec. 4.2 (sin-waves, GKS + S2O4, dt = dx^(r/4), C1 = 0.001): the
+  printed L1 errors are reproduced -- 1-D at N = 20 and 40 for orders 5, 7, 9 to 1 % (0.2 %
+  observed), and the 2-D diagonal wave at N = 20, order 7, to 2 %.  (With the C1 = 0.05 of
+  the paper's shock-case captions the 1-D errors come out 2 % higher; C1 = 0.001 is the
+  reading for the accuracy runs.)
 * Conservation on a periodic grid.
 """
 import math
@@ -98,6 +100,7 @@ def test_mirror_symmetry(oracle):
 
 def run_sin_wave_1d(oracle, N, r):
     pb, W = P.sin_wave_1d(N, r)
+    pb = pb.replace(gks_c1=0.001)  # reading G24: the accuracy runs' C1 (not printed)
     n = int(math.ceil(2.0 / pb.dx ** (r / 4.0)))  # dt = dx^(r/s), s = 4 (S2O4), reading G28
     Wn, *_ = oracle.gks_run(pb, W, nsteps=n, dt=2.0 / n)
     ex = P.sin_wave_1d_exact(pb, 2.0)
@@ -116,6 +119,7 @@ def test_sin_wave_2d_reproduces_table2(oracle, golden):
     """The diagonal wave at N = 20, order 7 (dt = dx^(7/4), below the CFL limit)."""
     tab = golden("sin_wave_accuracy_tables.json")["table2_2d"]["r7"]
     pb, W = P.sin_wave_2d_diag(20, 7)
+    pb = pb.replace(gks_c1=0.001)
     n = int(math.ceil(2.0 / pb.dx ** (7 / 4.0)))
     Wn, *_ = oracle.gks_run(pb, W, nsteps=n, dt=2.0 / n)
     ex = P.sin_wave_2d_diag_exact(pb, 2.0)
