@@ -672,6 +672,41 @@ def suite_bench(args):
                                            "gradient_over_plain_forward", "residual_adjoint_over_residual")},
                  "cpu_1core": {"tape_over_forward": round(rev / fwd, 2), "cores": 1,
                                "sample": "oracle tape (reverse mode incl. taping) vs plain oracle, 32^2, 2 steps"}})
+    # gas-kinetic path: Configuration 3, 20 S2O4 steps at 100^2 .. 400^2 (the workload of
+    # the paper's Table 4, whose single-core EPYC times are quoted as context)
+    table4 = {5: [5.974, 23.116, 51.349, 90.954], 7: [9.053, 32.852, 72.788, 128.006],
+              9: [10.803, 42.554, 94.64, 165.221]}
+    for r in (5, 7, 9):
+        per_n = []
+        for k, nn in enumerate((100, 200, 300, 400)):
+            pb, W0 = P.configuration3(nn, r)
+            s = A.Solver(pb, W0)
+            for _ in range(2):
+                s.gks_step()
+            s.set_state(W0)
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record()
+            for _ in range(20):
+                s.gks_step()
+            e1.record()
+            e1.synchronize()
+            gms = e0.elapsed_time(e1)
+            flags = s.status()[0]
+            s.close()
+            per_n.append({"n": nn, "ms_20_steps": round(gms, 3),
+                          "value": round(pb.ncells * 2 * 20 / (gms * 1e-3) / 1e6, 3), "flags": flags,
+                          "paper_cpu_s_20_steps": table4[r][k],
+                          "paper_cpu_over_gpu": round(table4[r][k] / (gms * 1e-3), 1)})
+        pbc, Wc = P.configuration3(100, r)
+        sxc, syc = O.prime_sigma(pbc, Wc)
+        t0 = time.perf_counter()
+        O.gks_residual(pbc, Wc, sxc, syc, 0.5 * O.cfl_dt(pbc, Wc))
+        one = time.perf_counter() - t0
+        rows.append({"config": "GKS + S2O4, Configuration 3, r=%d, 20 CFL steps (Table 4 workload)" % r,
+                     "gpu": per_n, "unit": "Mcell-updates/s per stage (2 stages per S2O4 step)",
+                     "cpu_1core": {"value": round(pbc.ncells / one / 1e6, 4), "cores": 1,
+                                   "sample": "one GKS stage of Configuration 3 at 100^2, oracle"}})
     print(json.dumps({"suite": rows, "cores": cores}), flush=True)
 
 

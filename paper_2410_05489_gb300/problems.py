@@ -258,6 +258,20 @@ def riemann_2d(n: int, order: int, seed: int, ny: int | None = None) -> Tuple[Pr
     return pb, np.ascontiguousarray(conservative((rho[q], u[q], v[q], p[q]), pb.gamma, 2))
 
 
+def configuration3(n: int, order: int, gks_c1: float = 0.05, gks_c2: float = 1.0) -> Tuple[Problem, np.ndarray]:
+    """Configuration 3 of Sec. 4.3 (Example 2): [0,1]^2, quadrant states split at
+    (0.7, 0.7), outflow, gamma 1.4; the workload of the paper's timing table (Table 4)."""
+    pb = Problem(ndim=2, nx=n, ny=n, order=order, gamma=1.4, gks_c1=gks_c1, gks_c2=gks_c2)
+    x = (np.arange(n) + 0.5) * pb.dx
+    X, Y = np.meshgrid(x, x)
+    lo_x, lo_y = X < 0.7, Y < 0.7
+    rho = np.where(lo_x & lo_y, 0.138, np.where(~lo_x & lo_y, 0.5323, np.where(~lo_x & ~lo_y, 1.5, 0.5323)))
+    u = np.where(lo_x & lo_y, 1.206, np.where(~lo_x & lo_y, 0.0, np.where(~lo_x & ~lo_y, 0.0, 1.206)))
+    v = np.where(lo_x & lo_y, 1.206, np.where(~lo_x & lo_y, 1.206, np.where(~lo_x & ~lo_y, 0.0, 0.0)))
+    p = np.where(lo_x & lo_y, 0.129, np.where(~lo_x & lo_y, 0.3, np.where(~lo_x & ~lo_y, 1.5, 0.3)))
+    return pb, np.ascontiguousarray(conservative((rho, u, v, p), pb.gamma, 2))
+
+
 def smooth_random(pb: Problem, seed: int, nmodes: int = 3) -> np.ndarray:
     """Random smooth periodic Fourier field with O(1) relative variation."""
     rng = np.random.default_rng(seed)
