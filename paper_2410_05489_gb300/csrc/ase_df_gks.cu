@@ -376,17 +376,22 @@ __device__ __forceinline__ bool gks_physical(const double* q, double gamma) {
 // ---------------------------------------------------------------------------------
 // the face kernel
 // ---------------------------------------------------------------------------------
+// 16 x 16 faces per CTA in 2D (one face per thread): the gas-kinetic flux needs ~255
+// registers, so one CTA runs per SM, and the smaller tile gives more CTAs per grid.
+template <int R, int DIM>
+using GksTileShape = Tile<R, DIM, (DIM == 2) ? 16 : 1>;
+
 template <int R, int DIM>
 struct GksTile {
-  using TL = Tile<R, DIM>;
+  using TL = GksTileShape<R, DIM>;
   static constexpr size_t smem_doubles = TL::smem_doubles + 2 * (size_t)TL::C * TL::NB * TL::NQ;
 };
 
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(Tile<R, DIM>::NT, 1)
+__global__ void __launch_bounds__(GksTileShape<R, DIM>::NT, 1)
 gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constant__ Tables T,
                  const __grid_constant__ DTables D) {
-  using TL = Tile<R, DIM>;
+  using TL = GksTileShape<R, DIM>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
   constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
   constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
@@ -456,34 +461,11 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
     else { tb = it % TT; fa = it / TT; }
     const int f = a0 + fa, b = b0 + tb;
     if (f > n || b >= mlin) continue;
-    double st[2][G][C], sx_[2][G][C], sy_[2][G][C];  // value, normal and tangential derivative
+    // tangential branches of the two sides' columns (from the same sigma_in)
+    Branch bt[2];
+    if (DIM == 2) {
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int qa = fa + side;
-      const double* Q = side == 0 ? sQP : sQM;
-      const double* Dn = side == 0 ? sDP : sDM;
-      if (DIM == 2) {
-        const Branch bt = select_branch<R>(sSt + qa * NST + tb, g.thres);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          double out[G], dout[G], nout[G];
-          recon_eval_d<R, G>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt, T, D, 2, out, dout);
-          recon_eval<R, G>(Dn + (c * NB + tb + K) * NQ + qa, NQ, bt, T, 2, nout);
-#pragma unroll
-          for (int q = 0; q < G; ++q) {
-            st[side][q][c] = out[q];
-            sy_[side][q][c] = dout[q] * args.inv_dt;
-            sx_[side][q][c] = nout[q];
-          }
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          st[side][0][c] = Q[c * NQ + qa];
-          sx_[side][0][c] = Dn[c * NQ + qa];
-          sy_[side][0][c] = 0.0;
-        }
-      }
+      for (int side = 0; side < 2; ++side) bt[side] = select_branch<R>(sSt + (fa + side) * NST + tb, g.thres);
     }
     double ca[C], cb[C];
 #pragma unroll
@@ -496,19 +478,36 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
     for (int c = 0; c < C; ++c) Fs[c] = Fts[c] = 0.0;
     double ssum = 0.0;
     bool anyfb = false;
-#pragma unroll
+    // one Gauss point at a time (keeps the live state small)
+#pragma unroll 1
     for (int q = 0; q < G; ++q) {
-      // face frame: (rho, m_n, m_t, E)
+      // each side's value, normal (x) and tangential (y) derivative, face frame
+      // (rho, m_n, m_t, E)
       double ql[C], qr[C], qlx[C], qrx[C], qly[C], qry[C];
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
-        ql[c] = st[0][q][src];
-        qr[c] = st[1][q][src];
-        qlx[c] = sx_[0][q][src];
-        qrx[c] = sx_[1][q][src];
-        qly[c] = sy_[0][q][src];
-        qry[c] = sy_[1][q][src];
+      for (int side = 0; side < 2; ++side) {
+        const int qa = fa + side;
+        const double* Q = side == 0 ? sQP : sQM;
+        const double* Dn = side == 0 ? sDP : sDM;
+        double* v = side == 0 ? ql : qr;
+        double* vx = side == 0 ? qlx : qrx;
+        double* vy = side == 0 ? qly : qry;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
+          if (DIM == 2) {
+            double o, d, nd;
+            recon_eval_d<R, 1>(Q + (src * NB + tb + K) * NQ + qa, NQ, bt[side], T, D, 2 + q, &o, &d);
+            recon_eval<R, 1>(Dn + (src * NB + tb + K) * NQ + qa, NQ, bt[side], T, 2 + q, &nd);
+            v[c] = o;
+            vx[c] = nd;
+            vy[c] = d * args.inv_dt;
+          } else {
+            v[c] = Q[src * NQ + qa];
+            vx[c] = Dn[src * NQ + qa];
+            vy[c] = 0.0;
+          }
+        }
       }
       double sg;
       if (!(gks_physical<C>(ql, g.gamma) && gks_physical<C>(qr, g.gamma))) {
@@ -558,7 +557,7 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
 template <int R, int DIM, int DIR>
 cudaError_t gks_launch(const GridInfo& g, const GksSweepArgs& a, const Tables& t, const DTables& d,
                        cudaStream_t s) {
-  using TL = Tile<R, DIM>;
+  using TL = GksTileShape<R, DIM>;
   const size_t smem = GksTile<R, DIM>::smem_doubles * sizeof(double);
   auto k = gks_sweep_kernel<R, DIM, DIR>;
   static bool attr = false;

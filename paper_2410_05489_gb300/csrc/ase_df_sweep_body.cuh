@@ -184,14 +184,14 @@ __device__ __forceinline__ void tang_eval(const double* v, int vs, const Branch&
   recon_eval<R, G>(v, vs, br, T, 2, out);
 }
 
-template <int R, int DIM>
+template <int R, int DIM, int TT_ = (DIM == 2) ? 32 : 1>
 struct Tile {
   static constexpr int K = (R - 1) / 2;
   static constexpr int C = (DIM == 1) ? 3 : 4;
   static constexpr int KT = (DIM == 2) ? K : 0;
   static constexpr int G = (DIM == 2) ? (R == 3 ? 1 : K) : 1;
   static constexpr int TN = (DIM == 2) ? 16 : 256;   // faces along the sweep
-  static constexpr int TT = (DIM == 2) ? 32 : 1;     // lines
+  static constexpr int TT = TT_;                     // lines
   static constexpr int NT = 256;                     // threads
   static constexpr int NA = TN + 1 + 2 * K;          // staged cells along the sweep
   static constexpr int NB = TT + 2 * KT;             // staged lines
