@@ -54,8 +54,11 @@ typedef enum {
 typedef enum {
   ASE_DF_BC_PERIODIC = 0,   /* ghost cells wrap around */
   ASE_DF_BC_OUTFLOW = 1,    /* zero-gradient: ghost cells copy the nearest interior cell */
-  ASE_DF_BC_INFLOW_BAND = 2 /* x-lo only: ghost cells whose centre y lies in
+  ASE_DF_BC_INFLOW_BAND = 2, /* x-lo only: ghost cells whose centre y lies in
                                (inflow_lo, inflow_hi) hold inflow_state; outflow elsewhere */
+  ASE_DF_BC_REFLECT = 3     /* reflecting wall: ghost cells mirror the interior about the wall
+                               face with the normal momentum negated (needs (r+1)/2 cells or
+                               more in that direction; not supported by the adjoint) */
 } ase_df_bc;
 
 /* Device status word bits (ase_df_get_status). */

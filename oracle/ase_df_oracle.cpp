@@ -172,7 +172,7 @@ static inline real kmax(real a, real b) { return rmax(a, b); }
 // ---------------------------------------------------------------------------------
 // Problem description.  Its own copy; the Python wrapper fills it field by field.
 // ---------------------------------------------------------------------------------
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2, BC_REFLECT = 3 };
 
 struct OracleParams {
   int32_t ndim;        // 1 or 2
@@ -527,23 +527,31 @@ struct Grid {
   int64_t nx, ny;
   double dx, dy;
 
+  // A reflecting wall mirrors the cells (and faces) about the wall face.
+  static int64_t mirror_cell(int64_t i, int64_t n) { return i < 0 ? -1 - i : 2 * n - 1 - i; }
   int64_t cell_x(int64_t i) const {
+    if (i >= 0 && i < nx) return i;
     int bc = (i < 0) ? p->bc[0] : p->bc[1];
+    if (bc == BC_REFLECT) return mirror_cell(i, nx);
     return bc == BC_PERIODIC ? wrap(i, nx) : clampi(i, 0, nx - 1);
   }
   int64_t cell_y(int64_t j) const {
     if (p->ndim == 1) return 0;
+    if (j >= 0 && j < ny) return j;
     int bc = (j < 0) ? p->bc[2] : p->bc[3];
+    if (bc == BC_REFLECT) return mirror_cell(j, ny);
     return bc == BC_PERIODIC ? wrap(j, ny) : clampi(j, 0, ny - 1);
   }
   int64_t face_x(int64_t f) const {  // x-face index 0..nx
     if (f >= 0 && f <= nx) return f;
     int bc = (f < 0) ? p->bc[0] : p->bc[1];
+    if (bc == BC_REFLECT) return f < 0 ? -f : 2 * nx - f;
     return bc == BC_PERIODIC ? wrap(f, nx) : clampi(f, 0, nx);
   }
   int64_t face_y(int64_t g) const {  // y-face index 0..ny
     if (g >= 0 && g <= ny) return g;
     int bc = (g < 0) ? p->bc[2] : p->bc[3];
+    if (bc == BC_REFLECT) return g < 0 ? -g : 2 * ny - g;
     return bc == BC_PERIODIC ? wrap(g, ny) : clampi(g, 0, ny);
   }
   // Conservative value of component c of (possibly ghost) cell (i, j).
@@ -553,7 +561,12 @@ struct Grid {
       if (yc > p->inflow_lo && yc < p->inflow_hi) return inflow_cons(c);
     }
     int64_t ii = cell_x(i), jj = cell_y(j);
-    return Wd[((int64_t)c * ny + jj) * nx + ii];
+    real v = Wd[((int64_t)c * ny + jj) * nx + ii];
+    // a reflecting wall negates the momentum normal to it
+    const bool rx = (i < 0 && p->bc[0] == BC_REFLECT) || (i >= nx && p->bc[1] == BC_REFLECT);
+    const bool ry = p->ndim == 2 && ((j < 0 && p->bc[2] == BC_REFLECT) || (j >= ny && p->bc[3] == BC_REFLECT));
+    if ((c == 1 && rx) || (c == 2 && ry)) v = -v;
+    return v;
   }
   real inflow_cons(int c) const {
     double rho = p->inflow[0], u = p->inflow[1], v = p->inflow[2], pr = p->inflow[3];

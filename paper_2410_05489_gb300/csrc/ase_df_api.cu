@@ -133,10 +133,17 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
   if (!(p.sigma_thres > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "sigma_thres must be > 0");
   if (!(p.cfl > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "cfl must be > 0");
   for (int s = 0; s < 4; ++s) {
-    if (p.bc[s] < 0 || p.bc[s] > 2) return fail(nullptr, ASE_DF_E_INVAL, "bad boundary code %d", p.bc[s]);
+    if (p.bc[s] < 0 || p.bc[s] > 3) return fail(nullptr, ASE_DF_E_INVAL, "bad boundary code %d", p.bc[s]);
     if (p.bc[s] == ASE_DF_BC_INFLOW_BAND && s != 0)
       return fail(nullptr, ASE_DF_E_INVAL, "the inflow band is supported on x-lo only");
     if (p.ndim == 1 && s >= 2) p.bc[s] = ASE_DF_BC_OUTFLOW;
+  }
+  {
+    const int64_t need = (p.order + 1) / 2;
+    if ((p.bc[0] == ASE_DF_BC_REFLECT || p.bc[1] == ASE_DF_BC_REFLECT) && p.nx < need)
+      return fail(nullptr, ASE_DF_E_INVAL, "a reflecting x-wall needs nx >= %lld", (long long)need);
+    if (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_REFLECT || p.bc[3] == ASE_DF_BC_REFLECT) && p.ny < need)
+      return fail(nullptr, ASE_DF_E_INVAL, "a reflecting y-wall needs ny >= %lld", (long long)need);
   }
   if ((p.bc[0] == ASE_DF_BC_PERIODIC) != (p.bc[1] == ASE_DF_BC_PERIODIC))
     return fail(nullptr, ASE_DF_E_INVAL, "periodic boundaries must come in pairs (x)");
@@ -548,6 +555,8 @@ ase_df_status ase_df_residual_adjoint(ase_df_ctx* c, const double* W, const doub
   ase_df_status r = check_ptrs(c, W, sx_in, sy_in);
   if (r != ASE_DF_OK) return r;
   if (!Wbar) return fail(c, ASE_DF_E_INVAL, "Wbar is NULL");
+  for (int b = 0; b < 4; ++b)
+    if (c->g.bc[b] == BC_REFLECT) return fail(c, ASE_DF_E_INVAL, "the adjoint does not support reflecting walls");
   if (Wbar == W || Wbar == Lbar || (sxbar_in && (sxbar_in == sx_in || sxbar_in == sxbar_out)) ||
       (c->dim == 2 && sybar_in && (sybar_in == sy_in || sybar_in == sybar_out)))
     return fail(c, ASE_DF_E_INVAL, "adjoint outputs must not alias the inputs");
@@ -565,6 +574,8 @@ ase_df_status ase_df_step_adjoint(ase_df_ctx* c, const double* W, const double* 
   ase_df_status r = check_ptrs(c, W, sx, sy);
   if (r != ASE_DF_OK) return r;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ASE_DF_E_INVAL, "the step adjoint needs a fixed dt > 0");
+  for (int b = 0; b < 4; ++b)
+    if (c->g.bc[b] == BC_REFLECT) return fail(c, ASE_DF_E_INVAL, "the adjoint does not support reflecting walls");
   if (!Wbar || !sxbar || (c->dim == 2 && !sybar)) return fail(c, ASE_DF_E_INVAL, "NULL adjoint pointer");
   if (Wbar == W || sxbar == sx || (c->dim == 2 && sybar == sy))
     return fail(c, ASE_DF_E_INVAL, "adjoint arrays must not alias the state");

@@ -298,8 +298,14 @@ static bool valid_problem(ase_df_params& p, char* why, size_t nwhy) {
   if (!(p.x1 > p.x0) || (p.ndim == 2 && !(p.y1 > p.y0))) { snprintf(why, nwhy, "empty domain"); return false; }
   if (!(p.gamma > 1.0) || !(p.sigma_thres > 0.0) || !(p.cfl > 0.0)) { snprintf(why, nwhy, "bad gamma / sigma_thres / cfl"); return false; }
   for (int s = 0; s < 4; ++s) {
-    if (p.bc[s] < 0 || p.bc[s] > 2 || (p.bc[s] == ASE_DF_BC_INFLOW_BAND && s != 0)) { snprintf(why, nwhy, "bad boundary code"); return false; }
+    if (p.bc[s] < 0 || p.bc[s] > 3 || (p.bc[s] == ASE_DF_BC_INFLOW_BAND && s != 0)) { snprintf(why, nwhy, "bad boundary code"); return false; }
     if (p.ndim == 1 && s >= 2) p.bc[s] = ASE_DF_BC_OUTFLOW;
+  }
+  const int64_t need = (p.order + 1) / 2;
+  if (((p.bc[0] == ASE_DF_BC_REFLECT || p.bc[1] == ASE_DF_BC_REFLECT) && p.nx < need) ||
+      (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_REFLECT || p.bc[3] == ASE_DF_BC_REFLECT) && p.ny < need)) {
+    snprintf(why, nwhy, "a reflecting wall needs (order+1)/2 cells in its direction");
+    return false;
   }
   if ((p.bc[0] == ASE_DF_BC_PERIODIC) != (p.bc[1] == ASE_DF_BC_PERIODIC) ||
       (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_PERIODIC) != (p.bc[3] == ASE_DF_BC_PERIODIC))) {

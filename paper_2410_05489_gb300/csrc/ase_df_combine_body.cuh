@@ -22,6 +22,13 @@ __device__ __forceinline__ double rk_stage(int stage, double dt, double wn, doub
   return fma((2.0 / 3.0) * dt, L, fma(1.0 / 3.0, wn, (2.0 / 3.0) * ws));
 }
 
+// The flux difference -(dFx / dx + dFy / dy) as two rounded products and one add, so
+// that it is symmetric in the two directions bit for bit (a transposed problem with
+// dx = dy gives the transposed result).
+__device__ __forceinline__ double flux_div(double dFx, double inv_dx, double dFy, double inv_dy) {
+  return -__dadd_rn(__dmul_rn(dFx, inv_dx), __dmul_rn(dFy, inv_dy));
+}
+
 // rho > 0 and p > 0 (tested on p rho = (gamma-1)(E rho - |m|^2/2)), all finite.
 template <int C>
 __device__ __forceinline__ bool physical_state(const double* q, double gamma) {
@@ -68,7 +75,7 @@ __device__ __forceinline__ void combine_range(const GridInfo& g, const CombineAr
       double L = -(a.Fx[fx + 1] - a.Fx[fx]) * a.inv_dx;
       if (DIM == 2) {
         const size_t fy = ((size_t)c * (ny + 1) + j) * nx + i;
-        L = fma(-(a.Fy[fy + nx] - a.Fy[fy]), a.inv_dy, L);
+        L = flux_div(a.Fx[fx + 1] - a.Fx[fx], a.inv_dx, a.Fy[fy + nx] - a.Fy[fy], a.inv_dy);
       }
       const size_t w = (size_t)c * ncell + n;
       q[c] = (a.stage == 0) ? L : rk_stage(a.stage, dt, a.Wn[w], a.Ws[w], L);
@@ -169,7 +176,7 @@ __device__ __forceinline__ void repair_range(const GridInfo& g, const RepairArgs
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       double L = -(F[0][1][c] - F[0][0][c]) * a.inv_dx;
-      if (DIM == 2) L = fma(-(F[1][1][c] - F[1][0][c]), a.inv_dy, L);
+      if (DIM == 2) L = flux_div(F[0][1][c] - F[0][0][c], a.inv_dx, F[1][1][c] - F[1][0][c], a.inv_dy);
       const size_t w = (size_t)c * ncell + n;
       q[c] = rk_stage(a.stage, dt, a.Wn[w], a.Ws[w], L);
       a.out[w] = q[c];

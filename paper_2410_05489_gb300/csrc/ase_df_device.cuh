@@ -1,6 +1,7 @@
 // Device helpers shared by the sweep kernel and the combine / repair kernels: ghost-cell
-// index maps (periodic wrap, zero-gradient clamp, x-lo inflow band) and the local
-// Lax-Friedrichs flux with the discontinuity strength of one Gauss point.
+// index maps (periodic wrap, zero-gradient clamp, mirror at a reflecting wall, x-lo inflow
+// band) and the local Lax-Friedrichs flux with the discontinuity strength of one Gauss
+// point.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -79,13 +80,17 @@ __device__ __forceinline__ double rsqrt_pos(double x) {
   return fma(y0 * r, fma(r, 0.375, 0.5), y0);
 }
 
+// cell index 0..n-1 of a (ghost) cell; a reflecting wall mirrors about its face (the
+// ghost layers reach at most k+1 <= n cells deep, which the context validates)
 __device__ __forceinline__ int wrap_or_clamp(int i, int n, int bc_lo, int bc_hi) {
   if (i < 0) {
     if (bc_lo == BC_PERIODIC) { int m = i % n; return m < 0 ? m + n : m; }
+    if (bc_lo == BC_REFLECT) return -1 - i;
     return 0;
   }
   if (i >= n) {
     if (bc_hi == BC_PERIODIC) return i % n;
+    if (bc_hi == BC_REFLECT) return 2 * n - 1 - i;
     return n - 1;
   }
   return i;
@@ -96,9 +101,11 @@ __device__ __forceinline__ int face_map(int f, int n, int bc_lo, int bc_hi) {
   if (f >= 0 && f <= n) return f;
   if (f < 0) {
     if (bc_lo == BC_PERIODIC) { int m = f % n; return m < 0 ? m + n : m; }
+    if (bc_lo == BC_REFLECT) return -f;
     return 0;
   }
   if (bc_hi == BC_PERIODIC) return f % n;
+  if (bc_hi == BC_REFLECT) return 2 * n - f;
   return n;
 }
 
@@ -107,7 +114,11 @@ __device__ __forceinline__ double fetch_w(const GridInfo& g, const double* __res
   if (i < 0 && g.bc[0] == BC_INFLOW_BAND && j >= g.band_j0 && j <= g.band_j1) return g.inflow_cons[c];
   const int ii = wrap_or_clamp(i, g.nx, g.bc[0], g.bc[1]);
   const int jj = wrap_or_clamp(j, g.ny, g.bc[2], g.bc[3]);
-  return __ldg(W + ((size_t)c * g.ny + jj) * g.nx + ii);
+  const double v = __ldg(W + ((size_t)c * g.ny + jj) * g.nx + ii);
+  // a reflecting wall flips the momentum normal to it (x-walls: c = 1; y-walls, 2D: c = 2)
+  const bool fx = (c == 1) && ((i < 0 && g.bc[0] == BC_REFLECT) || (i >= g.nx && g.bc[1] == BC_REFLECT));
+  const bool fy = (c == 2) && ((j < 0 && g.bc[2] == BC_REFLECT) || (j >= g.ny && g.bc[3] == BC_REFLECT));
+  return (fx || fy) ? -v : v;
 }
 
 // Local Lax-Friedrichs flux (Sec. 2.3) and discontinuity strength sigma (Sec. 3.1) of

@@ -248,6 +248,11 @@ __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly
                           const double* Wrx, const double* Wry, double gamma, double dt, double C1, double C2,
                           double* F, double* Ft) {
   constexpr int n = DIM + 2;
+  if (!(dt > 0.0)) {  // a step of length 0 (t_end reached): no transport
+#pragma unroll
+    for (int i = 0; i < n; ++i) F[i] = Ft[i] = 0.0;
+    return;
+  }
   const double K = (DIM == 2) ? (4.0 - 2.0 * gamma) / (gamma - 1.0) : (3.0 - gamma) / (gamma - 1.0);
   Maxw gl, gr;
   maxw_init<DIM>(Wl, gamma, K, gl);

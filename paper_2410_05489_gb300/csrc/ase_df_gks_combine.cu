@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(256) gks_combine_kernel(const GridInfo g, cons
       double Lt = -(a.Fxt[fx + 1] - a.Fxt[fx]) * a.inv_dx;
       if (DIM == 2) {
         const size_t fy = ((size_t)c * (ny + 1) + j) * nx + i;
-        L = fma(-(a.Fy[fy + nx] - a.Fy[fy]), a.inv_dy, L);
-        Lt = fma(-(a.Fyt[fy + nx] - a.Fyt[fy]), a.inv_dy, Lt);
+        L = flux_div(a.Fx[fx + 1] - a.Fx[fx], a.inv_dx, a.Fy[fy + nx] - a.Fy[fy], a.inv_dy);
+        Lt = flux_div(a.Fxt[fx + 1] - a.Fxt[fx], a.inv_dx, a.Fyt[fy + nx] - a.Fyt[fy], a.inv_dy);
       }
       const size_t w = (size_t)c * ncell + n;
       if (a.stage == 0) {

@@ -66,7 +66,7 @@ struct DevState {
   unsigned long long frozen_total;    // cells left without a flux update (last resort)
 };
 
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2, BC_REFLECT = 3 };
 
 // Grid and boundary description handed to the kernels.
 struct GridInfo {

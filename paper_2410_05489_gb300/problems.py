@@ -25,16 +25,17 @@ from typing import Callable, Sequence, Tuple
 
 import numpy as np
 
-BC_NAMES = {"periodic": 0, "outflow": 1, "inflow": 2}
+BC_NAMES = {"periodic": 0, "outflow": 1, "inflow": 2, "reflect": 3}
 
 
 @dataclasses.dataclass
 class Problem:
     """A 1D or 2D Euler problem on a uniform Cartesian grid.
 
-    bc is (x-lo, x-hi, y-lo, y-hi), each "periodic", "outflow" or (x-lo only)
-    "inflow": the inflow band inflow_lo < y < inflow_hi of the x-lo boundary takes the
-    fixed primitive state inflow = (rho, u, v, p); outside the band it is outflow.
+    bc is (x-lo, x-hi, y-lo, y-hi), each "periodic", "outflow", "reflect" (a wall: mirrored
+    ghost cells with the normal momentum negated) or (x-lo only) "inflow": the inflow band
+    inflow_lo < y < inflow_hi of the x-lo boundary takes the fixed primitive state
+    inflow = (rho, u, v, p); outside the band it is outflow.
     """
 
     ndim: int
@@ -256,6 +257,31 @@ def riemann_2d(n: int, order: int, seed: int, ny: int | None = None) -> Tuple[Pr
     X, Y = np.meshgrid(x, y)
     q = (X >= 0.5).astype(int) + 2 * (Y >= 0.5).astype(int)
     return pb, np.ascontiguousarray(conservative((rho[q], u[q], v[q], p[q]), pb.gamma, 2))
+
+
+def blast_wave(n: int = 400, order: int = 5, gks_c2: float = 5.0) -> Tuple[Problem, np.ndarray]:
+    """Blast wave of Sec. 4.3 (Example 1): [0,1], reflecting walls, gamma 1.4, rho = 1, u = 0,
+    p = 1000 (x < 0.1), 0.01, 100 (x > 0.9); run to t = 0.038 (the printed "t = 3.8" read as
+    0.038, the time of the standard problem); c2 = 5.0 as in the paper's GKS runs."""
+    pb = Problem(ndim=1, nx=n, order=order, gamma=1.4, bc=("reflect", "reflect", "outflow", "outflow"),
+                 gks_c2=gks_c2)
+    x = (np.arange(n) + 0.5) * pb.dx
+    p = np.where(x < 0.1, 1000.0, np.where(x > 0.9, 100.0, 0.01))
+    one = np.ones(n)
+    return pb, np.ascontiguousarray(conservative((one, 0.0 * one, p), pb.gamma, 1)[:, None, :])
+
+
+def shu_osher(n: int = 200, order: int = 5) -> Tuple[Problem, np.ndarray]:
+    """Shu-Osher problem as Sec. 4.3 prints it: [0,10], (rho, u, p) = (3.857134, 2.629369,
+    10.33333) for x < 1, (1 + 0.2 sin(5x), 0, 1) elsewhere, gamma 1.4, outflow; run to t = 1.8."""
+    pb = Problem(ndim=1, nx=n, x0=0.0, x1=10.0, order=order, gamma=1.4)
+
+    def prim(x):
+        left = x < 1.0
+        return (np.where(left, 3.857134, 1.0 + 0.2 * np.sin(5.0 * x)), np.where(left, 2.629369, 0.0),
+                np.where(left, 10.33333, 1.0))
+
+    return pb, cell_average(pb, prim)
 
 
 def configuration3(n: int, order: int, gks_c1: float = 0.05, gks_c2: float = 1.0) -> Tuple[Problem, np.ndarray]:
