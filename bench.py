@@ -38,6 +38,10 @@ N_GRID = 1024
 ORDER = 9
 ORDER_ALSO = 7
 HBM_BYTES_PER_CELL_STAGE_2D = 128.0  # read W^(s), W^n, write W^(s+1), sigma in/out, both directions
+# DRAM bytes (read + write) per sweep launch measured by ncu on this kernel for the 1024^2,
+# order-9 workload (mean of the x- and y-face launches; profiles/sweep_kernel_r9_2d_vortex1024_ncu.md).
+# Reported as roofline.traffic for that workload only (null for other sizes / orders).
+SWEEP_DRAM_BYTES_1024_R9 = 63.72e6
 
 
 def algorithmic_flops_per_face(ndim: int, r: int) -> float:
@@ -313,7 +317,8 @@ def run_ours(args, world, rank, local):
             "peak": round(peak_tflops, 4),
             "unit": "TFLOP/s",
             "frac": round(achieved / peak_tflops, 4),
-            "traffic": None,
+            "traffic": SWEEP_DRAM_BYTES_1024_R9 if (args.n, args.order) == (1024, 9) else None,
+            "traffic_unit": "bytes per sweep launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_source": "2 FP64 FMA/cycle/SM (ncu DFMA peak_sustained) x %d SMs x %.0f MHz (median sampled "
                            "SM clock in the timed region) x 2 flops" % (n_sm, clk_mhz),
             "peak_microbench": round(2.0 * fma_rate / 1e12, 4),
@@ -710,6 +715,36 @@ def suite_bench(args):
     print(json.dumps({"suite": rows, "cores": cores}), flush=True)
 
 
+def gks_bench(args):
+    """The gas-kinetic path alone: Configuration 3 at n^2 and order r, 20 CFL S2O4 steps after
+    2 warm-up steps; one JSON line (Mcell-updates/s per stage, 2 stages per step)."""
+    import torch
+
+    from paper_2410_05489_gb300 import ase_df as A
+    from paper_2410_05489_gb300 import build
+
+    build.build()
+    pb, W0 = P.configuration3(args.n, args.order)
+    s = A.Solver(pb, W0)
+    for _ in range(max(2, args.warmup)):
+        s.gks_step()
+    s.set_state(W0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.gks_step()
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    flags = s.status()[0]
+    s.close()
+    print(json.dumps({"workload": "GKS + S2O4, Configuration 3, %d^2, order %d" % (args.n, args.order),
+                      "steps": args.steps, "ms_per_step": round(ms / args.steps, 4),
+                      "value": round(pb.ncells * 2 * args.steps / (ms * 1e-3) / 1e6, 3),
+                      "unit": "Mcell-updates/s per stage", "flags": flags}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -722,13 +757,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--gks", action="store_true",
+                    help="time only the gas-kinetic path on Configuration 3 (--n, --order, --steps)")
     ap.add_argument("--suite", action="store_true",
                     help="measure every workload configuration (GPU and CPU oracle) instead of the headline line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()
-    if args.suite:
+    if args.gks:
+        if rank == 0:
+            gks_bench(args)
+    elif args.suite:
         if rank == 0:
             suite_bench(args)
     elif args.impl == "reference":
