@@ -415,10 +415,15 @@ __device__ __forceinline__ int face_preimages(int e, int n, int bl, int bh, int 
 // ---------------------------------------------------------------------------------
 // K1: face kernel
 // ---------------------------------------------------------------------------------
+// 16 x 16 faces per CTA in 2D: the face adjoint needs ~255 registers (one CTA per SM), and
+// the smaller tile gives more CTAs per grid than the forward sweep's 16 x 32.
+template <int R, int DIM>
+using AdjTile = Tile<R, DIM, (DIM == 2) ? 16 : 1>;
+
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(Tile<R, DIM>::NT, 1)
+__global__ void __launch_bounds__(AdjTile<R, DIM>::NT, 1)
 adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const __grid_constant__ Tables T) {
-  using TL = Tile<R, DIM>;
+  using TL = AdjTile<R, DIM>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
   constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
   constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
@@ -810,7 +815,7 @@ inline int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>
 
 template <int R, int DIM, int DIR>
 cudaError_t adj_launch(const GridInfo& g, const SweepArgs& a, const AdjArgs& aa, const Tables& t, cudaStream_t s) {
-  using TL = Tile<R, DIM>;
+  using TL = AdjTile<R, DIM>;
   const size_t smem = TL::smem_doubles * sizeof(double);
   auto k1 = adj_face_kernel<R, DIM, DIR>;
   static bool attr = false;
