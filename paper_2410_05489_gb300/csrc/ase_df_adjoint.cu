@@ -416,9 +416,9 @@ __device__ __forceinline__ int face_preimages(int e, int n, int bl, int bh, int 
 // K1: face kernel
 // ---------------------------------------------------------------------------------
 // 16 x 16 faces per CTA in 2D: the face adjoint needs ~255 registers (one CTA per SM), and
-// the smaller tile gives more CTAs per grid than the forward sweep's 16 x 32.
+// the smaller tile gives more CTAs per grid than the forward sweep's 8 x 64.
 template <int R, int DIM>
-using AdjTile = Tile<R, DIM, (DIM == 2) ? 16 : 1>;
+using AdjTile = Tile<R, DIM, (DIM == 2) ? 16 : 1, (DIM == 2) ? 16 : 256>;
 
 template <int R, int DIM, int DIR>
 __global__ void __launch_bounds__(AdjTile<R, DIM>::NT, 1)

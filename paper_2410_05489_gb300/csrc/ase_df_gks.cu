@@ -384,7 +384,7 @@ __device__ __forceinline__ bool gks_physical(const double* q, double gamma) {
 // 16 x 16 faces per CTA in 2D (one face per thread): the gas-kinetic flux needs ~255
 // registers, so one CTA runs per SM, and the smaller tile gives more CTAs per grid.
 template <int R, int DIM>
-using GksTileShape = Tile<R, DIM, (DIM == 2) ? 16 : 1>;
+using GksTileShape = Tile<R, DIM, (DIM == 2) ? 16 : 1, (DIM == 2) ? 16 : 256>;
 
 template <int R, int DIM>
 struct GksTile {
