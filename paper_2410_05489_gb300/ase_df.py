@@ -324,6 +324,26 @@ class Solver:
     def status(self):
         return ase_df_get_status(self.ctx)
 
+    def save(self, path: str) -> None:
+        """Checkpoint: the state W, sigma and the device time t (one .npz file)."""
+        import numpy as np
+
+        flags, last_dt, t = self.status()
+        np.savez(path, W=self.W.cpu().numpy(), sx=self.sx.cpu().numpy(), sy=self.sy.cpu().numpy(),
+                 t=np.float64(t), last_dt=np.float64(last_dt), flags=np.uint32(flags))
+
+    def load(self, path: str) -> None:
+        """Resume from save(): the run continues bit for bit as if it had not stopped."""
+        import numpy as np
+
+        d = np.load(path)
+        if tuple(d["W"].shape) != tuple(self.W.shape):
+            raise ValueError("checkpoint of a different problem size")
+        self.W.copy_(torch.as_tensor(d["W"]))
+        self.sx.copy_(torch.as_tensor(d["sx"]))
+        self.sy.copy_(torch.as_tensor(d["sy"]))
+        ase_df_reset(self.ctx, float(d["t"]))
+
     def close(self) -> None:
         if getattr(self, "ctx", None) is not None:
             ase_df_destroy(self.ctx)
