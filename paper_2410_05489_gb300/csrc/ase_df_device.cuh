@@ -125,7 +125,8 @@ __device__ __forceinline__ double fetch_w(const GridInfo& g, const double* __res
 // one Gauss point; qa / qb are the left / right states in (x, y) momentum order and
 // NI / TI select the normal and tangential momentum.  A state is physical when rho > 0
 // and p > 0, tested on p rho = (gamma-1)(E rho - |m|^2 / 2) (no division); otherwise
-// the point takes the cell averages ca / cb (returns true then) and sigma = 1e30.
+// the point takes the cell averages ca / cb (component c at ca[c * cs], read only in that
+// case), returns true and sets sigma = 1e30.
 // FP64 divisions and square roots cost 6-9 FMA slots on this part, so the point uses
 // one reciprocal and two reciprocal square roots:
 //   D = rho_l rho_r (p rho)_l (p rho)_r,  1/(rho_l rho_r) = (p rho)_l (p rho)_r / D,
@@ -134,7 +135,8 @@ __device__ __forceinline__ double fetch_w(const GridInfo& g, const double* __res
 // weight by the caller).
 template <int C, int NI, int TI>
 __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, const double* ca,
-                                         const double* cb, double gamma, double* F2, double& sigma) {
+                                         const double* cb, int cs, double gamma, double* F2,
+                                         double& sigma) {
   const double gm1 = gamma - 1.0;
   double mmL = qa[NI] * qa[NI], mmR = qb[NI] * qb[NI];
   if (C == 4) {
@@ -147,10 +149,15 @@ __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, con
   double a[C], b[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    a[c] = ok ? qa[c] : ca[c];
-    b[c] = ok ? qb[c] : cb[c];
+    a[c] = qa[c];
+    b[c] = qb[c];
   }
   if (!ok) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      a[c] = ca[c * cs];
+      b[c] = cb[c * cs];
+    }
     mmL = a[NI] * a[NI];
     mmR = b[NI] * b[NI];
     if (C == 4) {
@@ -170,17 +177,16 @@ __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, con
   const double pL = prL * irL, pR = prR * irR;
   const double c2L = gamma * pL * irL, c2R = gamma * pR * irR;
   const double icL = rsqrt_pos(c2L), icR = rsqrt_pos(c2R);
-  const double cL = c2L * icL, cR = c2R * icR;
-  const double lam = max_nonneg(fabs(unL) + cL, fabs(unR) + cR);
-  double FL[C], FR[C];
-  FL[0] = a[NI];
-  FR[0] = b[NI];
-  FL[NI] = fma(a[NI], unL, pL);
-  FR[NI] = fma(b[NI], unR, pR);
+  // lambda = max(|u_n| + c) with c = c^2 / c
+  const double lam = max_nonneg(fma(c2L, icL, fabs(unL)), fma(c2R, icR, fabs(unR)));
+  // S = F(left) + F(right), summed as it is formed
+  const double ps = pL + pR;
+  double S[C];
+  S[0] = a[NI] + b[NI];
+  S[NI] = fma(a[NI], unL, fma(b[NI], unR, ps));
   if (C == 4) {
     const double utL = a[TI] * irL, utR = b[TI] * irR;
-    FL[TI] = a[NI] * utL;
-    FR[TI] = b[NI] * utR;
+    S[TI] = fma(a[NI], utL, b[NI] * utR);
     if (ok) {
       const double dmt = fma(utL, icL, -utR * icR);
       sigma = dmt * dmt;
@@ -188,16 +194,15 @@ __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, con
   } else {
     sigma = 0.0;
   }
-  FL[C - 1] = unL * (a[C - 1] + pL);
-  FR[C - 1] = unR * (b[C - 1] + pR);
+  S[C - 1] = fma(unL, a[C - 1] + pL, unR * (b[C - 1] + pR));
 #pragma unroll
-  for (int c = 0; c < C; ++c) F2[c] = fma(-lam, b[c] - a[c], FL[c] + FR[c]);
+  for (int c = 0; c < C; ++c) F2[c] = fma(-lam, b[c] - a[c], S[c]);
   if (ok) {
     const double dp = fabs(pL - pR);
     const double ipp = (rr * rr) * inv;  // 1 / (p_l p_r)
     const double dmn = fma(unL, icL, -unR * icR);
     sigma = fma(dmn, dmn, sigma);
-    sigma = fma(dp * (pL + pR), ipp, sigma);
+    sigma = fma(dp * ps, ipp, sigma);
   } else {
     sigma = kSigmaBig;
   }

@@ -29,6 +29,18 @@ __device__ __forceinline__ Branch select_branch(const double* s, double thres) {
   b.m = R;
   b.a3[0] = b.a3[1] = b.a3[2] = 1.0;
   b.a5 = 1.0;
+  // Smooth data without FP64 arithmetic: if every one of the 2K <= 8 strengths is at most
+  // thres/16 (compared as unsigned bit patterns, so negative values and NaN fail), each
+  // stencil sum is at most 8 thres/16 = thres/2 also after rounding (rounded addition is
+  // monotone in its operands), so every sum is below thres and the branch is linear order R.
+  {
+    const long long tb = dbits(thres);
+    const unsigned long long lim = ((tb >> 52) > 4) ? (unsigned long long)(tb - (4LL << 52)) : 0ull;
+    unsigned long long mx = (unsigned long long)dbits(s[0]);
+#pragma unroll
+    for (int t = 1; t < 2 * K; ++t) mx = max(mx, (unsigned long long)dbits(s[t]));
+    if (mx <= lim) return b;
+  }
   const double sm12 = s[K - 1], sp12 = s[K];  // sigma_{-1/2}, sigma_{1/2}
   if (R == 3) {
     const double A = sm12 + sp12;
@@ -306,12 +318,9 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
         for (int c = 0; c < C; ++c) st[side][0][c] = Q[c * NQ + qa];
       }
     }
-    double ca[C], cb[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      ca[c] = sW[(c * NB + tb + KT) * NA + fa + K];
-      cb[c] = sW[(c * NB + tb + KT) * NA + fa + K + 1];
-    }
+    // cell averages either side of the face (read by a Gauss point only if it falls back)
+    const double* ca = sW + (tb + KT) * NA + fa + K;
+    const double* cb = ca + 1;
     double Fs[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) Fs[c] = 0.0;
@@ -320,7 +329,7 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
 #pragma unroll
     for (int q = 0; q < G; ++q) {
       double F[C], sg;
-      anyfb |= lf_point<C, NI, TI>(st[0][q], st[1][q], ca, cb, g.gamma, F, sg);
+      anyfb |= lf_point<C, NI, TI>(st[0][q], st[1][q], ca, cb, NB * NA, g.gamma, F, sg);
 #pragma unroll
       for (int c = 0; c < C; ++c) Fs[c] = fma((DIM == 2) ? T.hgw[q] : 0.5, F[c], Fs[c]);
       ssum += sg;
