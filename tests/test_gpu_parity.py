@@ -132,7 +132,7 @@ def make_case(kind, ndim, order, seed, nx, ny):
 @pytest.mark.parametrize("order", [3, 5, 7, 9])
 @pytest.mark.parametrize("kind", ["smooth", "noise", "riemann"])
 def test_residual_parity_2d(A, oracle, order, kind):
-    """Several tiles with ragged tails in both directions (tiles are 32 faces x 8 lines)."""
+    """Several tiles with ragged tails in both directions (tiles are 8 faces x 64 lines)."""
     pb, W = make_case(kind, 2, order, 10 + order, 67, 45)
     check_residual(A, oracle, pb, W, *oracle.prime_sigma(pb, W))
     sx, sy = P.random_sigma(pb, order, 1.0)  # stencil sums straddle sigma_thres = 2
@@ -147,6 +147,36 @@ def test_residual_parity_1d(A, oracle, order, kind):
     pb, W = make_case(kind, 1, order, 20 + order, 300, 1)
     check_residual(A, oracle, pb, W, *oracle.prime_sigma(pb, W))
     check_residual(A, oracle, pb, W, *P.random_sigma(pb, order, 1.0))
+
+
+@pytest.mark.parametrize("order", [3, 5, 9])
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_residual_parity_sigma_on_branch_boundaries(A, oracle, ndim, order):
+    """Face strengths drawn from values on and next to the points where the branch choice
+    changes: thres/16 (the largest strength for which the kernel skips the stencil sums),
+    thres/8 (eight of them sum to exactly thres, which is not smooth), thres/4, zero, -0
+    and negative values (smooth: the sums are below thres)."""
+    thres = 2.0
+    vals = np.array([0.0, -0.0, -0.25, thres / 16, np.nextafter(thres / 16, np.inf),
+                     np.nextafter(thres / 16, 0.0), thres / 8, np.nextafter(thres / 8, 0.0),
+                     np.nextafter(thres / 8, np.inf), thres / 4, 3 * thres / 8, 1e-300])
+    nx, ny = (200, 1) if ndim == 1 else (37, 29)
+    pb = P.Problem(ndim=ndim, nx=nx, ny=ny, order=order, bc=("periodic",) * 4, x1=2.0, y1=1.5)
+    W = P.smooth_random(pb, 7 + order)
+    rng = np.random.default_rng(100 + 10 * ndim + order)
+    sx = vals[rng.integers(0, len(vals), size=(pb.nyc, nx + 1))]
+    sx[:, -1] = sx[:, 0]  # periodic: x-faces 0 and nx are the same face
+    if ndim == 2:
+        sy = vals[rng.integers(0, len(vals), size=(ny + 1, nx))]
+        sy[-1, :] = sy[0, :]
+    else:
+        sy = np.zeros((1, 1))
+    check_residual(A, oracle, pb, W, sx, sy)
+    # every face on the same value: all stencils on one side of a boundary at once
+    for v in (thres / 16, np.nextafter(thres / 16, np.inf), thres / 8, np.nextafter(thres / 8, 0.0)):
+        sx = np.full((pb.nyc, nx + 1), v)
+        sy = np.full((ny + 1, nx), v) if ndim == 2 else np.zeros((1, 1))
+        check_residual(A, oracle, pb, W, sx, sy)
 
 
 @pytest.mark.parametrize("order", [7, 9])
