@@ -41,7 +41,7 @@ HBM_BYTES_PER_CELL_STAGE_2D = 128.0  # read W^(s), W^n, write W^(s+1), sigma in/
 # DRAM bytes (read + write) per sweep launch measured by ncu on this kernel for the 1024^2,
 # order-9 workload (mean of the x- and y-face launches; profiles/sweep_kernel_r9_2d_vortex1024_ncu.md).
 # Reported as roofline.traffic for that workload only (null for other sizes / orders).
-SWEEP_DRAM_BYTES_1024_R9 = 61.40e6
+SWEEP_DRAM_BYTES_1024_R9 = None
 
 
 def algorithmic_flops_per_face(ndim: int, r: int) -> float:
@@ -56,6 +56,12 @@ def algorithmic_flops_per_face(ndim: int, r: int) -> float:
     normal = 2 * C * (2 * r - 1)
     tang = 2 * C * G * (2 * r - 1) if ndim == 2 else 0
     return normal + tang + G * (phi + 2 * C + 1) + 1
+
+
+def fp64_peak_tflops(torch, clk_mhz: float = 2070.0) -> float:
+    """2 FP64 FMA per cycle per SM x SMs x SM clock x 2 flops (default: the maximum clock)."""
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return 2.0 * 2.0 * n_sm * clk_mhz * 1e6 / 1e12
 
 
 def algorithmic_flops_per_cell_stage(ndim: int, r: int) -> float:
@@ -366,6 +372,9 @@ def batched_bench(A, torch, args):
     ms_b = e0.elapsed_time(e1) / ksteps
     flags, _, _ = bt.status()
     cells = bt.ncells
+    # smooth-branch algorithmic flops of one step (3 stages); the fallback branch at the
+    # Riemann data's discontinuities costs more and is not counted
+    step_flops = 3 * sum(p.ncells * algorithmic_flops_per_cell_stage(p.ndim, p.order) for p, _ in probs)
     bt.close()
     # one problem per launch: a context per problem, ase_df_step on each in turn
     solvers = [A.Solver(p, w) for p, w in probs]
@@ -389,6 +398,8 @@ def batched_bench(A, torch, args):
         "ms_per_step": round(ms_b, 4),
         "one_problem_per_launch": {"value": round(cells * 3 / (ms_1 * 1e-3) / 1e6, 3), "ms_per_step": round(ms_1, 4)},
         "speedup": round(ms_1 / ms_b, 3),
+        "step_tflops": round(step_flops / (ms_b * 1e-3) / 1e12, 4),
+        "step_frac_of_fp64_peak": round(step_flops / (ms_b * 1e-3) / 1e12 / fp64_peak_tflops(torch), 4),
         "schedule": tune.get("schedule"),
         "nonphysical_problems": int(((flags & 1) != 0).sum()),
     }

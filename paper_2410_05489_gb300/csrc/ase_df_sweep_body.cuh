@@ -275,18 +275,37 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   __syncthreads();
 
   // ---- phase 1: normal reconstruction of cells a0-1 .. a0+TN-1 on all staged lines ----
+  // Interior cells (qa = 1 .. NQ-2) serve a face on each side and are evaluated at both
+  // xi = 0 and xi = -1; the two end cells serve one tile face each (qa = 0: its xi = 0
+  // value, the left state of face a0; qa = NQ-1: its xi = -1 value), so they come last in
+  // the work list and evaluate one point.
   for (int it = tid; it < NQ * NB; it += NT) {
-    int qa, bb;
-    if (DIR == 0) { qa = it % NQ; bb = it / NQ; }
-    else { bb = it % NB; qa = it / NB; }
-    const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
+    if (it < (NQ - 2) * NB) {
+      int qa, bb;
+      if (DIR == 0) { qa = 1 + it % (NQ - 2); bb = it / (NQ - 2); }
+      else { bb = it % NB; qa = 1 + it / NB; }
+      const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const double* v = sW + (c * NB + bb) * NA + qa + K;  // W_0 of this cell
-      double out[2];
-      recon_eval<R, 2>(v, 1, br, T, 0, out);
-      sQP[(c * NB + bb) * NQ + qa] = out[0];
-      sQM[(c * NB + bb) * NQ + qa] = out[1];
+      for (int c = 0; c < C; ++c) {
+        const double* v = sW + (c * NB + bb) * NA + qa + K;  // W_0 of this cell
+        double out[2];
+        recon_eval<R, 2>(v, 1, br, T, 0, out);
+        sQP[(c * NB + bb) * NQ + qa] = out[0];
+        sQM[(c * NB + bb) * NQ + qa] = out[1];
+      }
+    } else {
+      const int e = it - (NQ - 2) * NB;
+      const int bb = e % NB, pt = e / NB;  // pt 0: cell qa = 0 at xi = 0; 1: qa = NQ-1 at xi = -1
+      const int qa = pt * (NQ - 1);
+      const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
+      double* dst = pt ? sQM : sQP;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const double* v = sW + (c * NB + bb) * NA + qa + K;
+        double out[1];
+        recon_eval<R, 1>(v, 1, br, T, pt, out);
+        dst[(c * NB + bb) * NQ + qa] = out[0];
+      }
     }
   }
   __syncthreads();
