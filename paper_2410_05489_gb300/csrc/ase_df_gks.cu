@@ -123,20 +123,25 @@ __device__ __forceinline__ void recon_eval_d(const double* v, int vs, const Bran
 // ---------------------------------------------------------------------------------
 // Maxwellian moments (Appendix A)
 // ---------------------------------------------------------------------------------
+// FP64 division and square root take 6-9 FMA issue slots on this part, so the moments
+// work from the reciprocal density and h = p / rho = 1 / (2 lambda), each one seeded
+// reciprocal (rcp_pos), and every later division becomes a multiplication.
 struct Maxw {
-  double rho, U, V, lam;
-  double mu[7], mv[6], mx[3];  // <u^n> (n <= 6), <v^n> (n <= 5), <xi^0>, <xi^2>, <xi^4>
+  double rho, ir, U, V, lam, h;  // ir = 1 / rho, h = 1 / (2 lambda)
+  double mu[7], mv[6], mx[3];    // <u^n> (n <= 6), <v^n> (n <= 5), <xi^0>, <xi^2>, <xi^4>
 };
 
 template <int DIM>
 __device__ __forceinline__ void maxw_init(const double* W, double gamma, double K, Maxw& m) {
   m.rho = W[0];
-  const double ir = 1.0 / W[0];
+  const double ir = rcp_pos(W[0]);
+  m.ir = ir;
   m.U = W[1] * ir;
   m.V = (DIM == 2) ? W[2] * ir : 0.0;
   const double p = (gamma - 1.0) * (W[DIM + 1] - 0.5 * m.rho * (m.U * m.U + m.V * m.V));
-  m.lam = 0.5 * m.rho / p;
   const double h = p * ir;  // 1 / (2 lambda)
+  m.h = h;
+  m.lam = 0.5 * rcp_pos(h);
   m.mu[0] = 1.0;
   m.mu[1] = m.U;
 #pragma unroll
@@ -152,11 +157,13 @@ __device__ __forceinline__ void maxw_init(const double* W, double gamma, double 
 
 // <u^n> over u > 0 (pos) or u < 0, n <= 6
 __device__ __forceinline__ void half_moments(const Maxw& m, bool pos, double* mh) {
-  const double sl = sqrt(m.lam);
-  const double e = 0.5 * exp(-m.lam * m.U * m.U) / sqrt(3.141592653589793 * m.lam);
+  const double isl = rsqrt_pos(m.lam);  // 1 / sqrt(lambda)
+  const double sl = m.lam * isl;
+  // exp(-lambda U^2) / (2 sqrt(pi lambda)), 1 / (2 sqrt(pi)) = 0.28209479177387814
+  const double e = 0.28209479177387814 * exp(-m.lam * m.U * m.U) * isl;
   mh[0] = 0.5 * erfc(pos ? -sl * m.U : sl * m.U);
   mh[1] = fma(m.U, mh[0], pos ? e : -e);
-  const double h = 0.5 / m.lam;
+  const double h = m.h;
 #pragma unroll
   for (int n = 0; n < 5; ++n) mh[n + 2] = fma(m.U, mh[n + 1], (n + 1) * h * mh[n]);
 }
@@ -221,23 +228,21 @@ __device__ __forceinline__ void slope_moments(const double* a, int s, int t, con
   }
 }
 
-// a with <psi psi^T> a = b (Appendix A closed form; b = W_x / rho)
+// a with <psi psi^T> a = b (Appendix A closed form; b = W_x / rho).  D = K + DIM, i4D = 4 / D.
 template <int DIM>
-__device__ __forceinline__ void solve_slope(const Maxw& m, double K, const double* b, double* a) {
+__device__ __forceinline__ void solve_slope(const Maxw& m, double D, double i4D, const double* b, double* a) {
   const double l = m.lam, U = m.U, V = m.V;
   if (DIM == 2) {
-    const double D = K + 2.0;
-    const double q = U * U + V * V + D / (2.0 * l);
+    const double q = U * U + V * V + D * m.h;
     const double R4 = 2.0 * b[3] - q * b[0], R3 = b[2] - V * b[0], R2 = b[1] - U * b[0];
-    a[3] = 4.0 * l * l / D * (R4 - 2.0 * U * R2 - 2.0 * V * R3);
+    a[3] = i4D * l * l * (R4 - 2.0 * U * R2 - 2.0 * V * R3);
     a[2] = 2.0 * l * R3 - V * a[3];
     a[1] = 2.0 * l * R2 - U * a[3];
     a[0] = b[0] - U * a[1] - V * a[2] - 0.5 * a[3] * q;
   } else {
-    const double D = K + 1.0;
-    const double q = U * U + D / (2.0 * l);
+    const double q = U * U + D * m.h;
     const double R3 = 2.0 * b[2] - q * b[0], R2 = b[1] - U * b[0];
-    a[2] = 4.0 * l * l / D * (R3 - 2.0 * U * R2);
+    a[2] = i4D * l * l * (R3 - 2.0 * U * R2);
     a[1] = 2.0 * l * R2 - U * a[2];
     a[0] = b[0] - U * a[1] - 0.5 * a[2] * q;
   }
@@ -245,32 +250,32 @@ __device__ __forceinline__ void solve_slope(const Maxw& m, double K, const doubl
 
 template <int DIM>
 __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly, const double* Wr,
-                          const double* Wrx, const double* Wry, double gamma, double dt, double C1, double C2,
-                          double* F, double* Ft) {
+                          const double* Wrx, const double* Wry, double gamma, double K, double i4D,
+                          double dt, double idt, double C1, double C2, double* F, double* Ft) {
   constexpr int n = DIM + 2;
   if (!(dt > 0.0)) {  // a step of length 0 (t_end reached): no transport
 #pragma unroll
     for (int i = 0; i < n; ++i) F[i] = Ft[i] = 0.0;
     return;
   }
-  const double K = (DIM == 2) ? (4.0 - 2.0 * gamma) / (gamma - 1.0) : (3.0 - gamma) / (gamma - 1.0);
+  const double D = K + DIM;
   Maxw gl, gr;
   maxw_init<DIM>(Wl, gamma, K, gl);
   maxw_init<DIM>(Wr, gamma, K, gr);
   double b[4], alx[4], aly[4], arx[4], ary[4];
 #pragma unroll
-  for (int i = 0; i < n; ++i) b[i] = Wlx[i] / gl.rho;
-  solve_slope<DIM>(gl, K, b, alx);
+  for (int i = 0; i < n; ++i) b[i] = Wlx[i] * gl.ir;
+  solve_slope<DIM>(gl, D, i4D, b, alx);
 #pragma unroll
-  for (int i = 0; i < n; ++i) b[i] = Wrx[i] / gr.rho;
-  solve_slope<DIM>(gr, K, b, arx);
+  for (int i = 0; i < n; ++i) b[i] = Wrx[i] * gr.ir;
+  solve_slope<DIM>(gr, D, i4D, b, arx);
   if (DIM == 2) {
 #pragma unroll
-    for (int i = 0; i < n; ++i) b[i] = Wly[i] / gl.rho;
-    solve_slope<DIM>(gl, K, b, aly);
+    for (int i = 0; i < n; ++i) b[i] = Wly[i] * gl.ir;
+    solve_slope<DIM>(gl, D, i4D, b, aly);
 #pragma unroll
-    for (int i = 0; i < n; ++i) b[i] = Wry[i] / gr.rho;
-    solve_slope<DIM>(gr, K, b, ary);
+    for (int i = 0; i < n; ++i) b[i] = Wry[i] * gr.ir;
+    solve_slope<DIM>(gr, D, i4D, b, ary);
   }
   double mlp[7], mrn[7];
   half_moments(gl, true, mlp);
@@ -293,19 +298,19 @@ __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly
   maxw_init<DIM>(Wc, gamma, K, gc);
   double acx[4], acy[4] = {0.0, 0.0, 0.0, 0.0}, Ac[4];
 #pragma unroll
-  for (int i = 0; i < n; ++i) b[i] = Wcx[i] / gc.rho;
-  solve_slope<DIM>(gc, K, b, acx);
+  for (int i = 0; i < n; ++i) b[i] = Wcx[i] * gc.ir;
+  solve_slope<DIM>(gc, D, i4D, b, acx);
   if (DIM == 2) {
 #pragma unroll
-    for (int i = 0; i < n; ++i) b[i] = Wcy[i] / gc.rho;
-    solve_slope<DIM>(gc, K, b, acy);
+    for (int i = 0; i < n; ++i) b[i] = Wcy[i] * gc.ir;
+    solve_slope<DIM>(gc, D, i4D, b, acy);
   }
   // compatibility: <psi psi^T> A = -(<u a_x psi> + <v a_y psi>)
   slope_moments<DIM>(acx, 1, 0, gc.mu, gc, t1);
   if (DIM == 2) slope_moments<DIM>(acy, 0, 1, gc.mu, gc, t2);
 #pragma unroll
-  for (int i = 0; i < n; ++i) b[i] = -(t1[i] + (DIM == 2 ? t2[i] : 0.0)) / gc.rho;
-  solve_slope<DIM>(gc, K, b, Ac);
+  for (int i = 0; i < n; ++i) b[i] = -(t1[i] + (DIM == 2 ? t2[i] : 0.0)) * gc.ir;
+  solve_slope<DIM>(gc, D, i4D, b, Ac);
   // flux vectors
   double T0[4], T1[4], T2[4], T3[4], T4[4];
 #pragma unroll
@@ -329,13 +334,15 @@ __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly
     for (int i = 0; i < n; ++i) T4[i] += t1[i] + t2[i];
   }
   // numerical collision time and the time integrals over [0, dt] and [0, dt/2]
-  const double pl = 0.5 * gl.rho / gl.lam, pr = 0.5 * gr.rho / gr.lam;
-  const double taun = C1 * dt + C2 * fabs((pl - pr) / (pl + pr)) * dt;
+  const double pl = gl.rho * gl.h, pr = gr.rho * gr.h;
+  const double taun = C1 * dt + C2 * (fabs(pl - pr) * rcp_pos(pl + pr)) * dt;
+  // exp(-dt / tau_n) = exp(-dt / (2 tau_n))^2
+  const double eh = exp(-0.5 * dt * rcp_pos(taun));
   double Fd[2][4];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const double d = (h == 0) ? dt : 0.5 * dt;
-    const double e = exp(-d / taun);
+    const double e = (h == 0) ? eh * eh : eh;
     const double c1 = d - taun * (1.0 - e);
     const double c2 = taun * taun * (1.0 - e) - taun * d * e;
     const double c3 = 0.5 * d * d;
@@ -343,7 +350,6 @@ __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly
 #pragma unroll
     for (int i = 0; i < n; ++i) Fd[h][i] = c1 * T0[i] + c2 * (T1[i] - T4[i]) + c3 * T2[i] + c4 * T3[i];
   }
-  const double idt = 1.0 / dt;
 #pragma unroll
   for (int i = 0; i < n; ++i) {
     F[i] = (4.0 * Fd[1][i] - Fd[0][i]) * idt;
@@ -351,21 +357,23 @@ __device__ void gks_point(const double* Wl, const double* Wlx, const double* Wly
   }
 }
 
-// sigma of one Gauss point (Sec. 3.1) for physical states in the face frame
+// sigma of one Gauss point (Sec. 3.1) for physical states in the face frame:
+// |dp| (1/p_a + 1/p_b) + (dMa_n)^2 + (dMa_t)^2, with seeded reciprocals of rho and p and
+// seeded reciprocal square roots of c^2 (no FP64 division or square root)
 template <int C, int NI, int TI>
 __device__ __forceinline__ double sigma_point(const double* qa, const double* qb, double gamma) {
-  const double ia = 1.0 / qa[0], ib = 1.0 / qb[0];
+  const double ia = rcp_pos(qa[0]), ib = rcp_pos(qb[0]);
   const double ua = qa[NI] * ia, ub = qb[NI] * ib;
   const double wa = (C == 4) ? qa[TI] * ia : 0.0, wb = (C == 4) ? qb[TI] * ib : 0.0;
   const double pa = (gamma - 1.0) * (qa[C - 1] - 0.5 * qa[0] * (ua * ua + wa * wa));
   const double pb = (gamma - 1.0) * (qb[C - 1] - 0.5 * qb[0] * (ub * ub + wb * wb));
-  const double ca = sqrt(gamma * pa * ia), cb = sqrt(gamma * pb * ib);
+  const double ica = rsqrt_pos(gamma * pa * ia), icb = rsqrt_pos(gamma * pb * ib);  // 1 / c
   const double dp = fabs(pa - pb);
-  const double dmn = ua / ca - ub / cb;
-  double s = dp / pa + dp / pb + dmn * dmn;
+  const double dmn = ua * ica - ub * icb;
+  double s = fma(dp, rcp_pos(pa) + rcp_pos(pb), dmn * dmn);
   if (C == 4) {
-    const double dmt = wa / ca - wb / cb;
-    s += dmt * dmt;
+    const double dmt = wa * ica - wb * icb;
+    s = fma(dmt, dmt, s);
   }
   return s;
 }
@@ -419,6 +427,10 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
   const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
   const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
   const double dt = args.dt_fixed > 0.0 ? args.dt_fixed : args.st->dt;
+  const double idt = 1.0 / dt;
+  // internal degrees of freedom K (Sec. 2.2) and 4 / (K + DIM) of the slope solves
+  const double Kdof = (DIM == 2) ? (4.0 - 2.0 * g.gamma) / (g.gamma - 1.0) : (3.0 - g.gamma) / (g.gamma - 1.0);
+  const double i4D = 4.0 / (Kdof + DIM);
 
   for (int idx = tid; idx < C * NB * NA; idx += NT) {
     int c, bb, ai;
@@ -529,7 +541,7 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
         sg = sigma_point<C, 1, 2>(ql, qr, g.gamma);
       }
       double Fq[C], Ftq[C];
-      gks_point<DIM>(ql, qlx, qly, qr, qrx, qry, g.gamma, dt, args.c1, args.c2, Fq, Ftq);
+      gks_point<DIM>(ql, qlx, qly, qr, qrx, qry, g.gamma, Kdof, i4D, dt, idt, args.c1, args.c2, Fq, Ftq);
       const double w = (DIM == 2) ? T.gw[q] : 1.0;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
