@@ -4,13 +4,18 @@ seeded inputs.
 Tolerances (per component c, normalised by the largest magnitude of that component):
   * residual L:               max|L_gpu - L_cpu| / max|L_cpu|      <= 1e-12
   * face fluxes:              max|F_gpu - F_cpu| / max|F_cpu|      <= 1e-13
-  * sigma_out:                |s_gpu - s_cpu| <= 1e-12 (1 + |s|) + 1e-14 s^2 elementwise
-    (sigma ~ |p_l - p_r| / p: where a Gauss-point pressure is small, p carries the
-    rounding of E - |m|^2/(2 rho), relative ~ eps E / p <~ eps sigma, so the error of
-    sigma grows like eps sigma^2)
-  * L is normalised by max(max|L_c|, 1e-3 max|F_c| (1/dx + 1/dy)): the rounding of a
-    flux difference is ~1e-15 max|F| / dx, so below that floor L itself is
-    cancellation noise (e.g. a single-cell grid with random sigma)
+  * sigma_out:                |s_gpu - s_cpu| <= 1e-12 (1 + |s|) + 1e-13 s^2 elementwise
+    (sigma ~ |p_l - p_r| (p_l + p_r) / (p_l p_r) ~ p_r / p_l where one Gauss-point
+    pressure is small; p_l carries the rounding of E - |m|^2/(2 rho), relative eps E / p_l,
+    so sigma's error is ~ eps sigma (E / p_l) = eps sigma^2 (E / p_r).  The inputs bound
+    E / p_r: rho <= 10, |u|^2 <= 8, p >= 0.1 give E / p <~ 400 (plus reconstruction
+    overshoot), and eps 400 ~ 1e-13)
+  * L is normalised by max(max|L_c|, 1e-2 max|F_c| (1/dx + 1/dy)): L = -(F_+ - F_-)/dx
+    (the flux difference of the semi-discrete update) carries the rounding of the face
+    fluxes, tens of ulps of max|F| through the primitives, reciprocals and the Gauss sum,
+    i.e. ~1e-14 max|F| / dx whatever |L| is; a relative 1e-12 on L is meaningful only where
+    |L| is at least ~1e-2 max|F| / dx (smooth data on fine grids: |L| ~ |F'| while
+    |F| / dx grows with N; a single-cell grid with random sigma: L is cancellation noise)
   * after 100 SSP-RK3 steps:  max|W_gpu - W_cpu| / max|W_cpu|      <= 1e-9
 Branch decisions are taken from the same sigma_in with the same association on both
 sides, so they agree exactly; the remaining differences are rounding (FMA contraction,
@@ -61,7 +66,7 @@ def comp_err(gpu, cpu, floor=None):
 def residual_floor(pb, Fx, Fy):
     inv = 1.0 / pb.dx + (1.0 / pb.dy if pb.ndim == 2 else 0.0)
     F = [max(np.abs(Fx[c]).max(), np.abs(Fy[c]).max() if Fy is not None else 0.0) for c in range(pb.ncomp)]
-    return [1e-3 * f * inv for f in F]
+    return [1e-2 * f * inv for f in F]
 
 
 def gpu_residual(A, pb, W, sx, sy):
@@ -100,7 +105,7 @@ def check_residual(A, oracle, pb, W, sx, sy):
 
 
 def check_sigma(g, c):
-    bad = np.abs(g - c) > 1e-12 * (1 + np.abs(c)) + 1e-14 * c * c
+    bad = np.abs(g - c) > 1e-12 * (1 + np.abs(c)) + 1e-13 * c * c
     if np.any(bad):
         idx = np.argwhere(bad)[:8]
         raise AssertionError("sigma mismatch at %d faces, e.g. %s" % (
@@ -147,6 +152,28 @@ def test_residual_parity_1d(A, oracle, order, kind):
     pb, W = make_case(kind, 1, order, 20 + order, 300, 1)
     check_residual(A, oracle, pb, W, *oracle.prime_sigma(pb, W))
     check_residual(A, oracle, pb, W, *P.random_sigma(pb, order, 1.0))
+
+
+SWEEP_1D = (64, 333, 1000, 4096)
+SWEEP_2D = (16, 47, 128, 256)
+SWEEP_KINDS = ("smooth", "riemann", "noise")
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_seeded_parity_sweep(A, oracle, seed):
+    """Seeds 0..9 of the parity inputs: smooth Fourier fields, random Riemann data and
+    per-cell white noise, 1D grids of 64..4096 cells and 2D grids of 16^2..256^2, orders
+    3/5/7/9, sigma_in primed and random (uniform in [0, sigma_thres / 2)).  Each seed
+    takes one kind, one order and one size of each dimension in turn, so that the ten
+    seeds cover every kind, order and size."""
+    kind = SWEEP_KINDS[seed % 3]
+    order = (3, 5, 7, 9)[seed % 4]
+    n1 = SWEEP_1D[(seed // 2) % 4]
+    n2 = SWEEP_2D[(seed + 1) % 4]
+    for ndim, nx, ny in ((1, n1, 1), (2, n2, n2)):
+        pb, W = make_case(kind, ndim, order, 1000 + seed, nx, ny)
+        check_residual(A, oracle, pb, W, *oracle.prime_sigma(pb, W))
+        check_residual(A, oracle, pb, W, *P.random_sigma(pb, 2000 + seed, 1.0))
 
 
 @pytest.mark.parametrize("order", [3, 5, 9])
