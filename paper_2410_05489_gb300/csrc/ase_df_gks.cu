@@ -129,6 +129,7 @@ __device__ __forceinline__ void recon_eval_d(const double* v, int vs, const Bran
 struct Maxw {
   double rho, ir, U, V, lam, h;  // ir = 1 / rho, h = 1 / (2 lambda)
   double mu[7], mv[6], mx[3];    // <u^n> (n <= 6), <v^n> (n <= 5), <xi^0>, <xi^2>, <xi^4>
+  double dx4;                    // <xi^4> - <xi^2>^2 = 2 K h^2
 };
 
 template <int DIM>
@@ -153,6 +154,7 @@ __device__ __forceinline__ void maxw_init(const double* W, double gamma, double 
   m.mx[0] = 1.0;
   m.mx[1] = K * h;
   m.mx[2] = (K + 2.0) * h * m.mx[1];
+  m.dx4 = 2.0 * K * h * h;
 }
 
 // <u^n> over u > 0 (pos) or u < 0, n <= 6
@@ -184,47 +186,45 @@ __device__ __forceinline__ double mom1(int i, int s, int t, const double* mu, co
   return 0.5 * (M(s + 2, 0, 0) + M(s, 0, 1));
 }
 
-template <int DIM>
-__device__ __forceinline__ double mom2(int i, int j, int s, int t, const double* mu, const Maxw& m) {
-  auto M = [&](int a, int b, int l) { return mu[a] * m.mv[b] * m.mx[l]; };
-  if (i > j) { const int x = i; i = j; j = x; }
-  if (DIM == 2) {
-    switch (i * 4 + j) {
-      case 0: return M(s, t, 0);
-      case 1: return M(s + 1, t, 0);
-      case 2: return M(s, t + 1, 0);
-      case 3: return 0.5 * (M(s + 2, t, 0) + M(s, t + 2, 0) + M(s, t, 1));
-      case 5: return M(s + 2, t, 0);
-      case 6: return M(s + 1, t + 1, 0);
-      case 7: return 0.5 * (M(s + 3, t, 0) + M(s + 1, t + 2, 0) + M(s + 1, t, 1));
-      case 10: return M(s, t + 2, 0);
-      case 11: return 0.5 * (M(s + 2, t + 1, 0) + M(s, t + 3, 0) + M(s, t + 1, 1));
-      default:
-        return 0.25 * (M(s + 4, t, 0) + M(s, t + 4, 0) + M(s, t, 2)) +
-               0.5 * (M(s + 2, t + 2, 0) + M(s + 2, t, 1) + M(s, t + 2, 1));
-    }
-  }
-  switch (i * 3 + j) {
-    case 0: return M(s, 0, 0);
-    case 1: return M(s + 1, 0, 0);
-    case 2: return 0.5 * (M(s + 2, 0, 0) + M(s, 0, 1));
-    case 4: return M(s + 2, 0, 0);
-    case 5: return 0.5 * (M(s + 3, 0, 0) + M(s + 1, 0, 1));
-    default: return 0.25 * (M(s + 4, 0, 0) + M(s, 0, 2)) + 0.5 * M(s + 2, 0, 1);
-  }
-}
-
-// out_i = rho sum_j a_j <u^s v^t psi_j psi_i>
+// out_i = rho sum_j a_j <u^s v^t psi_j psi_i> = rho <u^s v^t psi_i P> with the polynomial
+// P = psi . a = a0 + a1 u + a2 v + (a3 / 2)(u^2 + v^2 + xi^2) (2D; 1D without v).  The
+// u, v and xi moments factor, so with a0' = a0 + (a3 / 2) <xi^2>,
+//   A(n) = a0' <u^n> + a1 <u^(n+1)> + (a3 / 2) <u^(n+2)>,  B(n) = a2 <v^(n+1)> + (a3 / 2) <v^(n+2)>,
+//   Phi(i, j) = <u^(s+i) v^(t+j) P> = <v^(t+j)> A(s+i) + <u^(s+i)> B(t+j),
+//   <u^s v^t xi^2 P> = <xi^2> Phi(0, 0) + (a3 / 2) (<xi^4> - <xi^2>^2) <u^s> <v^t>,
+// and out = rho (Phi(0,0), Phi(1,0), Phi(0,1), (Phi(2,0) + Phi(0,2) + <u^s v^t xi^2 P>) / 2).
 template <int DIM>
 __device__ __forceinline__ void slope_moments(const double* a, int s, int t, const double* mu, const Maxw& m,
                                               double* out) {
-  constexpr int n = DIM + 2;
+  if (DIM == 2) {
+    const double a3h = 0.5 * a[3];
+    const double a0p = fma(a3h, m.mx[1], a[0]);
+    double A[3], B[3];
 #pragma unroll
-  for (int i = 0; i < n; ++i) {
-    double acc = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      A[k] = fma(a3h, mu[s + k + 2], fma(a[1], mu[s + k + 1], a0p * mu[s + k]));
+      B[k] = fma(a3h, m.mv[t + k + 2], a[2] * m.mv[t + k + 1]);
+    }
+    const double P00 = fma(m.mv[t], A[0], mu[s] * B[0]);
+    const double P10 = fma(m.mv[t], A[1], mu[s + 1] * B[0]);
+    const double P01 = fma(m.mv[t + 1], A[0], mu[s] * B[1]);
+    const double P20 = fma(m.mv[t], A[2], mu[s + 2] * B[0]);
+    const double P02 = fma(m.mv[t + 2], A[0], mu[s] * B[2]);
+    const double Px = fma(m.mx[1], P00, a3h * m.dx4 * (mu[s] * m.mv[t]));
+    out[0] = m.rho * P00;
+    out[1] = m.rho * P10;
+    out[2] = m.rho * P01;
+    out[3] = 0.5 * m.rho * (P20 + P02 + Px);
+  } else {
+    const double a2h = 0.5 * a[2];
+    const double a0p = fma(a2h, m.mx[1], a[0]);
+    double A[3];
 #pragma unroll
-    for (int j = 0; j < n; ++j) acc = fma(a[j], mom2<DIM>(i, j, s, t, mu, m), acc);
-    out[i] = m.rho * acc;
+    for (int k = 0; k < 3; ++k) A[k] = fma(a2h, mu[s + k + 2], fma(a[1], mu[s + k + 1], a0p * mu[s + k]));
+    const double Px = fma(m.mx[1], A[0], a2h * m.dx4 * mu[s]);
+    out[0] = m.rho * A[0];
+    out[1] = m.rho * A[1];
+    out[2] = 0.5 * m.rho * (A[2] + Px);
   }
 }
 
@@ -389,15 +389,26 @@ __device__ __forceinline__ bool gks_physical(const double* q, double gamma) {
 // ---------------------------------------------------------------------------------
 // the face kernel
 // ---------------------------------------------------------------------------------
-// 16 x 16 faces per CTA in 2D (one face per thread): the gas-kinetic flux needs ~255
-// registers, so one CTA runs per SM, and the smaller tile gives more CTAs per grid.
+// One (face, Gauss point) per thread: the gas-kinetic flux needs ~220 registers, so one
+// 256-thread CTA runs per SM, and a tile of TN x TT faces with TN TT G ~ 256 keeps the CTAs
+// small enough that the last wave of a grid is a small part of it (400^2 at order 9: 2525
+// tiles of 4 x 16 faces, 16.6 waves, instead of 650 tiles of 16 x 16 faces, 4.3 waves).
 template <int R, int DIM>
-using GksTileShape = Tile<R, DIM, (DIM == 2) ? 16 : 1, (DIM == 2) ? 16 : 256>;
+struct GksShape {
+  static constexpr int G = (DIM == 2) ? (R == 3 ? 1 : (R - 1) / 2) : 1;
+  static constexpr int TN = (DIM == 2) ? (G == 1 ? 8 : 4) : 256;
+  static constexpr int TT = (DIM == 2) ? 256 / (TN * G) : 1;  // r9: 16, r7: 21, r5: 32, r3: 32
+};
+
+template <int R, int DIM>
+using GksTileShape = Tile<R, DIM, GksShape<R, DIM>::TT, GksShape<R, DIM>::TN>;
 
 template <int R, int DIM>
 struct GksTile {
   using TL = GksTileShape<R, DIM>;
-  static constexpr size_t smem_doubles = TL::smem_doubles + 2 * (size_t)TL::C * TL::NB * TL::NQ;
+  // + normal derivatives at both faces, + per-point flux, flux derivative and sigma
+  static constexpr size_t smem_doubles = TL::smem_doubles + 2 * (size_t)TL::C * TL::NB * TL::NQ +
+                                         (size_t)TL::TN * TL::TT * TL::G * (2 * TL::C + 1);
 };
 
 template <int R, int DIM, int DIR>
@@ -419,6 +430,7 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
   double* sSt = sSn + NB * NSN;
   double* sDP = sSt + (DIM == 2 ? NQ * NST : 0);  // normal derivatives (physical) at xi = 0 / -1
   double* sDM = sDP + C * NB * NQ;
+  double* sR = sDM + C * NB * NQ;                 // [TN TT][G][2C + 1]: F, F_t, sigma per point
 
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int mlin = (DIR == 0) ? g.ny : g.nx;
@@ -472,86 +484,95 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
   }
   __syncthreads();
 
-  for (int it = tid; it < TN * TT; it += NT) {
+  // phase 2: one (face, Gauss point) per thread; the G points of a face are neighbours
+  constexpr int NF = TN * TT;
+  for (int it = tid; it < NF * G; it += NT) {
+    const int fi = it / G, q = it % G;
     int fa, tb;
-    if (DIR == 0) { fa = it % TN; tb = it / TN; }
-    else { tb = it % TT; fa = it / TT; }
+    if (DIR == 0) { fa = fi % TN; tb = fi / TN; }
+    else { tb = fi % TT; fa = fi / TT; }
     const int f = a0 + fa, b = b0 + tb;
     if (f > n || b >= mlin) continue;
-    // tangential branches of the two sides' columns (from the same sigma_in)
-    Branch bt[2];
-    if (DIM == 2) {
+    // each side's value, normal (x) and tangential (y) derivative at point q, face frame
+    // (rho, m_n, m_t, E)
+    double ql[C], qr[C], qlx[C], qrx[C], qly[C], qry[C];
 #pragma unroll
-      for (int side = 0; side < 2; ++side) bt[side] = select_branch<R>(sSt + (fa + side) * NST + tb, g.thres);
+    for (int side = 0; side < 2; ++side) {
+      const int qa = fa + side;
+      const double* Q = side == 0 ? sQP : sQM;
+      const double* Dn = side == 0 ? sDP : sDM;
+      double* v = side == 0 ? ql : qr;
+      double* vx = side == 0 ? qlx : qrx;
+      double* vy = side == 0 ? qly : qry;
+      Branch bt;
+      if (DIM == 2) bt = select_branch<R>(sSt + qa * NST + tb, g.thres);  // the side's column
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
+        if (DIM == 2) {
+          double o, d, nd;
+          recon_eval_d<R, 1>(Q + (src * NB + tb + K) * NQ + qa, NQ, bt, T, D, 2 + q, &o, &d);
+          recon_eval<R, 1>(Dn + (src * NB + tb + K) * NQ + qa, NQ, bt, T, 2 + q, &nd);
+          v[c] = o;
+          vx[c] = nd;
+          vy[c] = d * args.inv_dt;
+        } else {
+          v[c] = Q[src * NQ + qa];
+          vx[c] = Dn[src * NQ + qa];
+          vy[c] = 0.0;
+        }
+      }
     }
-    double ca[C], cb[C];
+    double sg;
+    if (!(gks_physical<C>(ql, g.gamma) && gks_physical<C>(qr, g.gamma))) {
+      // first-order fallback: the two cell averages, no slopes
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
+        ql[c] = sW[(src * NB + tb + KT) * NA + fa + K];
+        qr[c] = sW[(src * NB + tb + KT) * NA + fa + K + 1];
+        qlx[c] = qrx[c] = qly[c] = qry[c] = 0.0;
+      }
+      sg = kSigmaBig;
+      atomicOr(&const_cast<DevState*>(args.st)->flags, 0x2u);
+    } else {
+      sg = sigma_point<C, 1, 2>(ql, qr, g.gamma);
+    }
+    double Fq[C], Ftq[C];
+    gks_point<DIM>(ql, qlx, qly, qr, qrx, qry, g.gamma, Kdof, i4D, dt, idt, args.c1, args.c2, Fq, Ftq);
+    double* res = sR + (size_t)it * (2 * C + 1);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      ca[c] = sW[(c * NB + tb + KT) * NA + fa + K];
-      cb[c] = sW[(c * NB + tb + KT) * NA + fa + K + 1];
+      res[c] = Fq[c];
+      res[C + c] = Ftq[c];
     }
+    res[2 * C] = sg;
+  }
+  __syncthreads();
+
+  // Gauss sums per face, points in order
+  for (int fi = tid; fi < NF; fi += NT) {
+    int fa, tb;
+    if (DIR == 0) { fa = fi % TN; tb = fi / TN; }
+    else { tb = fi % TT; fa = fi / TT; }
+    const int f = a0 + fa, b = b0 + tb;
+    if (f > n || b >= mlin) continue;
     double Fs[C], Fts[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) Fs[c] = Fts[c] = 0.0;
     double ssum = 0.0;
-    bool anyfb = false;
-    // one Gauss point at a time (keeps the live state small)
-#pragma unroll 1
+#pragma unroll
     for (int q = 0; q < G; ++q) {
-      // each side's value, normal (x) and tangential (y) derivative, face frame
-      // (rho, m_n, m_t, E)
-      double ql[C], qr[C], qlx[C], qrx[C], qly[C], qry[C];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int qa = fa + side;
-        const double* Q = side == 0 ? sQP : sQM;
-        const double* Dn = side == 0 ? sDP : sDM;
-        double* v = side == 0 ? ql : qr;
-        double* vx = side == 0 ? qlx : qrx;
-        double* vy = side == 0 ? qly : qry;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
-          if (DIM == 2) {
-            double o, d, nd;
-            recon_eval_d<R, 1>(Q + (src * NB + tb + K) * NQ + qa, NQ, bt[side], T, D, 2 + q, &o, &d);
-            recon_eval<R, 1>(Dn + (src * NB + tb + K) * NQ + qa, NQ, bt[side], T, 2 + q, &nd);
-            v[c] = o;
-            vx[c] = nd;
-            vy[c] = d * args.inv_dt;
-          } else {
-            v[c] = Q[src * NQ + qa];
-            vx[c] = Dn[src * NQ + qa];
-            vy[c] = 0.0;
-          }
-        }
-      }
-      double sg;
-      if (!(gks_physical<C>(ql, g.gamma) && gks_physical<C>(qr, g.gamma))) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const int src = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
-          ql[c] = ca[src];
-          qr[c] = cb[src];
-          qlx[c] = qrx[c] = qly[c] = qry[c] = 0.0;
-        }
-        sg = kSigmaBig;
-        anyfb = true;
-      } else {
-        sg = sigma_point<C, 1, 2>(ql, qr, g.gamma);
-      }
-      double Fq[C], Ftq[C];
-      gks_point<DIM>(ql, qlx, qly, qr, qrx, qry, g.gamma, Kdof, i4D, dt, idt, args.c1, args.c2, Fq, Ftq);
+      const double* res = sR + (size_t)(fi * G + q) * (2 * C + 1);
       const double w = (DIM == 2) ? T.gw[q] : 1.0;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const int dst = (c == 1) ? NI : (c == 2 && C == 4) ? TI : c;
-        Fs[dst] = fma(w, Fq[c], Fs[dst]);
-        Fts[dst] = fma(w, Ftq[c], Fts[dst]);
+        Fs[dst] = fma(w, res[c], Fs[dst]);
+        Fts[dst] = fma(w, res[C + c], Fts[dst]);
       }
-      ssum += sg;
+      ssum += res[2 * C];
     }
-    if (anyfb) atomicOr(&const_cast<DevState*>(args.st)->flags, 0x2u);
     const double sface = (G == 1) ? ssum : ssum * (1.0 / G);
     if (DIR == 0) {
 #pragma unroll
