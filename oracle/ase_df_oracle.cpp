@@ -172,7 +172,11 @@ static inline real kmax(real a, real b) { return rmax(a, b); }
 // ---------------------------------------------------------------------------------
 // Problem description.  Its own copy; the Python wrapper fills it field by field.
 // ---------------------------------------------------------------------------------
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2, BC_REFLECT = 3 };
+// BC_WALL_AFTER (y-lo only): ghost cells whose centre x is below wall_x take the fixed
+// inflow state, the rest mirror a reflecting wall.  BC_MOVING_SHOCK (y-hi only): ghost
+// cells take the inflow state where their centre x is below shock_x0 + shock_speed t and
+// state_b beyond (the double Mach reflection problem of Sec. 4.3, reading G32).
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2, BC_REFLECT = 3, BC_WALL_AFTER = 4, BC_MOVING_SHOCK = 5 };
 
 struct OracleParams {
   int32_t ndim;        // 1 or 2
@@ -186,6 +190,10 @@ struct OracleParams {
   double inflow[4];    // rho, u, v, p of the x-lo inflow band
   double inflow_lo, inflow_hi;  // the band is inflow_lo < y < inflow_hi
   double gks_c1, gks_c2;        // tau_n constants of the gas-kinetic path (reading G24)
+  double t;                     // time of the evaluation (time-dependent boundaries)
+  double state_b[4];            // rho, u, v, p beyond the moving shock (BC_MOVING_SHOCK)
+  double wall_x;                // BC_WALL_AFTER: the wall starts at x = wall_x
+  double shock_x0, shock_speed; // BC_MOVING_SHOCK: the shock is at x = shock_x0 + shock_speed t
 };
 
 namespace {
@@ -539,9 +547,13 @@ struct Grid {
     if (p->ndim == 1) return 0;
     if (j >= 0 && j < ny) return j;
     int bc = (j < 0) ? p->bc[2] : p->bc[3];
-    if (bc == BC_REFLECT) return mirror_cell(j, ny);
+    if (bc == BC_REFLECT || bc == BC_WALL_AFTER) return mirror_cell(j, ny);
     return bc == BC_PERIODIC ? wrap(j, ny) : clampi(j, 0, ny - 1);
   }
+  // centre x of (ghost) column i
+  double xc(int64_t i) const { return p->x0 + ((double)i + 0.5) * dx; }
+  // column i lies before the wall of a BC_WALL_AFTER boundary (its ghosts are fixed)
+  bool before_wall(int64_t i) const { return p->ndim == 2 && p->bc[2] == BC_WALL_AFTER && xc(i) < p->wall_x; }
   int64_t face_x(int64_t f) const {  // x-face index 0..nx
     if (f >= 0 && f <= nx) return f;
     int bc = (f < 0) ? p->bc[0] : p->bc[1];
@@ -551,7 +563,7 @@ struct Grid {
   int64_t face_y(int64_t g) const {  // y-face index 0..ny
     if (g >= 0 && g <= ny) return g;
     int bc = (g < 0) ? p->bc[2] : p->bc[3];
-    if (bc == BC_REFLECT) return g < 0 ? -g : 2 * ny - g;
+    if (bc == BC_REFLECT || bc == BC_WALL_AFTER) return g < 0 ? -g : 2 * ny - g;
     return bc == BC_PERIODIC ? wrap(g, ny) : clampi(g, 0, ny);
   }
   // Conservative value of component c of (possibly ghost) cell (i, j).
@@ -560,16 +572,20 @@ struct Grid {
       double yc = p->y0 + ((double)j + 0.5) * dy;
       if (yc > p->inflow_lo && yc < p->inflow_hi) return inflow_cons(c);
     }
+    if (j < 0 && before_wall(i)) return inflow_cons(c);
+    if (p->ndim == 2 && j >= ny && p->bc[3] == BC_MOVING_SHOCK)
+      return (xc(i) < p->shock_x0 + p->shock_speed * p->t) ? inflow_cons(c) : state_cons(p->state_b, c);
     int64_t ii = cell_x(i), jj = cell_y(j);
     real v = Wd[((int64_t)c * ny + jj) * nx + ii];
     // a reflecting wall negates the momentum normal to it
     const bool rx = (i < 0 && p->bc[0] == BC_REFLECT) || (i >= nx && p->bc[1] == BC_REFLECT);
-    const bool ry = p->ndim == 2 && ((j < 0 && p->bc[2] == BC_REFLECT) || (j >= ny && p->bc[3] == BC_REFLECT));
+    const bool ry = p->ndim == 2 && ((j < 0 && (p->bc[2] == BC_REFLECT || p->bc[2] == BC_WALL_AFTER)) ||
+                                     (j >= ny && p->bc[3] == BC_REFLECT));
     if ((c == 1 && rx) || (c == 2 && ry)) v = -v;
     return v;
   }
-  real inflow_cons(int c) const {
-    double rho = p->inflow[0], u = p->inflow[1], v = p->inflow[2], pr = p->inflow[3];
+  real state_cons(const double* s, int c) const {
+    double rho = s[0], u = s[1], v = s[2], pr = s[3];
     double vv = (p->ndim == 2) ? v : 0.0;
     double E = pr / (p->gamma - 1.0) + 0.5 * rho * (u * u + vv * vv);
     if (c == 0) return real(rho);
@@ -577,11 +593,17 @@ struct Grid {
     if (p->ndim == 2 && c == 2) return real(rho * v);
     return real(E);
   }
+  real inflow_cons(int c) const { return state_cons(p->inflow, c); }
+  // sigma of x-face f on (ghost) row j: below a BC_WALL_AFTER boundary the rows of the
+  // fixed part (the column right of the face before the wall) clamp, the wall mirrors
   real sx(const real* s, int64_t f, int64_t j) const {
-    return s[cell_y(j) * (nx + 1) + face_x(f)];
+    const int64_t jj = (j < 0 && before_wall(f)) ? 0 : cell_y(j);
+    return s[jj * (nx + 1) + face_x(f)];
   }
+  // sigma of y-face g of (ghost) column i: the fixed part of a BC_WALL_AFTER boundary clamps
   real sy(const real* s, int64_t i, int64_t g) const {
-    return s[face_y(g) * nx + cell_x(i)];
+    const int64_t gg = (g < 0 && before_wall(i)) ? 0 : face_y(g);
+    return s[gg * nx + cell_x(i)];
   }
 };
 
@@ -1055,7 +1077,11 @@ bool stage_update(const Grid& g, int stage, real dt, const real* Wn, const real*
 // on exit; sx / sy hold sigma^n on entry and the last stage's sigma on exit.
 bool step_real(const OracleParams* p, std::vector<real>& w, std::vector<real>& sx, std::vector<real>& sy,
                real dt, int64_t* hist) {
-  Grid g = make_grid(p);
+  // stage times t, t + dt, t + dt/2 (the times of the SSP-RK3 stage values)
+  OracleParams p2 = *p, p3 = *p;
+  p2.t = p->t + val(dt);
+  p3.t = p->t + 0.5 * val(dt);
+  Grid g = make_grid(p), g2 = make_grid(&p2), g3 = make_grid(&p3);
   const Sizes z = sizes_of(p);
   const int64_t ny = g.ny;
   int64_t h[BR_COUNT] = {0};
@@ -1067,13 +1093,13 @@ bool step_real(const OracleParams* p, std::vector<real>& w, std::vector<real>& s
   residual(p, Wn.data(), sx.data(), sy.data(), L.data(), sxa.data(), sya.data(), Fx.data(), Fy.data(), h, 0, ny - 1);
   ok &= stage_update(g, 1, dt, Wn.data(), Wn.data(), Fx.data(), Fy.data(), sxa.data(), sya.data(), W1.data(), h);
   // stage 2
-  residual(p, W1.data(), sxa.data(), sya.data(), L.data(), sxb.data(), syb.data(), Fx.data(), Fy.data(), h, 0,
+  residual(&p2, W1.data(), sxa.data(), sya.data(), L.data(), sxb.data(), syb.data(), Fx.data(), Fy.data(), h, 0,
            ny - 1);
-  ok &= stage_update(g, 2, dt, Wn.data(), W1.data(), Fx.data(), Fy.data(), sxb.data(), syb.data(), W2.data(), h);
+  ok &= stage_update(g2, 2, dt, Wn.data(), W1.data(), Fx.data(), Fy.data(), sxb.data(), syb.data(), W2.data(), h);
   // stage 3: its sigma becomes sigma^{n+1}
-  residual(p, W2.data(), sxb.data(), syb.data(), L.data(), sx.data(), sy.data(), Fx.data(), Fy.data(), h, 0,
+  residual(&p3, W2.data(), sxb.data(), syb.data(), L.data(), sx.data(), sy.data(), Fx.data(), Fy.data(), h, 0,
            ny - 1);
-  ok &= stage_update(g, 3, dt, Wn.data(), W2.data(), Fx.data(), Fy.data(), sx.data(), sy.data(), w.data(), h);
+  ok &= stage_update(g3, 3, dt, Wn.data(), W2.data(), Fx.data(), Fy.data(), sx.data(), sy.data(), w.data(), h);
   if (hist) for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[b];
   return ok;
 }
@@ -1624,7 +1650,9 @@ double oracle_gks_step(const OracleParams* p, double* W, double* sx, double* sy,
   int64_t h[BR_COUNT] = {0};
   gks_residual(p, W, sx, syin, dt, L0.data(), Lt0.data(), sxa.data(), sya.data(), h);
   for (int64_t i = 0; i < z.w; ++i) Ws[(size_t)i] = W[i] + 0.5 * dt * L0[(size_t)i] + 0.125 * dt * dt * Lt0[(size_t)i];
-  gks_residual(p, Ws.data(), sxa.data(), sya.data(), dt, L1.data(), Lt1.data(), sx,
+  OracleParams ph = *p;  // the second stage value W* is the state at t + dt/2
+  ph.t = p->t + 0.5 * dt;
+  gks_residual(&ph, Ws.data(), sxa.data(), sya.data(), dt, L1.data(), Lt1.data(), sx,
                (p->ndim == 2) ? sy : syz.data(), h);
   for (int64_t i = 0; i < z.w; ++i)
     W[i] = W[i] + dt * L0[(size_t)i] + (1.0 / 6.0) * dt * dt * (Lt0[(size_t)i] + 2.0 * Lt1[(size_t)i]);

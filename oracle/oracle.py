@@ -54,6 +54,8 @@ class _Params(ctypes.Structure):
         ("bc", ctypes.c_int32 * 4), ("inflow", ctypes.c_double * 4),
         ("inflow_lo", ctypes.c_double), ("inflow_hi", ctypes.c_double),
         ("gks_c1", ctypes.c_double), ("gks_c2", ctypes.c_double),
+        ("t", ctypes.c_double), ("state_b", ctypes.c_double * 4), ("wall_x", ctypes.c_double),
+        ("shock_x0", ctypes.c_double), ("shock_speed", ctypes.c_double),
     ]
 
 
@@ -114,7 +116,9 @@ def _lib(counting: bool = False, tape: bool = False):
     return _libs[key]
 
 
-def _params(pb) -> _Params:
+def _params(pb, t: float = 0.0) -> _Params:
+    """The problem's parameters; t is the time of the evaluation (the moving-shock boundary
+    depends on it)."""
     p = _Params()
     p.ndim, p.order = pb.ndim, pb.order
     p.nx, p.ny = pb.nx, pb.nyc
@@ -126,6 +130,10 @@ def _params(pb) -> _Params:
         p.inflow[i] = pb.inflow[i]
     p.inflow_lo, p.inflow_hi = pb.inflow_lo, pb.inflow_hi
     p.gks_c1, p.gks_c2 = pb.gks_c1, pb.gks_c2
+    p.t = float(t)
+    for i in range(4):
+        p.state_b[i] = pb.state_b[i]
+    p.wall_x, p.shock_x0, p.shock_speed = pb.wall_x, pb.shock_x0, pb.shock_speed
     return p
 
 
@@ -140,8 +148,8 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
-def residual(pb, W, sx, sy, counting: bool = False):
-    """One residual evaluation L(W; sigma_in) -> (L, sx_out, sy_out, Fx, Fy, hist)."""
+def residual(pb, W, sx, sy, counting: bool = False, t: float = 0.0):
+    """One residual evaluation L(W; sigma_in) at time t -> (L, sx_out, sy_out, Fx, Fy, hist)."""
     W, sx, sy = _f64(W), _f64(sx), _f64(sy)
     assert W.shape == pb.state_shape and sx.shape == pb.sx_shape and sy.shape == pb.sy_shape
     L = np.empty_like(W)
@@ -150,7 +158,7 @@ def residual(pb, W, sx, sy, counting: bool = False):
     Fx = np.empty((pb.ncomp, pb.nyc, pb.nx + 1))
     Fy = np.empty((pb.ncomp, pb.ny + 1, pb.nx)) if pb.ndim == 2 else None
     hist = np.zeros(len(BRANCHES), dtype=np.int64)
-    p = _params(pb)
+    p = _params(pb, t)
     _lib(counting).oracle_residual(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), _ptr(L), _ptr(sxo),
                                    _ptr(syo), _ptr(Fx), _ptr(Fy), hist.ctypes.data_as(_I64))
     return L, sxo, syo, Fx, Fy, hist
@@ -187,11 +195,11 @@ def cfl_dt(pb, W) -> float:
     return _lib().oracle_cfl_dt(ctypes.byref(p), _ptr(_f64(W)))
 
 
-def step(pb, W, sx, sy, dt: float = 0.0, hist: Optional[np.ndarray] = None):
-    """One SSP-RK3 step; returns (W_new, sx_new, sy_new, dt_used)."""
+def step(pb, W, sx, sy, dt: float = 0.0, hist: Optional[np.ndarray] = None, t: float = 0.0):
+    """One SSP-RK3 step from time t; returns (W_new, sx_new, sy_new, dt_used)."""
     W, sx, sy = _f64(W).copy(), _f64(sx).copy(), _f64(sy).copy()
     h = hist if hist is not None else np.zeros(len(BRANCHES), dtype=np.int64)
-    p = _params(pb)
+    p = _params(pb, t)
     dt_used = _lib().oracle_step(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), float(dt),
                                  h.ctypes.data_as(_I64))
     return W, sx, sy, dt_used
@@ -214,7 +222,7 @@ def run(pb, W, t_end: float = 0.0, nsteps: int = 0, dt: float = 0.0, sigma=None)
             raise FloatingPointError("non-physical state at t=%g" % t)
         if t_end and t + h > t_end:
             h = t_end - t
-        W, sx, sy, h = step(pb, W, sx, sy, h)
+        W, sx, sy, h = step(pb, W, sx, sy, h, t=t)
         if h < 0:
             raise FloatingPointError("non-physical state after the step at t=%g" % t)
         t += h
@@ -326,25 +334,26 @@ def gks_point(dim: int, gamma: float, Wl, Wlx, Wly, Wr, Wrx, Wry, dt: float, c1:
     return F, Ft
 
 
-def gks_residual(pb, W, sx, sy, dt: float):
-    """One GKS evaluation: -> (L, L_t, sx_out, sy_out, hist)."""
+def gks_residual(pb, W, sx, sy, dt: float, t: float = 0.0):
+    """One GKS evaluation at time t: -> (L, L_t, sx_out, sy_out, hist)."""
     W, sx, sy = _f64(W), _f64(sx), _f64(sy)
     L = np.empty_like(W)
     Lt = np.empty_like(W)
     sxo = np.empty(pb.sx_shape)
     syo = np.zeros(pb.sy_shape)
     hist = np.zeros(len(BRANCHES), dtype=np.int64)
-    p = _params(pb)
+    p = _params(pb, t)
     _lib().oracle_gks_residual(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), float(dt), _ptr(L), _ptr(Lt),
                                _ptr(sxo), _ptr(syo), hist.ctypes.data_as(_I64))
     return L, Lt, sxo, syo, hist
 
 
-def gks_step(pb, W, sx, sy, dt: float = 0.0, hist: Optional[np.ndarray] = None):
-    """One S2O4 step (CFL when dt <= 0): -> (W, sx, sy, dt used; negative if non-physical)."""
+def gks_step(pb, W, sx, sy, dt: float = 0.0, hist: Optional[np.ndarray] = None, t: float = 0.0):
+    """One S2O4 step from time t (CFL when dt <= 0): -> (W, sx, sy, dt used; negative if
+    non-physical)."""
     W, sx, sy = _f64(W).copy(), _f64(sx).copy(), _f64(sy).copy()
     h = np.zeros(len(BRANCHES), dtype=np.int64) if hist is None else hist
-    p = _params(pb)
+    p = _params(pb, t)
     d = _lib().oracle_gks_step(ctypes.byref(p), _ptr(W), _ptr(sx), _ptr(sy), float(dt), h.ctypes.data_as(_I64))
     return W, sx, sy, d
 
@@ -367,7 +376,7 @@ def gks_run(pb, W, t_end: float = 0.0, nsteps: int = 0, dt: float = 0.0, dt_cap:
             h = min(h, dt_cap)
         if t_end and t + h > t_end:
             h = t_end - t
-        W, sx, sy, h2 = gks_step(pb, W, sx, sy, h)
+        W, sx, sy, h2 = gks_step(pb, W, sx, sy, h, t=t)
         if h2 < 0:
             raise FloatingPointError("non-physical state after the step at t=%g" % t)
         t += h

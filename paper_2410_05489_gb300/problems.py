@@ -25,7 +25,7 @@ from typing import Callable, Sequence, Tuple
 
 import numpy as np
 
-BC_NAMES = {"periodic": 0, "outflow": 1, "inflow": 2, "reflect": 3}
+BC_NAMES = {"periodic": 0, "outflow": 1, "inflow": 2, "reflect": 3, "wall_after": 4, "moving_shock": 5}
 
 
 @dataclasses.dataclass
@@ -35,7 +35,11 @@ class Problem:
     bc is (x-lo, x-hi, y-lo, y-hi), each "periodic", "outflow", "reflect" (a wall: mirrored
     ghost cells with the normal momentum negated) or (x-lo only) "inflow": the inflow band
     inflow_lo < y < inflow_hi of the x-lo boundary takes the fixed primitive state
-    inflow = (rho, u, v, p); outside the band it is outflow.
+    inflow = (rho, u, v, p); outside the band it is outflow.  Two more for the double Mach
+    reflection: (y-lo only) "wall_after": ghost cells whose centre x is below wall_x take the
+    inflow state, the rest a reflecting wall; (y-hi only) "moving_shock": ghost cells take
+    the inflow state where their centre x is below shock_x0 + shock_speed t, and state_b
+    beyond.
     """
 
     ndim: int
@@ -55,6 +59,10 @@ class Problem:
     inflow_hi: float = 0.0
     gks_c1: float = 0.05   # tau_n constants of the gas-kinetic path (Sec. 2.2; the paper's
     gks_c2: float = 1.0    # captions give 0.05 and 1.0, and c2 = 5.0 for the blast wave)
+    state_b: Tuple[float, float, float, float] = (0.0, 0.0, 0.0, 0.0)
+    wall_x: float = 0.0
+    shock_x0: float = 0.0
+    shock_speed: float = 0.0
 
     @property
     def ncomp(self) -> int:
@@ -296,6 +304,31 @@ def configuration3(n: int, order: int, gks_c1: float = 0.05, gks_c2: float = 1.0
     v = np.where(lo_x & lo_y, 1.206, np.where(~lo_x & lo_y, 1.206, np.where(~lo_x & ~lo_y, 0.0, 0.0)))
     p = np.where(lo_x & lo_y, 0.129, np.where(~lo_x & lo_y, 0.3, np.where(~lo_x & ~lo_y, 1.5, 0.3)))
     return pb, np.ascontiguousarray(conservative((rho, u, v, p), pb.gamma, 2))
+
+
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)
+DMR_POST = (8.0, 7.145, -4.125, 116.8333)
+
+
+def double_mach_reflection(nx: int, order: int, gks_c1: float = 0.05, gks_c2: float = 1.0,
+                           post: Tuple[float, float, float, float] = DMR_POST) -> Tuple[Problem, np.ndarray]:
+    """Double Mach reflection, Sec. 4.3 Example 4 (reading G32): [0,4] x [0,1] with nx x nx/4
+    cells, gamma 1.4; a Mach 10 shock at 60 degrees to the x-axis through (1/6, 0), the
+    pre-shock state (1.4, 0, 0, 1) below y = sqrt(3) (x - 1/6) and the post-shock state
+    (8, 7.145, -4.125, 116.8333) above; x-lo the post-shock inflow, x-hi outflow, y-lo the
+    post-shock state for x < 1/6 and a slip wall after, y-hi the exact shock position
+    x = 1/6 + (1 + 20 t) / sqrt(3).  Cell averages by 8 x 8 Gauss points."""
+    s3 = np.sqrt(3.0)
+    pb = Problem(ndim=2, nx=nx, ny=nx // 4, x0=0.0, x1=4.0, y0=0.0, y1=1.0, order=order, gamma=1.4,
+                 bc=("inflow", "outflow", "wall_after", "moving_shock"), inflow=tuple(post),
+                 inflow_lo=-1.0, inflow_hi=2.0, state_b=DMR_PRE, wall_x=1.0 / 6.0,
+                 shock_x0=1.0 / 6.0 + 1.0 / s3, shock_speed=20.0 / s3, gks_c1=gks_c1, gks_c2=gks_c2)
+
+    def prim(x, y):
+        pre = y < s3 * (x - 1.0 / 6.0)
+        return tuple(np.where(pre, a, b) for a, b in zip(DMR_PRE, post))
+
+    return pb, cell_average(pb, prim, npts=8)
 
 
 def smooth_random(pb: Problem, seed: int, nmodes: int = 3) -> np.ndarray:
