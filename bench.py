@@ -41,7 +41,7 @@ HBM_BYTES_PER_CELL_STAGE_2D = 128.0  # read W^(s), W^n, write W^(s+1), sigma in/
 # DRAM bytes (read + write) per sweep launch measured by ncu on this kernel for the 1024^2,
 # order-9 workload (mean of the x- and y-face launches; profiles/sweep_kernel_r9_2d_vortex1024_ncu.md).
 # Reported as roofline.traffic for that workload only (null for other sizes / orders).
-SWEEP_DRAM_BYTES_1024_R9 = 62.70e6
+SWEEP_DRAM_BYTES_1024_R9 = None
 
 
 def algorithmic_flops_per_face(ndim: int, r: int) -> float:
@@ -723,6 +723,39 @@ def suite_bench(args):
                      "gpu": per_n, "unit": "Mcell-updates/s per stage (2 stages per S2O4 step)",
                      "cpu_1core": {"value": round(pbc.ncells / one / 1e6, 4), "cores": 1,
                                    "sample": "one GKS stage of Configuration 3 at 100^2, oracle"}})
+    # double Mach reflection at the paper's 960 x 240 (Sec. 4.3 Example 4), order 9, both
+    # flux solvers: 20 CFL steps from t = 0 after 2 warm-up steps; oracle one stage at 240 x 60
+    for gks in (False, True):
+        pb, W0 = P.double_mach_reflection(960, 9)
+        s = A.Solver(pb, W0)
+        for _ in range(2):
+            s.gks_step() if gks else s.step()
+        s.set_state(W0)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(20):
+            s.gks_step() if gks else s.step()
+        e1.record()
+        e1.synchronize()
+        gms = e0.elapsed_time(e1)
+        flags, _, t_gpu = s.status()
+        s.close()
+        stages = 2 if gks else 3
+        pbc, Wc = P.double_mach_reflection(240, 9)
+        sxc, syc = O.prime_sigma(pbc, Wc)
+        t0 = time.perf_counter()
+        if gks:
+            O.gks_residual(pbc, Wc, sxc, syc, 0.5 * O.cfl_dt(pbc, Wc))
+        else:
+            O.residual(pbc, Wc, sxc, syc)
+        one = time.perf_counter() - t0
+        rows.append({"config": "double Mach reflection 960x240, r=9, %s, 20 CFL steps from t=0" %
+                               ("GKS + S2O4" if gks else "L-F + SSP-RK3"),
+                     "gpu": {"value": round(pb.ncells * stages * 20 / (gms * 1e-3) / 1e6, 3),
+                             "ms_per_step": round(gms / 20, 4), "t": t_gpu, "flags": flags},
+                     "cpu_1core": {"value": round(pbc.ncells / one / 1e6, 4), "cores": 1,
+                                   "sample": "one stage at 240x60, oracle"}})
     print(json.dumps({"suite": rows, "cores": cores}), flush=True)
 
 

@@ -56,9 +56,17 @@ typedef enum {
   ASE_DF_BC_OUTFLOW = 1,    /* zero-gradient: ghost cells copy the nearest interior cell */
   ASE_DF_BC_INFLOW_BAND = 2, /* x-lo only: ghost cells whose centre y lies in
                                (inflow_lo, inflow_hi) hold inflow_state; outflow elsewhere */
-  ASE_DF_BC_REFLECT = 3     /* reflecting wall: ghost cells mirror the interior about the wall
+  ASE_DF_BC_REFLECT = 3,    /* reflecting wall: ghost cells mirror the interior about the wall
                                face with the normal momentum negated (needs (r+1)/2 cells or
                                more in that direction; not supported by the adjoint) */
+  ASE_DF_BC_WALL_AFTER = 4, /* y-lo only (2D; the double Mach reflection of Sec. 4.3): ghost
+                               cells whose centre x is below wall_x hold inflow_state, the
+                               others a reflecting wall (needs (r+1)/2 rows or more) */
+  ASE_DF_BC_MOVING_SHOCK = 5 /* y-hi only (2D): ghost cells whose centre x is below
+                               shock_x0 + shock_speed t hold inflow_state, the others state_b;
+                               t is the time of the stage being evaluated (the device time of
+                               the context plus the stage's offset: SSP-RK3 stages at t,
+                               t + dt, t + dt/2; gas-kinetic S2O4 stages at t, t + dt/2) */
 } ase_df_bc;
 
 /* Device status word bits (ase_df_get_status). */
@@ -88,6 +96,9 @@ typedef struct {
                               (Sec. 2.2); <= 0 takes 0.05 and 1.0, the values of the paper's
                               figure captions for Configuration 3, Shu-Osher and the double Mach
                               reflection (5.0 for c2 in its blast wave) */
+  double state_b[4];       /* primitive (rho, u, v, p) beyond the moving shock (ASE_DF_BC_MOVING_SHOCK) */
+  double wall_x;           /* ASE_DF_BC_WALL_AFTER: x where the wall starts */
+  double shock_x0, shock_speed;  /* ASE_DF_BC_MOVING_SHOCK: shock at x = shock_x0 + shock_speed t */
 } ase_df_params;
 
 typedef struct ase_df_ctx ase_df_ctx;

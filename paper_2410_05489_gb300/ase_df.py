@@ -45,6 +45,8 @@ class ase_df_params(ctypes.Structure):
         ("inflow_lo", ctypes.c_double), ("inflow_hi", ctypes.c_double),
         ("t_end", ctypes.c_double),
         ("gks_c1", ctypes.c_double), ("gks_c2", ctypes.c_double),
+        ("state_b", ctypes.c_double * 4), ("wall_x", ctypes.c_double),
+        ("shock_x0", ctypes.c_double), ("shock_speed", ctypes.c_double),
     ]
 
 
@@ -105,6 +107,9 @@ def params_from_problem(pb: Problem, t_end: float = 0.0) -> ase_df_params:
     p.inflow_lo, p.inflow_hi = pb.inflow_lo, pb.inflow_hi
     p.t_end = t_end
     p.gks_c1, p.gks_c2 = pb.gks_c1, pb.gks_c2
+    for i in range(4):
+        p.state_b[i] = pb.state_b[i]
+    p.wall_x, p.shock_x0, p.shock_speed = pb.wall_x, pb.shock_x0, pb.shock_speed
     return p
 
 
@@ -263,6 +268,11 @@ class Solver:
         if prime:
             self.prime()
         ase_df_reset(self.ctx, 0.0)
+
+    def set_time(self, t: float) -> None:
+        """Sets the device time t (and clears the status word); time-dependent boundaries
+        are evaluated at it."""
+        ase_df_reset(self.ctx, t)
 
     def prime(self) -> None:
         ase_df_prime_sigma(self.ctx, self.W, self.sx, self._sy(self.sy))

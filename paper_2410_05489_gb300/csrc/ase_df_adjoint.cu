@@ -452,7 +452,7 @@ adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const 
     else { bb = idx % NB; ai = (idx / NB) % NA; c = idx / (NA * NB); }
     const int a = a0 - 1 - K + ai, b = b0 - KT + bb;
     const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
-    sW[(c * NB + bb) * NA + ai] = fetch_w(g, args.W, c, i, j);
+    sW[(c * NB + bb) * NA + ai] = fetch_w(g, args.W, c, i, j, 0.0);
   }
   for (int idx = tid; idx < NB * NSN; idx += NT) {
     const int fa = idx % NSN, bb = idx / NSN;
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(256) adj_normal_kernel(const GridInfo g, const
 #pragma unroll
       for (int m = 0; m < NS; ++m) {
         const int x = a - K + m;
-        v[m] = (DIR == 0) ? fetch_w(g, args.W, c, x, l) : fetch_w(g, args.W, c, l, x);
+        v[m] = (DIR == 0) ? fetch_w(g, args.W, c, x, l, 0.0) : fetch_w(g, args.W, c, l, x, 0.0);
         vb[m] = 0.0;
       }
       const double pb[2] = {QPb[c], QMb[c]};

@@ -111,6 +111,19 @@ static double sound_speed_sum(const ase_df_params& p, double inv_dx, double inv_
   return s;
 }
 
+// primitive (rho, u, v, p) -> conservative (rho, rho u, [rho v], E)
+static void to_conservative(const double* q, double gamma, int C, double* out) {
+  const double rho = q[0], u = q[1], v = q[2], pr = q[3];
+  out[0] = rho;
+  out[1] = rho * u;
+  if (C == 4) {
+    out[2] = rho * v;
+    out[3] = pr / (gamma - 1.0) + 0.5 * rho * (u * u + v * v);
+  } else {
+    out[2] = pr / (gamma - 1.0) + 0.5 * rho * u * u;
+  }
+}
+
 extern "C" {
 
 ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
@@ -133,24 +146,39 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
   if (!(p.sigma_thres > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "sigma_thres must be > 0");
   if (!(p.cfl > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "cfl must be > 0");
   for (int s = 0; s < 4; ++s) {
-    if (p.bc[s] < 0 || p.bc[s] > 3) return fail(nullptr, ASE_DF_E_INVAL, "bad boundary code %d", p.bc[s]);
+    if (p.bc[s] < 0 || p.bc[s] > 5) return fail(nullptr, ASE_DF_E_INVAL, "bad boundary code %d", p.bc[s]);
     if (p.bc[s] == ASE_DF_BC_INFLOW_BAND && s != 0)
       return fail(nullptr, ASE_DF_E_INVAL, "the inflow band is supported on x-lo only");
+    if (p.bc[s] == ASE_DF_BC_WALL_AFTER && (s != 2 || p.ndim != 2))
+      return fail(nullptr, ASE_DF_E_INVAL, "the split wall is supported on y-lo of a 2D grid only");
+    if (p.bc[s] == ASE_DF_BC_MOVING_SHOCK && (s != 3 || p.ndim != 2))
+      return fail(nullptr, ASE_DF_E_INVAL, "the moving-shock boundary is supported on y-hi of a 2D grid only");
     if (p.ndim == 1 && s >= 2) p.bc[s] = ASE_DF_BC_OUTFLOW;
   }
   {
     const int64_t need = (p.order + 1) / 2;
     if ((p.bc[0] == ASE_DF_BC_REFLECT || p.bc[1] == ASE_DF_BC_REFLECT) && p.nx < need)
       return fail(nullptr, ASE_DF_E_INVAL, "a reflecting x-wall needs nx >= %lld", (long long)need);
-    if (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_REFLECT || p.bc[3] == ASE_DF_BC_REFLECT) && p.ny < need)
+    if (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_REFLECT || p.bc[3] == ASE_DF_BC_REFLECT ||
+                        p.bc[2] == ASE_DF_BC_WALL_AFTER) && p.ny < need)
       return fail(nullptr, ASE_DF_E_INVAL, "a reflecting y-wall needs ny >= %lld", (long long)need);
   }
   if ((p.bc[0] == ASE_DF_BC_PERIODIC) != (p.bc[1] == ASE_DF_BC_PERIODIC))
     return fail(nullptr, ASE_DF_E_INVAL, "periodic boundaries must come in pairs (x)");
   if (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_PERIODIC) != (p.bc[3] == ASE_DF_BC_PERIODIC))
     return fail(nullptr, ASE_DF_E_INVAL, "periodic boundaries must come in pairs (y)");
-  if (p.bc[0] == ASE_DF_BC_INFLOW_BAND && !(p.inflow_state[0] > 0.0 && p.inflow_state[3] > 0.0))
+  const bool uses_inflow = p.bc[0] == ASE_DF_BC_INFLOW_BAND || p.bc[2] == ASE_DF_BC_WALL_AFTER ||
+                           p.bc[3] == ASE_DF_BC_MOVING_SHOCK;
+  if (uses_inflow && !(p.inflow_state[0] > 0.0 && p.inflow_state[3] > 0.0))
     return fail(nullptr, ASE_DF_E_INVAL, "inflow state must have rho > 0 and p > 0");
+  if (p.bc[3] == ASE_DF_BC_MOVING_SHOCK) {
+    if (!(p.state_b[0] > 0.0 && p.state_b[3] > 0.0))
+      return fail(nullptr, ASE_DF_E_INVAL, "state_b must have rho > 0 and p > 0");
+    if (!std::isfinite(p.shock_x0) || !std::isfinite(p.shock_speed))
+      return fail(nullptr, ASE_DF_E_INVAL, "shock_x0 and shock_speed must be finite");
+  }
+  if (p.bc[2] == ASE_DF_BC_WALL_AFTER && !std::isfinite(p.wall_x))
+    return fail(nullptr, ASE_DF_E_INVAL, "wall_x must be finite");
 
   ase_df_ctx* c = new (std::nothrow) ase_df_ctx;
   if (!c) return fail(nullptr, ASE_DF_E_NOMEM, "host allocation failed");
@@ -188,16 +216,24 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
       }
     }
     if (j0 >= 0) { g.band_j0 = j0; g.band_j1 = j1; }
-    const double rho = p.inflow_state[0], u = p.inflow_state[1], v = p.inflow_state[2], pr = p.inflow_state[3];
-    g.inflow_cons[0] = rho;
-    g.inflow_cons[1] = rho * u;
-    if (C == 4) {
-      g.inflow_cons[2] = rho * v;
-      g.inflow_cons[3] = pr / (p.gamma - 1.0) + 0.5 * rho * (u * u + v * v);
-    } else {
-      g.inflow_cons[2] = pr / (p.gamma - 1.0) + 0.5 * rho * u * u;
-    }
     c->inflow_speed = sound_speed_sum(p, c->inv_dx, c->inv_dy);
+  }
+  if (uses_inflow) to_conservative(p.inflow_state, p.gamma, C, g.inflow_cons);
+  if (p.bc[3] == ASE_DF_BC_MOVING_SHOCK) to_conservative(p.state_b, p.gamma, C, g.state_b_cons);
+  g.x0 = p.x0;
+  g.dx = c->dx;
+  g.shock_x0 = p.shock_x0;
+  g.shock_speed = p.shock_speed;
+  if (p.bc[2] == ASE_DF_BC_WALL_AFTER) {
+    // the first column whose centre x0 + (i + 1/2) dx is at or past wall_x; ghost columns
+    // reach k + 1 cells beyond the grid, so the search is confined to that range
+    const int lo = -(c->K + 2), hi = g.nx + c->K + 2;
+    auto centre = [&](int i) { return p.x0 + ((double)i + 0.5) * c->dx; };
+    const double est = std::floor((p.wall_x - p.x0) / c->dx - 0.5) - 2.0;
+    int i0 = (int)std::max((double)lo, std::min((double)hi, est));
+    while (i0 > lo && centre(i0) >= p.wall_x) --i0;
+    while (i0 < hi && centre(i0) < p.wall_x) ++i0;
+    g.wall_i0 = i0;
   }
   g.gamma = p.gamma;
   g.thres = p.sigma_thres;
@@ -268,8 +304,9 @@ const char* ase_df_last_error(const ase_df_ctx* c) { return c ? c->err : g_init_
 // launch sequences
 // ---------------------------------------------------------------------------------
 static cudaError_t sweep(ase_df_ctx* c, int dir, const double* W, const double* sx, const double* sy,
-                         double* F, double* s_out, cudaStream_t s) {
+                         double* F, double* s_out, cudaStream_t s, double tfrac) {
   SweepArgs a;
+  a.tfrac = tfrac;
   a.W = W;
   a.s_norm = (dir == 0) ? sx : sy;
   a.s_tan = (dir == 0) ? sy : sx;
@@ -285,13 +322,18 @@ static cudaError_t sweep(ase_df_ctx* c, int dir, const double* W, const double* 
   }
 }
 
-// Face fluxes of both directions of W with sigma_in = (sx, sy), sigma_out -> (sxo, syo).
+// Face fluxes of both directions of W with sigma_in = (sx, sy), sigma_out -> (sxo, syo);
+// time-dependent ghosts at the device time t + tfrac dt.
 static cudaError_t face_fluxes(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
-                               double* sxo, double* syo, cudaStream_t s) {
-  cudaError_t e = sweep(c, 0, W, sx, sy, c->Fx, sxo, s);
+                               double* sxo, double* syo, cudaStream_t s, double tfrac = 0.0) {
+  cudaError_t e = sweep(c, 0, W, sx, sy, c->Fx, sxo, s, tfrac);
   if (e != cudaSuccess || c->dim == 1) return e;
-  return sweep(c, 1, W, sx, sy, c->Fy, syo, s);
+  return sweep(c, 1, W, sx, sy, c->Fy, syo, s, tfrac);
 }
+
+// Time offsets of the SSP-RK3 stage values (Sec. 2.3): W^n at t, W^(1) at t + dt, W^(2) at
+// t + dt/2; stage s's fluxes and repair see the boundaries at the time of its input.
+static double rk_tfrac(int stage) { return stage == 2 ? 1.0 : (stage == 3 ? 0.5 : 0.0); }
 
 // Stage combination (or L for stage 0); for stages 1..3 followed by the positivity
 // repair passes, which get the stage's sigma_out (sxo, syo).
@@ -332,6 +374,7 @@ static cudaError_t combine(ase_df_ctx* c, int stage, const double* Wn, const dou
   r.inv_dy = c->inv_dy;
   r.dt_fixed = dt_fixed;
   r.stage = stage;
+  r.tfrac = rk_tfrac(stage);
   for (int pass = 1; pass <= kRepairPasses && e == cudaSuccess; ++pass) {
     r.pass = pass;
     ProfScope prof(c, s, 4);
@@ -371,10 +414,10 @@ static ase_df_status step_launches(ase_df_ctx* c, double* W, double* sx, double*
   if ((e = face_fluxes(c, W, sx, sy, c->sxa, c->sya, s)) != cudaSuccess) return cuda_fail(c, e, "stage 1 sweep");
   if ((e = combine(c, 1, W, W, c->W1, dtf, s, c->sxa, c->sya)) != cudaSuccess) return cuda_fail(c, e, "stage 1 combine");
   // stage 2
-  if ((e = face_fluxes(c, c->W1, c->sxa, c->sya, c->sxb, c->syb, s)) != cudaSuccess) return cuda_fail(c, e, "stage 2 sweep");
+  if ((e = face_fluxes(c, c->W1, c->sxa, c->sya, c->sxb, c->syb, s, rk_tfrac(2))) != cudaSuccess) return cuda_fail(c, e, "stage 2 sweep");
   if ((e = combine(c, 2, W, c->W1, c->W2, dtf, s, c->sxb, c->syb)) != cudaSuccess) return cuda_fail(c, e, "stage 2 combine");
   // stage 3: sigma_out lands in the caller's sx / sy, W^{n+1} in W
-  if ((e = face_fluxes(c, c->W2, c->sxb, c->syb, sx, sy, s)) != cudaSuccess) return cuda_fail(c, e, "stage 3 sweep");
+  if ((e = face_fluxes(c, c->W2, c->sxb, c->syb, sx, sy, s, rk_tfrac(3))) != cudaSuccess) return cuda_fail(c, e, "stage 3 sweep");
   if ((e = combine(c, 3, W, c->W2, W, dtf, s, sx, sy)) != cudaSuccess) return cuda_fail(c, e, "stage 3 combine");
   return ASE_DF_OK;
 }
@@ -556,7 +599,7 @@ ase_df_status ase_df_residual_adjoint(ase_df_ctx* c, const double* W, const doub
   if (r != ASE_DF_OK) return r;
   if (!Wbar) return fail(c, ASE_DF_E_INVAL, "Wbar is NULL");
   for (int b = 0; b < 4; ++b)
-    if (c->g.bc[b] == BC_REFLECT) return fail(c, ASE_DF_E_INVAL, "the adjoint does not support reflecting walls");
+    if (c->g.bc[b] >= BC_REFLECT) return fail(c, ASE_DF_E_INVAL, "the adjoint does not support walls or the moving-shock boundary");
   if (Wbar == W || Wbar == Lbar || (sxbar_in && (sxbar_in == sx_in || sxbar_in == sxbar_out)) ||
       (c->dim == 2 && sybar_in && (sybar_in == sy_in || sybar_in == sybar_out)))
     return fail(c, ASE_DF_E_INVAL, "adjoint outputs must not alias the inputs");
@@ -575,7 +618,7 @@ ase_df_status ase_df_step_adjoint(ase_df_ctx* c, const double* W, const double* 
   if (r != ASE_DF_OK) return r;
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ASE_DF_E_INVAL, "the step adjoint needs a fixed dt > 0");
   for (int b = 0; b < 4; ++b)
-    if (c->g.bc[b] == BC_REFLECT) return fail(c, ASE_DF_E_INVAL, "the adjoint does not support reflecting walls");
+    if (c->g.bc[b] >= BC_REFLECT) return fail(c, ASE_DF_E_INVAL, "the adjoint does not support walls or the moving-shock boundary");
   if (!Wbar || !sxbar || (c->dim == 2 && !sybar)) return fail(c, ASE_DF_E_INVAL, "NULL adjoint pointer");
   if (Wbar == W || sxbar == sx || (c->dim == 2 && sybar == sy))
     return fail(c, ASE_DF_E_INVAL, "adjoint arrays must not alias the state");
@@ -594,7 +637,7 @@ ase_df_status ase_df_step_adjoint(ase_df_ctx* c, const double* W, const double* 
   // stages 1 and 2 of the forward step: W1, sigma1 (sxa, sya), W2, sigma2 (sxb, syb)
   if ((e = face_fluxes(c, W, sx, sy, c->sxa, c->sya, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 1 sweep");
   if ((e = combine(c, 1, W, W, c->W1, dt, s, c->sxa, c->sya)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 1 combine");
-  if ((e = face_fluxes(c, c->W1, c->sxa, c->sya, c->sxb, c->syb, s)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 2 sweep");
+  if ((e = face_fluxes(c, c->W1, c->sxa, c->sya, c->sxb, c->syb, s, rk_tfrac(2))) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 2 sweep");
   if ((e = combine(c, 2, W, c->W1, c->W2, dt, s, c->sxb, c->syb)) != cudaSuccess) return cuda_fail(c, e, "adjoint: stage 2 combine");
   // stage 3: W^{n+1} = W^n / 3 + 2/3 W2 + 2/3 dt L(W2, sigma2), sigma3 = sigma_out(W2, sigma2)
   e = launch_axpby(c->Abn, 1.0 / 3.0, Wbar, 0.0, nullptr, nW, s);
@@ -652,9 +695,11 @@ static ase_df_status ensure_gks(ase_df_ctx* c) {
 }
 
 static cudaError_t gks_face_fluxes(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
-                                   double* sxo, double* syo, double dt_fixed, cudaStream_t s) {
+                                   double* sxo, double* syo, double dt_fixed, cudaStream_t s,
+                                   double tfrac = 0.0) {
   for (int dir = 0; dir < c->dim; ++dir) {
     GksSweepArgs a;
+    a.tfrac = tfrac;
     a.W = W;
     a.s_norm = (dir == 0) ? sx : sy;
     a.s_tan = (dir == 0) ? sy : sx;
@@ -743,7 +788,7 @@ ase_df_status ase_df_gks_step(ase_df_ctx* c, double* W, double* sx, double* sy, 
   if (e == cudaSuccess) e = gks_face_fluxes(c, W, sx, sy, c->sxa, c->sya, dtf, s);
   if (e == cudaSuccess) e = gks_combine(c, 1, W, c->W1, nullptr, dtf, s);
   // stage 2: W^{n+1} from L(W^n), L_t(W^n) and L_t(W*); its sigma lands in sx, sy
-  if (e == cudaSuccess) e = gks_face_fluxes(c, c->W1, c->sxa, c->sya, sx, sy, dtf, s);
+  if (e == cudaSuccess) e = gks_face_fluxes(c, c->W1, c->sxa, c->sya, sx, sy, dtf, s, 0.5);  // W* at t + dt/2
   if (e == cudaSuccess) e = gks_combine(c, 2, W, W, nullptr, dtf, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "gas-kinetic step");
   return ASE_DF_OK;

@@ -115,6 +115,7 @@ __device__ __forceinline__ void repair_range(const GridInfo& g, const RepairArgs
   const int nx = g.nx, ny = g.ny;
   const size_t ncell = (size_t)nx * ny;
   const double dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.st->dt;
+  const double ts = stage_time(a.st, a.tfrac, dt);  // for time-dependent ghosts
   const unsigned int pass = (unsigned int)a.pass;
   auto marked = [&](int i, int j) {
     const unsigned int m = a.mark[(size_t)j * nx + i];
@@ -142,8 +143,8 @@ __device__ __forceinline__ void repair_range(const GridInfo& g, const RepairArgs
         double cl[C], cr[C], F2[C], sg;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          cl[c] = fetch_w(g, a.Ws, c, f - 1, j);
-          cr[c] = fetch_w(g, a.Ws, c, f, j);
+          cl[c] = fetch_w(g, a.Ws, c, f - 1, j, ts);
+          cr[c] = fetch_w(g, a.Ws, c, f, j, ts);
         }
         lf_point<C, 1, 2>(cl, cr, cl, cr, 1, g.gamma, F2, sg);
 #pragma unroll
@@ -159,8 +160,8 @@ __device__ __forceinline__ void repair_range(const GridInfo& g, const RepairArgs
           double cl[C], cr[C], F2[C], sg;
 #pragma unroll
           for (int c = 0; c < C; ++c) {
-            cl[c] = fetch_w(g, a.Ws, c, i, fy - 1);
-            cr[c] = fetch_w(g, a.Ws, c, i, fy);
+            cl[c] = fetch_w(g, a.Ws, c, i, fy - 1, ts);
+            cr[c] = fetch_w(g, a.Ws, c, i, fy, ts);
           }
           lf_point<C, 2, 1>(cl, cr, cl, cr, 1, g.gamma, F2, sg);
 #pragma unroll

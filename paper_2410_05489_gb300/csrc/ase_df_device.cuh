@@ -81,11 +81,12 @@ __device__ __forceinline__ double rsqrt_pos(double x) {
 }
 
 // cell index 0..n-1 of a (ghost) cell; a reflecting wall mirrors about its face (the
-// ghost layers reach at most k+1 <= n cells deep, which the context validates)
+// ghost layers reach at most k+1 <= n cells deep, which the context validates); the wall
+// part of a BC_WALL_AFTER boundary mirrors too (its fixed part is handled by the callers)
 __device__ __forceinline__ int wrap_or_clamp(int i, int n, int bc_lo, int bc_hi) {
   if (i < 0) {
     if (bc_lo == BC_PERIODIC) { int m = i % n; return m < 0 ? m + n : m; }
-    if (bc_lo == BC_REFLECT) return -1 - i;
+    if (bc_lo == BC_REFLECT || bc_lo == BC_WALL_AFTER) return -1 - i;
     return 0;
   }
   if (i >= n) {
@@ -101,7 +102,7 @@ __device__ __forceinline__ int face_map(int f, int n, int bc_lo, int bc_hi) {
   if (f >= 0 && f <= n) return f;
   if (f < 0) {
     if (bc_lo == BC_PERIODIC) { int m = f % n; return m < 0 ? m + n : m; }
-    if (bc_lo == BC_REFLECT) return -f;
+    if (bc_lo == BC_REFLECT || bc_lo == BC_WALL_AFTER) return -f;
     return 0;
   }
   if (bc_hi == BC_PERIODIC) return f % n;
@@ -109,16 +110,45 @@ __device__ __forceinline__ int face_map(int f, int n, int bc_lo, int bc_hi) {
   return n;
 }
 
+// Time of a stage: st->t + tfrac dt (exactly st->t for tfrac = 0)
+__device__ __forceinline__ double stage_time(const DevState* st, double tfrac, double dt) {
+  return tfrac == 0.0 ? st->t : __dadd_rn(st->t, __dmul_rn(tfrac, dt));
+}
+
+// Component c of (ghost) cell (i, j) at time ts (the time-dependent BC_MOVING_SHOCK ghosts).
 __device__ __forceinline__ double fetch_w(const GridInfo& g, const double* __restrict__ W, int c,
-                                          int i, int j) {
+                                          int i, int j, double ts) {
   if (i < 0 && g.bc[0] == BC_INFLOW_BAND && j >= g.band_j0 && j <= g.band_j1) return g.inflow_cons[c];
+  if (j < 0 && g.bc[2] == BC_WALL_AFTER && i < g.wall_i0) return g.inflow_cons[c];
+  if (j >= g.ny && g.bc[3] == BC_MOVING_SHOCK) {
+    // ghost centre against the shock position, each rounded once
+    const double xc = __dadd_rn(g.x0, __dmul_rn((double)i + 0.5, g.dx));
+    const double xs = __dadd_rn(g.shock_x0, __dmul_rn(g.shock_speed, ts));
+    return xc < xs ? g.inflow_cons[c] : g.state_b_cons[c];
+  }
   const int ii = wrap_or_clamp(i, g.nx, g.bc[0], g.bc[1]);
   const int jj = wrap_or_clamp(j, g.ny, g.bc[2], g.bc[3]);
   const double v = __ldg(W + ((size_t)c * g.ny + jj) * g.nx + ii);
   // a reflecting wall flips the momentum normal to it (x-walls: c = 1; y-walls, 2D: c = 2)
   const bool fx = (c == 1) && ((i < 0 && g.bc[0] == BC_REFLECT) || (i >= g.nx && g.bc[1] == BC_REFLECT));
-  const bool fy = (c == 2) && ((j < 0 && g.bc[2] == BC_REFLECT) || (j >= g.ny && g.bc[3] == BC_REFLECT));
+  const bool fy = (c == 2) && ((j < 0 && (g.bc[2] == BC_REFLECT || g.bc[2] == BC_WALL_AFTER)) ||
+                               (j >= g.ny && g.bc[3] == BC_REFLECT));
   return (fx || fy) ? -v : v;
+}
+
+// sigma of x-face f (index before the boundary map) on (ghost) row j; below a
+// BC_WALL_AFTER boundary the rows of x-faces whose right-hand column is before the wall
+// clamp (fixed ghosts), the others mirror
+__device__ __forceinline__ double sigma_x_at(const GridInfo& g, const double* __restrict__ s, int f, int j) {
+  const int jj = (j < 0 && g.bc[2] == BC_WALL_AFTER && f < g.wall_i0) ? 0 : wrap_or_clamp(j, g.ny, g.bc[2], g.bc[3]);
+  return __ldg(s + (size_t)jj * (g.nx + 1) + face_map(f, g.nx, g.bc[0], g.bc[1]));
+}
+
+// sigma of y-face f (index before the boundary map) of (ghost) column i; the fixed part of
+// a BC_WALL_AFTER boundary clamps, its wall part mirrors
+__device__ __forceinline__ double sigma_y_at(const GridInfo& g, const double* __restrict__ s, int f, int i) {
+  const int ff = (f < 0 && g.bc[2] == BC_WALL_AFTER && i < g.wall_i0) ? 0 : face_map(f, g.ny, g.bc[2], g.bc[3]);
+  return __ldg(s + (size_t)ff * g.nx + wrap_or_clamp(i, g.nx, g.bc[0], g.bc[1]));
 }
 
 // Local Lax-Friedrichs flux (Sec. 2.3) and discontinuity strength sigma (Sec. 3.1) of

@@ -436,9 +436,8 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
   const int mlin = (DIR == 0) ? g.ny : g.nx;
   const int a0 = blockIdx.x * TN, b0 = blockIdx.y * TT;
   const int tid = threadIdx.x;
-  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
-  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
   const double dt = args.dt_fixed > 0.0 ? args.dt_fixed : args.st->dt;
+  const double ts = stage_time(args.st, args.tfrac, dt);  // for time-dependent ghosts
   const double idt = 1.0 / dt;
   // internal degrees of freedom K (Sec. 2.2) and 4 / (K + DIM) of the slope solves
   const double Kdof = (DIM == 2) ? (4.0 - 2.0 * g.gamma) / (g.gamma - 1.0) : (3.0 - g.gamma) / (g.gamma - 1.0);
@@ -450,20 +449,18 @@ gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constan
     else { bb = idx % NB; ai = (idx / NB) % NA; c = idx / (NA * NB); }
     const int a = a0 - 1 - K + ai, b = b0 - KT + bb;
     const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
-    sW[(c * NB + bb) * NA + ai] = fetch_w(g, args.W, c, i, j);
+    sW[(c * NB + bb) * NA + ai] = fetch_w(g, args.W, c, i, j, ts);
   }
   for (int idx = tid; idx < NB * NSN; idx += NT) {
     const int fa = idx % NSN, bb = idx / NSN;
-    const int f = face_map(a0 - K + fa, n, bcn_lo, bcn_hi);
-    const int b = wrap_or_clamp(b0 - KT + bb, mlin, bct_lo, bct_hi);
-    sSn[bb * NSN + fa] = (DIR == 0) ? args.s_norm[(size_t)b * (g.nx + 1) + f] : args.s_norm[(size_t)f * g.nx + b];
+    sSn[bb * NSN + fa] = (DIR == 0) ? sigma_x_at(g, args.s_norm, a0 - K + fa, b0 - KT + bb)
+                                    : sigma_y_at(g, args.s_norm, a0 - K + fa, b0 - KT + bb);
   }
   if (DIM == 2) {
     for (int idx = tid; idx < NQ * (NST - 1); idx += NT) {
       const int qa = idx % NQ, fb = idx / NQ;
-      const int a = wrap_or_clamp(a0 - 1 + qa, n, bcn_lo, bcn_hi);
-      const int f = face_map(b0 - K + 1 + fb, mlin, bct_lo, bct_hi);
-      sSt[qa * NST + fb] = (DIR == 0) ? args.s_tan[(size_t)f * g.nx + a] : args.s_tan[(size_t)a * (g.nx + 1) + f];
+      sSt[qa * NST + fb] = (DIR == 0) ? sigma_y_at(g, args.s_tan, b0 - K + 1 + fb, a0 - 1 + qa)
+                                      : sigma_x_at(g, args.s_tan, b0 - K + 1 + fb, a0 - 1 + qa);
     }
   }
   __syncthreads();

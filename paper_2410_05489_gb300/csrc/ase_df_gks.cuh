@@ -19,6 +19,7 @@ struct GksSweepArgs {
   double dt_fixed;        // > 0: the step's dt
   double inv_dn, inv_dt;  // 1/h along the sweep and across it
   double c1, c2;          // tau_n = c1 dt + c2 |p_l - p_r| / (p_l + p_r) dt
+  double tfrac = 0.0;     // the stage's time is st->t + tfrac dt (time-dependent ghosts)
 };
 
 struct GksCombineArgs {

@@ -66,7 +66,7 @@ struct DevState {
   unsigned long long frozen_total;    // cells left without a flux update (last resort)
 };
 
-enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2, BC_REFLECT = 3 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2, BC_REFLECT = 3, BC_WALL_AFTER = 4, BC_MOVING_SHOCK = 5 };
 
 // Grid and boundary description handed to the kernels.
 struct GridInfo {
@@ -76,6 +76,12 @@ struct GridInfo {
   double inflow_cons[4];
   double gamma;
   double thres;
+  // BC_WALL_AFTER (y-lo): columns i < wall_i0 (centre x below wall_x) have fixed ghosts
+  int wall_i0 = 0;
+  // BC_MOVING_SHOCK (y-hi): ghost centre x0 + (i + 1/2) dx below shock_x0 + shock_speed t
+  // takes inflow_cons, otherwise state_b_cons
+  double x0 = 0.0, dx = 0.0, shock_x0 = 0.0, shock_speed = 0.0;
+  double state_b_cons[4] = {0.0, 0.0, 0.0, 0.0};
 };
 
 struct SweepArgs {
@@ -85,6 +91,7 @@ struct SweepArgs {
   double* F;              // face fluxes of this direction
   double* s_out;          // sigma_out of this direction
   DevState* st;
+  double tfrac = 0.0;     // the stage's time is st->t + tfrac st->dt (time-dependent ghosts)
 };
 
 struct CombineArgs {
@@ -115,6 +122,7 @@ struct RepairArgs {
   double dt_fixed;
   int stage;
   int pass;           // 1..kRepairPasses
+  double tfrac = 0.0; // the stage's time is st->t + tfrac dt (time-dependent ghosts)
 };
 
 struct SpeedArgs {

@@ -238,9 +238,8 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   const int n = (DIR == 0) ? g.nx : g.ny;       // cells along the sweep
   const int mlin = (DIR == 0) ? g.ny : g.nx;    // lines
   const int tid = threadIdx.x;
-  const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
-  const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
 
+  const double ts = stage_time(args.st, args.tfrac, args.st->dt);  // for time-dependent ghosts
   // ---- stage cell averages: cells a0-1-K .. a0+TN-1+K, lines b0-KT .. b0+TT+KT-1 ----
   for (int idx = tid; idx < C * NB * NA; idx += NT) {
     int c, bb, aa;
@@ -248,17 +247,15 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
     else { bb = idx % NB; aa = (idx / NB) % NA; c = idx / (NA * NB); }
     const int a = a0 - 1 - K + aa, b = b0 - KT + bb;
     const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
-    sW[(c * NB + bb) * NA + aa] = fetch_w(g, args.W, c, i, j);
+    sW[(c * NB + bb) * NA + aa] = fetch_w(g, args.W, c, i, j, ts);
   }
   // ---- normal face strengths: faces a0-K .. a0+TN-1+K of every staged line ----
   for (int idx = tid; idx < NB * NSN; idx += NT) {
     int fa, bb;
     if (DIR == 0) { fa = idx % NSN; bb = idx / NSN; }
     else { bb = idx % NB; fa = idx / NB; }
-    const int f = face_map(a0 - K + fa, n, bcn_lo, bcn_hi);
-    const int b = wrap_or_clamp(b0 - KT + bb, mlin, bct_lo, bct_hi);
-    sSn[bb * NSN + fa] = (DIR == 0) ? __ldg(args.s_norm + (size_t)b * (g.nx + 1) + f)
-                                    : __ldg(args.s_norm + (size_t)f * g.nx + b);
+    sSn[bb * NSN + fa] = (DIR == 0) ? sigma_x_at(g, args.s_norm, a0 - K + fa, b0 - KT + bb)
+                                    : sigma_y_at(g, args.s_norm, a0 - K + fa, b0 - KT + bb);
   }
   // ---- tangential face strengths of the reconstructing cells' columns ----
   if (DIM == 2) {
@@ -266,10 +263,8 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
       int qa, fb;
       if (DIR == 0) { qa = idx % NQ; fb = idx / NQ; }
       else { fb = idx % (NST - 1); qa = idx / (NST - 1); }
-      const int a = wrap_or_clamp(a0 - 1 + qa, n, bcn_lo, bcn_hi);
-      const int f = face_map(b0 - K + 1 + fb, mlin, bct_lo, bct_hi);
-      sSt[qa * NST + fb] = (DIR == 0) ? __ldg(args.s_tan + (size_t)f * g.nx + a)
-                                      : __ldg(args.s_tan + (size_t)a * (g.nx + 1) + f);
+      sSt[qa * NST + fb] = (DIR == 0) ? sigma_y_at(g, args.s_tan, b0 - K + 1 + fb, a0 - 1 + qa)
+                                      : sigma_x_at(g, args.s_tan, b0 - K + 1 + fb, a0 - 1 + qa);
     }
   }
   __syncthreads();

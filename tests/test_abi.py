@@ -47,7 +47,9 @@ def test_params_struct_layout_matches_header():
     assert ase_df_params.inflow_state.offset == 96
     assert ase_df_params.t_end.offset == 144
     assert ase_df_params.gks_c1.offset == 152 and ase_df_params.gks_c2.offset == 160
-    assert ctypes.sizeof(ase_df_params) == 168
+    assert ase_df_params.state_b.offset == 168 and ase_df_params.wall_x.offset == 200
+    assert ase_df_params.shock_x0.offset == 208 and ase_df_params.shock_speed.offset == 216
+    assert ctypes.sizeof(ase_df_params) == 224
 
 
 def test_init_rejects_bad_parameters_without_a_device(lib):
@@ -69,3 +71,18 @@ def test_init_rejects_bad_parameters_without_a_device(lib):
     with pytest.raises(A.AseDfError) as ei:
         A.ase_df_init(A.params_from_problem(pb))
     assert ei.value.status == 6
+    # the double Mach reflection boundaries: the split wall on y-lo and the moving shock on
+    # y-hi of a 2D grid only, with physical states and finite positions
+    good = dict(ndim=2, nx=16, ny=8, order=5, bc=("inflow", "outflow", "wall_after", "moving_shock"),
+                inflow=(8.0, 7.1, -4.1, 116.0), inflow_lo=-1.0, inflow_hi=2.0, state_b=(1.4, 0.0, 0.0, 1.0),
+                wall_x=0.2, shock_x0=0.5, shock_speed=11.0)
+    for bad in (dict(bc=("wall_after", "outflow", "outflow", "outflow")),
+                dict(bc=("outflow", "outflow", "moving_shock", "outflow")),
+                dict(ndim=1, bc=("outflow", "outflow", "wall_after", "outflow")),
+                dict(state_b=(1.4, 0.0, 0.0, -1.0)), dict(inflow=(0.0, 0.0, 0.0, 1.0)),
+                dict(wall_x=float("nan")), dict(shock_speed=float("inf")), dict(ny=2, order=9)):
+        kw = dict(good)
+        kw.update(bad)
+        with pytest.raises(A.AseDfError) as ei:
+            A.ase_df_init(A.params_from_problem(Problem(**kw)))
+        assert ei.value.status == 1
