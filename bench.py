@@ -41,7 +41,7 @@ HBM_BYTES_PER_CELL_STAGE_2D = 128.0  # read W^(s), W^n, write W^(s+1), sigma in/
 # DRAM bytes (read + write) per sweep launch measured by ncu on this kernel for the 1024^2,
 # order-9 workload (mean of the x- and y-face launches; profiles/sweep_kernel_r9_2d_vortex1024_ncu.md).
 # Reported as roofline.traffic for that workload only (null for other sizes / orders).
-SWEEP_DRAM_BYTES_1024_R9 = None
+SWEEP_DRAM_BYTES_1024_R9 = 58.19e6
 
 
 def algorithmic_flops_per_face(ndim: int, r: int) -> float:

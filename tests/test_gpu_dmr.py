@@ -147,3 +147,20 @@ def test_gas_kinetic_run_matches_the_oracle(A, oracle):
     assert abs(t - 0.03) < 1e-12 and flags & 1 == 0
     Wc, *_ = oracle.gks_run(pb, W0, t_end=0.03)
     assert np.abs(W[0] - Wc[0]).mean() <= 1e-6 * np.abs(Wc[0]).mean()
+
+
+@pytest.mark.parametrize("gks", [False, True])
+def test_paper_resolution_run_stays_physical(A, gks):
+    """960 x 240 at order 9 to t = 0.2 (the paper's figure): no non-physical cell average,
+    density within the physical range of the problem, and the incident shock in the top rows
+    at the exact position x = 1/6 + (y + 20 t) / sqrt(3) within two cells."""
+    pb, W0 = P.double_mach_reflection(960, 9)
+    W, flags, t = run_gpu(A, pb, W0, 0.2, gks=gks)
+    assert abs(t - 0.2) < 1e-12 and flags & 1 == 0
+    rho = W[0]
+    assert rho.min() > 1.3 and rho.max() < 30.0
+    xs = pb.x0 + (np.arange(pb.nx) + 0.5) * pb.dx
+    for j in (pb.ny - 1, pb.ny - 5):
+        y = pb.y0 + (j + 0.5) * pb.dy
+        k = int(np.argmax((rho[j] < 4.7) & (xs > 2.0)))
+        assert abs(xs[k] - (1.0 / 6.0 + (y + 20.0 * t) / np.sqrt(3.0))) <= 2 * pb.dx
