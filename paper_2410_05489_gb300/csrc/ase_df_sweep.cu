@@ -27,22 +27,23 @@
 namespace asedf {
 namespace {
 
-template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(Tile<R, DIM>::NT, 2)
+template <int R, int DIM, int DIR, int TT>
+__global__ void __launch_bounds__(Tile<R, DIM, TT>::NT, 2)
 sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tables T) {
   extern __shared__ double smem[];
   if (DIR == 0 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x <= kRepairPasses) {
     args.st->cnt[threadIdx.x] = 0u;  // counters of the positivity repair of this stage
     args.st->rbad[threadIdx.x] = 0u;
   }
-  sweep_tile<R, DIM, DIR>(g, args, T, blockIdx.x * Tile<R, DIM>::TN, blockIdx.y * Tile<R, DIM>::TT, smem);
+  sweep_tile<R, DIM, DIR, TT>(g, args, T, blockIdx.x * Tile<R, DIM, TT>::TN, blockIdx.y * Tile<R, DIM, TT>::TT,
+                              smem);
 }
 
-template <int R, int DIM, int DIR>
-cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s) {
-  using TL = Tile<R, DIM>;
+template <int R, int DIM, int DIR, int TT>
+cudaError_t launch_tt(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s) {
+  using TL = Tile<R, DIM, TT>;
   const size_t smem = TL::smem_doubles * sizeof(double);
-  auto kern = sweep_kernel<R, DIM, DIR>;
+  auto kern = sweep_kernel<R, DIM, DIR, TT>;
   static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -54,6 +55,37 @@ cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaS
   dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
   kern<<<grid, TL::NT, smem, s>>>(g, a, t);
   return cudaGetLastError();
+}
+
+// Fraction of the CTA slots (two per SM) that a grid of `tiles` CTAs keeps busy over its waves.
+double wave_fill(long long tiles, int slots) {
+  const long long waves = (tiles + slots - 1) / slots;
+  return waves > 0 ? (double)tiles / (double)(waves * slots) : 0.0;
+}
+
+// 2D: tiles of 8 x 64 faces (two per thread) where they fill the GPU's waves, else 8 x 32
+// (one face per thread: twice the CTAs for small and medium grids; ~1 % more work per face
+// from the larger share of halo lines, hence the margin).
+template <int R, int DIM, int DIR>
+cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s) {
+  if constexpr (DIM == 1) {
+    return launch_tt<R, DIM, DIR, 1>(g, a, t, s);
+  } else {
+  static int slots = 0;
+  if (slots == 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 152;
+    slots = 2 * sms;
+  }
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int m = (DIR == 0) ? g.ny : g.nx;
+  const long long cols = (n + 1 + 7) / 8;
+  const double f64 = wave_fill(cols * ((m + 63) / 64), slots);
+  const double f32 = wave_fill(cols * ((m + 31) / 32), slots);
+  if (f32 > 1.02 * f64) return launch_tt<R, DIM, DIR, 32>(g, a, t, s);
+  return launch_tt<R, DIM, DIR, 64>(g, a, t, s);
+  }
 }
 
 }  // namespace

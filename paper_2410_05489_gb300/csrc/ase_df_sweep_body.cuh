@@ -219,10 +219,10 @@ struct Tile {
 
 // One tile: faces a0 .. a0+TN-1 along the sweep on lines b0 .. b0+TT-1 (threadIdx.x in
 // [0, TN*TT/..) is the worker index); smem holds Tile<R, DIM>::smem_doubles doubles.
-template <int R, int DIM, int DIR>
+template <int R, int DIM, int DIR, int TT_ = (DIM == 2) ? 64 : 1>
 __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& args, const Tables& T, int a0,
                                            int b0, double* smem) {
-  using TL = Tile<R, DIM>;
+  using TL = Tile<R, DIM, TT_>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
   constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
   constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
