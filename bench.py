@@ -42,6 +42,9 @@ HBM_BYTES_PER_CELL_STAGE_2D = 128.0  # read W^(s), W^n, write W^(s+1), sigma in/
 # order-9 workload (mean of the x- and y-face launches; profiles/sweep_kernel_r9_2d_vortex1024_ncu.md).
 # Reported as roofline.traffic for that workload only (null for other sizes / orders).
 SWEEP_DRAM_BYTES_1024_R9 = 58.19e6
+# FP64 pipe active (of active cycles) of the same captures (ncu --set full, the x- and y-face
+# launches): sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active, mean of the two.
+SWEEP_FP64_PIPE_ACTIVE_1024_R9 = 0.8455
 
 
 def algorithmic_flops_per_face(ndim: int, r: int) -> float:
@@ -324,6 +327,7 @@ def run_ours(args, world, rank, local):
             "unit": "TFLOP/s",
             "frac": round(achieved / peak_tflops, 4),
             "traffic": SWEEP_DRAM_BYTES_1024_R9 if (args.n, args.order) == (1024, 9) else None,
+            "ncu_fp64_pipe_active": SWEEP_FP64_PIPE_ACTIVE_1024_R9 if (args.n, args.order) == (1024, 9) else None,
             "traffic_unit": "bytes per sweep launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "peak_source": "2 FP64 FMA/cycle/SM (ncu DFMA peak_sustained) x %d SMs x %.0f MHz (median sampled "
                            "SM clock in the timed region) x 2 flops" % (n_sm, clk_mhz),
