@@ -405,6 +405,7 @@ def batched_bench(A, torch, args):
         "step_tflops": round(step_flops / (ms_b * 1e-3) / 1e12, 4),
         "step_frac_of_fp64_peak": round(step_flops / (ms_b * 1e-3) / 1e12 / fp64_peak_tflops(torch), 4),
         "schedule": tune.get("schedule"),
+        "tiles_2d_lines_by_order": tune.get("tiles"),
         "nonphysical_problems": int(((flags & 1) != 0).sum()),
     }
 

@@ -307,6 +307,11 @@ ase_df_status ase_df_batch_get_status(ase_df_batch* b, uint32_t* flags, double* 
 ase_df_status ase_df_batch_set_schedule(ase_df_batch* b, int32_t ctas_per_sm, int32_t order_by_cost,
                                         int32_t chunk_cells);
 
+/* Tile shape of the 2D sweeps per scheme order: lines[k] (k = 0..3 for orders 3, 5, 7, 9) is
+ * 64 (tiles of 8 x 64 faces, two faces per thread) or 32 (8 x 32, one face per thread).
+ * Chosen by the autotuner of the Python package; results do not depend on it. */
+ase_df_status ase_df_batch_set_tiles(ase_df_batch* b, const int32_t* lines);
+
 /* Message of the last error on this batch (or of the last failed ase_df_batch_init when
  * b is NULL). */
 const char* ase_df_batch_last_error(const ase_df_batch* b);

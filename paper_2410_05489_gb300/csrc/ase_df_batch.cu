@@ -72,11 +72,20 @@ __device__ __forceinline__ StagePtrs stage_ptrs(const BatchPtrs& P, const BatchP
 
 constexpr int kNT = 256;
 
-// One out-of-line copy per variant, so that each gets its own register allocation.
-template <int R, int DIM, int DIR>
+// One out-of-line copy per variant (order, dimension, direction, tile lines), so that each
+// gets its own register allocation.
+template <int R, int DIM, int DIR, int TT = (DIM == 2) ? 64 : 1>
 __device__ __noinline__ void tile_call(const GridInfo& g, const SweepArgs& a, const Tables& T, int a0, int b0,
                                        double* smem) {
-  sweep_tile<R, DIM, DIR>(g, a, T, a0, b0, smem);
+  sweep_tile<R, DIM, DIR, TT>(g, a, T, a0, b0, smem);
+}
+
+// 2D tile of 8 faces x tt lines (64: two faces per thread, 32: one)
+template <int R, int DIR>
+__device__ __forceinline__ void tile_call_2d(int tt, const GridInfo& g, const SweepArgs& a, const Tables& T, int a0,
+                                             int b0, double* smem) {
+  if (tt == 32) tile_call<R, 2, DIR, 32>(g, a, T, a0, b0, smem);
+  else tile_call<R, 2, DIR, 64>(g, a, T, a0, b0, smem);
 }
 
 template <int DIR>
@@ -95,7 +104,7 @@ batch_sweep_kernel(const BatchProblem* __restrict__ probs, const int4* __restric
     __syncthreads();
     const int it = s_item;
     if (it >= nitems) break;
-    const int4 w = items[it];  // problem, a0, b0
+    const int4 w = items[it];  // problem, a0, b0, lines of a 2D tile
     const BatchProblem& pb = probs[w.x];
     const int variant = pb.variant;
     if (variant != s_variant) {  // stage this order's tables in shared memory
@@ -125,17 +134,17 @@ batch_sweep_kernel(const BatchProblem* __restrict__ probs, const int4* __restric
         case 1: tile_call<5, 1, 0>(g, a, sT, w.y, w.z, smem); break;
         case 2: tile_call<7, 1, 0>(g, a, sT, w.y, w.z, smem); break;
         case 3: tile_call<9, 1, 0>(g, a, sT, w.y, w.z, smem); break;
-        case 4: tile_call<3, 2, 0>(g, a, sT, w.y, w.z, smem); break;
-        case 5: tile_call<5, 2, 0>(g, a, sT, w.y, w.z, smem); break;
-        case 6: tile_call<7, 2, 0>(g, a, sT, w.y, w.z, smem); break;
-        default: tile_call<9, 2, 0>(g, a, sT, w.y, w.z, smem); break;
+        case 4: tile_call_2d<3, 0>(w.w, g, a, sT, w.y, w.z, smem); break;
+        case 5: tile_call_2d<5, 0>(w.w, g, a, sT, w.y, w.z, smem); break;
+        case 6: tile_call_2d<7, 0>(w.w, g, a, sT, w.y, w.z, smem); break;
+        default: tile_call_2d<9, 0>(w.w, g, a, sT, w.y, w.z, smem); break;
       }
     } else {
       switch (variant) {
-        case 4: tile_call<3, 2, 1>(g, a, sT, w.y, w.z, smem); break;
-        case 5: tile_call<5, 2, 1>(g, a, sT, w.y, w.z, smem); break;
-        case 6: tile_call<7, 2, 1>(g, a, sT, w.y, w.z, smem); break;
-        default: tile_call<9, 2, 1>(g, a, sT, w.y, w.z, smem); break;
+        case 4: tile_call_2d<3, 1>(w.w, g, a, sT, w.y, w.z, smem); break;
+        case 5: tile_call_2d<5, 1>(w.w, g, a, sT, w.y, w.z, smem); break;
+        case 6: tile_call_2d<7, 1>(w.w, g, a, sT, w.y, w.z, smem); break;
+        default: tile_call_2d<9, 1>(w.w, g, a, sT, w.y, w.z, smem); break;
       }
     }
   }
@@ -266,6 +275,7 @@ struct ase_df_batch {
   size_t smem_bytes = 0;
   // schedule
   int ctas_per_sm = 2, order_by_cost = 1, chunk_cells = 16384;
+  int tile_lines[4] = {64, 64, 64, 64};  // lines of the 2D tiles of orders 3, 5, 7, 9
   // graph of one step
   cudaGraphExec_t graph = nullptr;
   double *g_W = nullptr, *g_sx = nullptr, *g_sy = nullptr;
@@ -384,16 +394,16 @@ static void build_items(ase_df_batch* b) {
         wx.push_back({fc * nf, make_int4(i, (int)a0, 0, 0)});
       }
     } else {
-      const int TN = Tile<3, 2>::TN, TT = Tile<3, 2>::TT;
+      const int TN = Tile<3, 2>::TN, TT = b->tile_lines[(p.order - 3) / 2];
       for (long long b0 = 0; b0 < p.ny; b0 += TT)
         for (long long a0 = 0; a0 <= p.nx; a0 += TN) {
           const long long nf = std::min<long long>(TN, p.nx + 1 - a0) * std::min<long long>(TT, p.ny - b0);
-          wx.push_back({fc * nf, make_int4(i, (int)a0, (int)b0, 0)});
+          wx.push_back({fc * nf, make_int4(i, (int)a0, (int)b0, TT)});
         }
       for (long long b0 = 0; b0 < p.nx; b0 += TT)
         for (long long a0 = 0; a0 <= p.ny; a0 += TN) {
           const long long nf = std::min<long long>(TN, p.ny + 1 - a0) * std::min<long long>(TT, p.nx - b0);
-          wy.push_back({fc * nf, make_int4(i, (int)a0, (int)b0, 0)});
+          wy.push_back({fc * nf, make_int4(i, (int)a0, (int)b0, TT)});
         }
     }
   }
@@ -726,6 +736,20 @@ ase_df_status ase_df_batch_set_schedule(ase_df_batch* b, int32_t ctas_per_sm, in
     b->graph = nullptr;
   }
   return ASE_DF_OK;
+}
+
+ase_df_status ase_df_batch_set_tiles(ase_df_batch* b, const int32_t* lines) {
+  if (!b || !lines) return ASE_DF_E_INVAL;
+  for (int k = 0; k < 4; ++k)
+    if (lines[k] != 32 && lines[k] != 64) return bfail(b, ASE_DF_E_INVAL, "tile lines must be 32 or 64");
+  bool changed = false;
+  for (int k = 0; k < 4; ++k) {
+    changed |= b->tile_lines[k] != lines[k];
+    b->tile_lines[k] = lines[k];
+  }
+  if (!changed) return ASE_DF_OK;
+  cudaDeviceSynchronize();
+  return upload_schedule(b);
 }
 
 }  // extern "C"

@@ -77,13 +77,17 @@ def test_batch_matches_oracle(B, oracle):
 
 
 def test_schedules_do_not_change_results(B):
+    """Schedules and 2D tile shapes (8 x 64 or 8 x 32 faces per tile, per order) change the
+    work assignment only: the results are the same bit for bit."""
     A, Bt = B
     probs = mixed_set()
     ref = None
-    for sched in ((2, True, 4096), (1, False, 65536), (2, False, 256)):
+    for sched, tiles in (((2, True, 4096), (64, 64, 64, 64)), ((1, False, 65536), (32, 32, 32, 32)),
+                         ((2, False, 256), (32, 64, 32, 64))):
         bt = Bt.Batch([p for p, _ in probs], [w for _, w in probs])
         try:
             bt.set_schedule(*sched)
+            bt.set_tiles(tiles)
             for _ in range(2):
                 bt.step()
             got = bt.W.cpu().numpy()
@@ -104,8 +108,10 @@ def test_autotune_restores_state_and_caches(B, tmp_path):
         cache = str(tmp_path / "sched.json")
         entry = Bt.autotune(bt, steps=1, cache=cache, candidates=[(2, True, 16384), (1, True, 4096)])
         assert len(entry["ms_per_step"]) == 2
+        assert len(entry["tiles_ms_per_step"]) == 4  # orders 3, 5, 7, 9 all have 2D problems here
+        assert all(v in (32, 64) for v in entry["tiles"])
         assert bool((bt.W == W0).all())
         again = Bt.autotune(bt, steps=1, cache=cache)
-        assert again["schedule"] == entry["schedule"]
+        assert again["schedule"] == entry["schedule"] and again["tiles"] == entry["tiles"]
     finally:
         bt.close()
