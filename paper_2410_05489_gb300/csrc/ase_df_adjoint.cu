@@ -233,20 +233,26 @@ __device__ __forceinline__ void sigma_vjp(const Branch& br, const double* ab, do
 // ---------------------------------------------------------------------------------
 // Lax-Friedrichs point VJP (the derivative of lf_point)
 // ---------------------------------------------------------------------------------
+// Primitives of one side with 1/rho and 1/c: FP64 division and square root take 6-9 FMA
+// issue slots on this part, so they come from the seeded reciprocal and reciprocal square
+// root of the forward flux (rcp_pos, rsqrt_pos) and the VJP multiplies by them.
 struct SidePrim {
-  double rho, u, w, p, c, E;
+  double rho, u, w, p, c, E, ir, ic;  // ir = 1 / rho, ic = 1 / c
 };
 
 template <int C, int NI, int TI>
 __device__ __forceinline__ SidePrim side_prim(const double* q, double gamma) {
   SidePrim s;
   s.rho = q[0];
-  const double ir = 1.0 / q[0];
+  const double ir = rcp_pos(q[0]);
+  s.ir = ir;
   s.u = q[NI] * ir;
   s.w = (C == 4) ? q[TI] * ir : 0.0;
   s.E = q[C - 1];
   s.p = (gamma - 1.0) * (s.E - 0.5 * q[0] * (s.u * s.u + s.w * s.w));
-  s.c = sqrt(gamma * s.p * ir);
+  const double c2 = gamma * s.p * ir;
+  s.ic = rsqrt_pos(c2);
+  s.c = c2 * s.ic;
   return s;
 }
 
@@ -256,8 +262,8 @@ __device__ __forceinline__ SidePrim side_prim(const double* q, double gamma) {
 template <int C, int NI, int TI>
 __device__ __forceinline__ void side_back(const SidePrim& s, double gamma, double ub, double wb, double pb,
                                           double cb, double* qb) {
-  const double ir = 1.0 / s.rho;
-  pb += cb * gamma * ir / (2.0 * s.c);
+  const double ir = s.ir;
+  pb += cb * gamma * ir * (0.5 * s.ic);
   double rb = -cb * s.c * 0.5 * ir;
   const double g1 = gamma - 1.0;
   qb[C - 1] += g1 * pb;
@@ -340,20 +346,21 @@ __device__ void lf_point_vjp(const double* qa, const double* qb_, const double* 
     const double dp = L.p - R.p;
     const double sg = dabs(dp, L.p + R.p);
     const double adp = fabs(dp);
-    const double h = 1.0 / L.p + 1.0 / R.p;
-    pLb += sb * (sg * h - adp / (L.p * L.p));
-    pRb += sb * (-sg * h - adp / (R.p * R.p));
-    const double dmn = L.u / L.c - R.u / R.c;
-    uLb += sb * 2.0 * dmn / L.c;
-    uRb -= sb * 2.0 * dmn / R.c;
-    cLb -= sb * 2.0 * dmn * L.u / (L.c * L.c);
-    cRb += sb * 2.0 * dmn * R.u / (R.c * R.c);
+    const double ipL = rcp_pos(L.p), ipR = rcp_pos(R.p);
+    const double h = ipL + ipR;
+    pLb += sb * (sg * h - adp * (ipL * ipL));
+    pRb += sb * (-sg * h - adp * (ipR * ipR));
+    const double dmn = L.u * L.ic - R.u * R.ic;
+    uLb += sb * 2.0 * dmn * L.ic;
+    uRb -= sb * 2.0 * dmn * R.ic;
+    cLb -= sb * 2.0 * dmn * L.u * (L.ic * L.ic);
+    cRb += sb * 2.0 * dmn * R.u * (R.ic * R.ic);
     if (C == 4) {
-      const double dmt = L.w / L.c - R.w / R.c;
-      wLb += sb * 2.0 * dmt / L.c;
-      wRb -= sb * 2.0 * dmt / R.c;
-      cLb -= sb * 2.0 * dmt * L.w / (L.c * L.c);
-      cRb += sb * 2.0 * dmt * R.w / (R.c * R.c);
+      const double dmt = L.w * L.ic - R.w * R.ic;
+      wLb += sb * 2.0 * dmt * L.ic;
+      wRb -= sb * 2.0 * dmt * R.ic;
+      cLb -= sb * 2.0 * dmt * L.w * (L.ic * L.ic);
+      cRb += sb * 2.0 * dmt * R.w * (R.ic * R.ic);
     }
   }
   side_back<C, NI, TI>(L, gamma, uLb, wLb, pLb, cLb, ab_);
