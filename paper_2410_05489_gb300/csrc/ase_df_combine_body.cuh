@@ -29,13 +29,20 @@ __device__ __forceinline__ double flux_div(double dFx, double inv_dx, double dFy
   return -__dadd_rn(__dmul_rn(dFx, inv_dx), __dmul_rn(dFy, inv_dy));
 }
 
-// rho > 0 and p > 0 (tested on p rho = (gamma-1)(E rho - |m|^2/2)), all finite.
+// rho > 0 and p > 0 (tested on p rho = (gamma-1)(E rho - |m|^2/2)), all finite; the
+// comparisons run on the bit patterns (pos_finite), which decide exactly as
+// (rho > 0) && (p rho > 0) && isfinite(p rho) (an infinite rho makes p rho non-finite).
 template <int C>
 __device__ __forceinline__ bool physical_state(const double* q, double gamma) {
   double mm = q[1] * q[1];
   if (C == 4) mm = fma(q[2], q[2], mm);
   const double pr = (gamma - 1.0) * fma(q[C - 1], q[0], -0.5 * mm);
-  return (q[0] > 0.0) && (pr > 0.0) && isfinite(pr);
+  return pos_finite(q[0]) && pos_finite(pr);
+}
+
+// isfinite on the bit pattern (exponent field not all ones)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (dbits(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }
 
 // Cells n = first, first + stride, ... < last of one problem; `leader` is true for
@@ -80,7 +87,7 @@ __device__ __forceinline__ void combine_range(const GridInfo& g, const CombineAr
       const size_t w = (size_t)c * ncell + n;
       q[c] = (a.stage == 0) ? L : rk_stage(a.stage, dt, a.Wn[w], a.Ws[w], L);
       a.out[w] = q[c];
-      if (!isfinite(q[c])) bad = true;
+      if (!finite_bits(q[c])) bad = true;
     }
     if (a.stage > 0) {
       const bool ok = physical_state<C>(q, g.gamma);
