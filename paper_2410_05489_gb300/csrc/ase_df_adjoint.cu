@@ -825,11 +825,10 @@ cudaError_t adj_launch(const GridInfo& g, const SweepArgs& a, const AdjArgs& aa,
   using TL = AdjTile<R, DIM>;
   const size_t smem = TL::smem_doubles * sizeof(double);
   auto k1 = adj_face_kernel<R, DIM, DIR>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> attr_done{0ull};
+  {
+    cudaError_t e = ensure_smem_limit(k1, smem, attr_done);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int m = (DIR == 0) ? g.ny : g.nx;

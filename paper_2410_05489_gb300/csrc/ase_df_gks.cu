@@ -595,11 +595,10 @@ cudaError_t gks_launch(const GridInfo& g, const GksSweepArgs& a, const Tables& t
   using TL = GksTileShape<R, DIM>;
   const size_t smem = GksTile<R, DIM>::smem_doubles * sizeof(double);
   auto k = gks_sweep_kernel<R, DIM, DIR>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> attr_done{0ull};
+  {
+    cudaError_t e = ensure_smem_limit(k, smem, attr_done);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int m = (DIR == 0) ? g.ny : g.nx;

@@ -7,10 +7,41 @@
 // flux difference (Sec. 2.1, Eq. 2.3) and SSP-RK3 (Sec. 2.3).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace asedf {
+
+// Raises a kernel's dynamic shared-memory limit once per device (the attribute belongs to
+// the function on the current device): `done` holds one bit per device ordinal (< 64) for
+// which it is set.  Safe to call from several host threads.
+template <typename Kernel>
+inline cudaError_t ensure_smem_limit(Kernel kern, size_t bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit != 0ull && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && bit != 0ull) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
+// Streaming multiprocessors of the current device (cached per device ordinal < 64).
+inline int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
+  if (dev < 64) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
 
 // Evaluation points of a reconstruction polynomial on its cell [-1, 0]:
 //   0: xi = 0 (the "plus" face), 1: xi = -1 (the "minus" face), 2..: Gauss points.

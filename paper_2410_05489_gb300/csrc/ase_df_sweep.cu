@@ -44,12 +44,9 @@ cudaError_t launch_tt(const GridInfo& g, const SweepArgs& a, const Tables& t, cu
   using TL = Tile<R, DIM, TT>;
   const size_t smem = TL::smem_doubles * sizeof(double);
   auto kern = sweep_kernel<R, DIM, DIR, TT>;
-  static bool attr_set = false;  // per process; the attribute is per function
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done{0ull};
+  cudaError_t e = ensure_smem_limit(kern, smem, attr_done);
+  if (e != cudaSuccess) return e;
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int m = (DIR == 0) ? g.ny : g.nx;
   dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
@@ -71,13 +68,7 @@ cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaS
   if constexpr (DIM == 1) {
     return launch_tt<R, DIM, DIR, 1>(g, a, t, s);
   } else {
-  static int slots = 0;
-  if (slots == 0) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 152;
-    slots = 2 * sms;
-  }
+  const int slots = 2 * device_sm_count();
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int m = (DIR == 0) ? g.ny : g.nx;
   const long long cols = (n + 1 + 7) / 8;
