@@ -27,6 +27,10 @@ def mixed_set():
            P.riemann_2d(20, 3, 5, ny=50), P.riemann_1d(129, 7, 6)]
     pb, W = P.sin_wave_2d(24, 9)
     out.append((pb, W))
+    # reflecting walls: the 1D blast wave and a 2D Riemann problem in a closed box
+    out.append(P.blast_wave(160, 5))
+    pb, W = P.riemann_2d(26, 9, 8, ny=21)
+    out.append((pb.replace(bc=("reflect",) * 4), W))
     return out
 
 
