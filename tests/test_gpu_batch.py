@@ -119,3 +119,38 @@ def test_autotune_restores_state_and_caches(B, tmp_path):
         assert again["schedule"] == entry["schedule"] and again["tiles"] == entry["tiles"]
     finally:
         bt.close()
+
+
+def test_full_batched_workload_sampled_problems(B, oracle):
+    """The batched workload at its full size (512 problems, 18.0 M cells), as the benchmark
+    runs it (graph replays): the smallest 1D and 2D problems against the oracle (1e-9, the
+    step tolerance of the parity tests) and a spread of the others, the largest included,
+    against the one-problem path (1e-13)."""
+    A, Bt = B
+    probs = P.batched_problems()
+    bt = Bt.Batch([p for p, _ in probs], [w for _, w in probs])
+    try:
+        bt.set_schedule(2, True, 4096)
+        bt.run(2)
+        flags, t, _ = bt.status()
+        assert not np.any(flags & 1)
+        size = np.array([p.ncells for p, _ in probs])
+        one_d = [i for i, (p, _) in enumerate(probs) if p.ndim == 1]
+        two_d = [i for i, (p, _) in enumerate(probs) if p.ndim == 2]
+        small = sorted(one_d, key=lambda i: size[i])[:3] + sorted(two_d, key=lambda i: size[i])[:2]
+        for i in small:
+            pb, W = probs[i]
+            Wc, _, _, tc, _ = oracle.run(pb, W, nsteps=2)
+            assert abs(t[i] - tc) <= 1e-12 * tc
+            assert comp_err(bt.state(i), Wc) <= 1e-9, i
+        rng = np.random.default_rng(5)
+        spread = list(rng.choice(len(probs), 6, replace=False)) + [int(np.argmax(size))]
+        for i in spread:
+            pb, W = probs[i]
+            s = A.Solver(pb, W)
+            for _ in range(2):
+                s.step()
+            assert comp_err(bt.state(i), s.W.cpu().numpy()) <= 1e-13, i
+            s.close()
+    finally:
+        bt.close()
