@@ -200,24 +200,47 @@ def time_steps(A, torch, pb, W0, steps, warmup, flush_buf, profile=False):
 
 
 def time_e2e(A, torch, pb, W0, steps, warmup):
-    """Same metric through the public API with host buffers: every step copies W^n from
-    pinned host memory to the device and W^{n+1} back, inside the timed region."""
+    """Same metric through the public API with host buffers: every step copies its input W^n
+    from pinned host memory to the device and its result W^{n+1} back, inside the timed region.
+    Two device state buffers let the copies of one step overlap the compute of its neighbours,
+    as a caller streaming states through the solver would run it: a copy stream, and events
+    that order each buffer's host-to-device copy, step and device-to-host copy."""
     s = A.Solver(pb, W0)
     host_in = torch.from_numpy(np.ascontiguousarray(W0)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    stream = torch.cuda.current_stream()
-    for _ in range(warmup):
-        s.W.copy_(host_in, non_blocking=True)
-        s.step()
-        host_out.copy_(s.W, non_blocking=True)
-    torch.cuda.synchronize()
+    comp = torch.cuda.current_stream()
+    cp = torch.cuda.Stream()
+    bufs = [s.W, torch.empty_like(s.W)]
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    ready, done = [ev(), ev()], [ev(), ev()]
+    sy = s.sy if pb.ndim == 2 else None
+
+    def pipeline(n, start):
+        cp.wait_event(start)
+        for k in range(min(2, n)):
+            with torch.cuda.stream(cp):
+                bufs[k].copy_(host_in, non_blocking=True)
+                ready[k].record(cp)
+        for k in range(n):
+            b = k % 2
+            comp.wait_event(ready[b])
+            A.ase_df_step(s.ctx, bufs[b], s.sx, sy, 0.0, comp)
+            done[b].record(comp)
+            cp.wait_event(done[b])
+            with torch.cuda.stream(cp):
+                host_out.copy_(bufs[b], non_blocking=True)
+                if k + 2 < n:
+                    bufs[b].copy_(host_in, non_blocking=True)
+                    ready[b].record(cp)
+        comp.wait_stream(cp)  # the last read-back is inside the timed region
+
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        s.W.copy_(host_in, non_blocking=True)
-        s.step()
-        host_out.copy_(s.W, non_blocking=True)
-    e1.record(stream)
+    e0.record(comp)
+    pipeline(warmup, e0)
+    torch.cuda.synchronize()
+    e0.record(comp)
+    pipeline(steps, e0)
+    e1.record(comp)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     s.close()
@@ -333,7 +356,10 @@ def run_ours(args, world, rank, local):
                     "frac": round(hbm_achieved / hbm_gbs, 5) if hbm_gbs else None,
                     "bytes_per_cell_stage": HBM_BYTES_PER_CELL_STAGE_2D},
         },
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                "method": "every step copies its input from pinned host memory and its result back; two device "
+                          "state buffers and a copy stream overlap the copies with the neighbouring steps; no L2 "
+                          "flush (the copied input passes through L2, unlike the device-timed steps)"},
         "gpu_launches": int(sum(prof[1])),
         "clocks": clocks,
         "status_flags": flags,
