@@ -11,7 +11,11 @@
  * adaptive stencil extension of Sec. 3 (Algorithm 1) driven by the discontinuity
  * feedback factor of Sec. 3.1, Eq. (3.2): linear 5th/7th/9th order where the stencil is
  * smooth, WENOZ-AO(5,3) with DF damping (Sec. 3.2) otherwise.  Time stepping is the
- * SSP-RK3 of Sec. 2.3.
+ * SSP-RK3 of Sec. 2.3.  Also here: the paper's gas-kinetic flux with S2O4 time stepping
+ * (Sec. 2.2, ase_df_gks_*), vector-Jacobian products of the residual and of a step
+ * (ase_df_residual_adjoint, ase_df_step_adjoint), batched solves of many independent
+ * problems (ase_df_batch_*), and a residual entry point that allocates nothing
+ * (ase_df_residual_noalloc).
  *
  * Conventions (all entry points):
  *   - Arrays are DEVICE pointers owned by the caller, FP64, C-contiguous:
@@ -24,7 +28,9 @@
  *   - sigma is solver state: the sigma a residual consumes is the one the previous
  *     residual (previous RK stage) produced; ase_df_prime_sigma gives sigma^0.
  *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls are
- *     stream-ordered and asynchronous; only ase_df_get_status synchronises.
+ *     stream-ordered and asynchronous; the status readers (ase_df_get_status,
+ *     ase_df_get_repair_stats, ase_df_batch_get_status), the benchmark helpers and the
+ *     batch schedule setters synchronise, as their comments say.
  *   - The context owns its scratch memory (face fluxes, RK stage states, sigma
  *     ping-pong buffers); one context per host thread.
  *   - Errors: argument and launch errors are returned at once (ase_df_last_error gives
@@ -303,13 +309,15 @@ ase_df_status ase_df_batch_get_status(ase_df_batch* b, uint32_t* flags, double* 
 
 /* Schedule: persistent sweep CTAs per SM (1 or 2), work items ordered by cost (1) or by
  * problem (0), cells per chunk of the per-cell kernels (256 .. 2^24).  Chosen by the
- * autotuner of the Python package; results do not depend on it. */
+ * autotuner of the Python package; results do not depend on it.  Synchronises the device
+ * when the work lists change. */
 ase_df_status ase_df_batch_set_schedule(ase_df_batch* b, int32_t ctas_per_sm, int32_t order_by_cost,
                                         int32_t chunk_cells);
 
 /* Tile shape of the 2D sweeps per scheme order: lines[k] (k = 0..3 for orders 3, 5, 7, 9) is
  * 64 (tiles of 8 x 64 faces, two faces per thread) or 32 (8 x 32, one face per thread).
- * Chosen by the autotuner of the Python package; results do not depend on it. */
+ * Chosen by the autotuner of the Python package; results do not depend on it.  Synchronises
+ * the device when the tiles change. */
 ase_df_status ase_df_batch_set_tiles(ase_df_batch* b, const int32_t* lines);
 
 /* Message of the last error on this batch (or of the last failed ase_df_batch_init when
