@@ -314,3 +314,24 @@ def test_jet_reaches_t_end_with_repair(oracle, order):
     rho = Wn[0]
     p = (pb.gamma - 1) * (Wn[3] - 0.5 * (Wn[1] ** 2 + Wn[2] ** 2) / rho)
     assert abs(t - 1e-5) < 1e-15 and rho.min() > 0 and p.min() > 0
+
+
+
+@pytest.mark.parametrize("r,min_order", [(5, 4.5), (7, 6.0)])
+def test_vortex_convergence_order(oracle, r, min_order):
+    """Measured convergence on the smooth isentropic vortex (strength 5 on (1,1,1,1),
+    periodic [0,10]^2): the vortex is advected unchanged, so the exact solution at t is the
+    initial field shifted by (t, t).  40^2 and 80^2 cells to t = 0.2 with dt = min(CFL dt,
+    dx^(r/3)) (the SSP-RK3 time error then scales as dx^r): L1 error of the density falls
+    at order >= 4.5 (r = 5, observed 4.72) and >= 6.0 (r = 7, observed 6.18; 40^2 cells
+    resolve the vortex core with 4 cells per unit, still pre-asymptotic for the high orders).
+    The GPU path's orders on 32^2 .. 256^2 to t = 2 are in tests/test_gpu_convergence.py."""
+    T = 0.2
+    errs = []
+    for n in (40, 80):
+        pb, W0 = P.isentropic_vortex(n, r)
+        h = min(oracle.cfl_dt(pb, W0), pb.dx ** (r / 3.0))
+        nsteps = int(np.ceil(T / h))
+        W, *_ = oracle.run(pb, W0, nsteps=nsteps, dt=T / nsteps)
+        errs.append(np.abs(W[0] - P.vortex_exact(pb, T)[0]).mean())
+    assert np.log2(errs[0] / errs[1]) >= min_order, errs
