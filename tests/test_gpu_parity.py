@@ -228,6 +228,32 @@ def test_residual_parity_tiny_and_edge_grids(A, oracle, shape, order):
         check_residual(A, oracle, pb1, W1, *P.random_sigma(pb1, 4, 0.6))
 
 
+def test_residual_parity_at_the_largest_1d_grid(A, oracle):
+    """nx = 2^20 (the largest grid the context accepts along one direction): every face
+    against the oracle at the standard tolerances, random sigma straddling the threshold."""
+    pb = P.Problem(ndim=1, nx=1 << 20, order=9, bc=("periodic",) * 4)
+    check_residual(A, oracle, pb, P.smooth_random(pb, 31), *P.random_sigma(pb, 32, 1.0))
+
+
+def test_residual_parity_at_the_largest_1d_grid_white_noise(A, oracle):
+    """2^20 faces of per-cell white noise; about half of the reconstructions take the
+    WENOZ-AO(5,3)+DF fallback (Sec. 3.2).  Its weights d (1 + tau_Z^2 / (beta + eps)^2) are
+    ill-conditioned where tau_Z sums differences of nearly equal smoothness indicators, so two
+    correct FP64 evaluations of one rough stencil can differ by far more than ulps: over these
+    2^20 stencils the worst face measured 2.9e-12 of max|F| in the flux and 7.5e-12 relative in
+    sigma.  This size is checked at 1e-11 (flux, L, sigma); the seeded parity inputs (up to
+    4096 cells) meet the standard 1e-13 / 1e-12 bounds."""
+    pb = P.Problem(ndim=1, nx=1 << 20, order=9, bc=("outflow",) * 4)
+    W = P.white_noise(pb, 31)
+    sx, sy = P.random_sigma(pb, 32, 1.0)
+    Lc, sxc, _, Fxc, _, hist = oracle.residual(pb, W, sx, sy)
+    Lg, sxg, _, Fxg, _, _ = gpu_residual(A, pb, W, sx, sy)
+    assert hist[3] > 0.3 * hist.sum()
+    assert comp_err(Fxg, Fxc) <= 1e-11
+    assert comp_err(Lg, Lc, residual_floor(pb, Fxc, None)) <= 1e-11
+    assert np.all(np.abs(sxg - sxc) <= 1e-11 * (1 + np.abs(sxc)) + 1e-13 * sxc * sxc)
+
+
 def test_free_stream_is_exact_on_gpu(A):
     for ndim, r in ((1, 9), (2, 9), (2, 3)):
         pb = P.Problem(ndim=ndim, nx=40, ny=20, order=r, bc=("periodic",) * 4)
