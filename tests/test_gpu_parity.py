@@ -17,6 +17,9 @@ Tolerances (per component c, normalised by the largest magnitude of that compone
     |L| is at least ~1e-2 max|F| / dx (smooth data on fine grids: |L| ~ |F'| while
     |F| / dx grows with N; a single-cell grid with random sigma: L is cancellation noise)
   * after 100 SSP-RK3 steps:  max|W_gpu - W_cpu| / max|W_cpu|      <= 1e-9
+One case is held to a wider bound: 2^20 cells of per-cell white noise (1e-11 for the flux, L and
+sigma), where the WENO-Z weights of the fallback amplify rounding on rough stencils; its test
+gives the measured worst face.
 Branch decisions are taken from the same sigma_in with the same association on both
 sides, so they agree exactly; the remaining differences are rounding (FMA contraction,
 reciprocal multiplications).
