@@ -77,7 +77,7 @@ constexpr int kNT = 256;
 template <int R, int DIM, int DIR, int TT = (DIM == 2) ? 64 : 1>
 __device__ __noinline__ void tile_call(const GridInfo& g, const SweepArgs& a, const Tables& T, int a0, int b0,
                                        double* smem) {
-  sweep_tile<R, DIM, DIR, TT>(g, a, T, a0, b0, smem);
+  sweep_tile<R, DIM, DIR, TT>(g, a, T, a0, b0, TT, smem);
 }
 
 // 2D tile of 8 faces x tt lines (64: two faces per thread, 32: one)

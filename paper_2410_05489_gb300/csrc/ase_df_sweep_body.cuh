@@ -217,11 +217,12 @@ struct Tile {
       (size_t)C * NB * NA + 2 * (size_t)C * NB * NQ + (size_t)NB * NSN + (DIM == 2 ? (size_t)NQ * NST : 0);
 };
 
-// One tile: faces a0 .. a0+TN-1 along the sweep on lines b0 .. b0+TT-1 (threadIdx.x in
-// [0, TN*TT/..) is the worker index); smem holds Tile<R, DIM>::smem_doubles doubles.
+// One tile: faces a0 .. a0+TN-1 along the sweep on lines b0 .. b0+tt-1, 1 <= tt <= TT
+// (threadIdx.x is the worker index); smem holds Tile<R, DIM, TT>::smem_doubles doubles,
+// laid out for TT lines whatever tt is.
 template <int R, int DIM, int DIR, int TT_ = (DIM == 2) ? 64 : 1>
 __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& args, const Tables& T, int a0,
-                                           int b0, double* smem) {
+                                           int b0, int tt, double* smem) {
   using TL = Tile<R, DIM, TT_>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
   constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
@@ -238,31 +239,33 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   const int n = (DIR == 0) ? g.nx : g.ny;       // cells along the sweep
   const int mlin = (DIR == 0) ? g.ny : g.nx;    // lines
   const int tid = threadIdx.x;
+  const int nb = tt + 2 * KT;  // staged lines of this tile (<= NB)
 
   const double ts = stage_time(args.st, args.tfrac, args.st->dt);  // for time-dependent ghosts
-  // ---- stage cell averages: cells a0-1-K .. a0+TN-1+K, lines b0-KT .. b0+TT+KT-1 ----
-  for (int idx = tid; idx < C * NB * NA; idx += NT) {
+  // ---- stage cell averages: cells a0-1-K .. a0+TN-1+K, lines b0-KT .. b0+tt+KT-1 ----
+  for (int idx = tid; idx < C * nb * NA; idx += NT) {
     int c, bb, aa;
-    if (DIR == 0) { aa = idx % NA; bb = (idx / NA) % NB; c = idx / (NA * NB); }
-    else { bb = idx % NB; aa = (idx / NB) % NA; c = idx / (NA * NB); }
+    if (DIR == 0) { aa = idx % NA; bb = (idx / NA) % nb; c = idx / (NA * nb); }
+    else { bb = idx % nb; aa = (idx / nb) % NA; c = idx / (NA * nb); }
     const int a = a0 - 1 - K + aa, b = b0 - KT + bb;
     const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
     sW[(c * NB + bb) * NA + aa] = fetch_w(g, args.W, c, i, j, ts);
   }
   // ---- normal face strengths: faces a0-K .. a0+TN-1+K of every staged line ----
-  for (int idx = tid; idx < NB * NSN; idx += NT) {
+  for (int idx = tid; idx < nb * NSN; idx += NT) {
     int fa, bb;
     if (DIR == 0) { fa = idx % NSN; bb = idx / NSN; }
-    else { bb = idx % NB; fa = idx / NB; }
+    else { bb = idx % nb; fa = idx / nb; }
     sSn[bb * NSN + fa] = (DIR == 0) ? sigma_x_at(g, args.s_norm, a0 - K + fa, b0 - KT + bb)
                                     : sigma_y_at(g, args.s_norm, a0 - K + fa, b0 - KT + bb);
   }
   // ---- tangential face strengths of the reconstructing cells' columns ----
   if (DIM == 2) {
-    for (int idx = tid; idx < NQ * (NST - 1); idx += NT) {
+    const int nst = tt + 2 * K - 1;  // tangential faces b0-K+1 .. b0+tt+K-1
+    for (int idx = tid; idx < NQ * nst; idx += NT) {
       int qa, fb;
       if (DIR == 0) { qa = idx % NQ; fb = idx / NQ; }
-      else { fb = idx % (NST - 1); qa = idx / (NST - 1); }
+      else { fb = idx % nst; qa = idx / nst; }
       sSt[qa * NST + fb] = (DIR == 0) ? sigma_y_at(g, args.s_tan, b0 - K + 1 + fb, a0 - 1 + qa)
                                       : sigma_x_at(g, args.s_tan, b0 - K + 1 + fb, a0 - 1 + qa);
     }
@@ -274,11 +277,11 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   // xi = 0 and xi = -1; the two end cells serve one tile face each (qa = 0: its xi = 0
   // value, the left state of face a0; qa = NQ-1: its xi = -1 value), so they come last in
   // the work list and evaluate one point.
-  for (int it = tid; it < NQ * NB; it += NT) {
-    if (it < (NQ - 2) * NB) {
+  for (int it = tid; it < NQ * nb; it += NT) {
+    if (it < (NQ - 2) * nb) {
       int qa, bb;
       if (DIR == 0) { qa = 1 + it % (NQ - 2); bb = it / (NQ - 2); }
-      else { bb = it % NB; qa = 1 + it / NB; }
+      else { bb = it % nb; qa = 1 + it / nb; }
       const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
@@ -289,8 +292,8 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
         sQM[(c * NB + bb) * NQ + qa] = out[1];
       }
     } else {
-      const int e = it - (NQ - 2) * NB;
-      const int bb = e % NB, pt = e / NB;  // pt 0: cell qa = 0 at xi = 0; 1: qa = NQ-1 at xi = -1
+      const int e = it - (NQ - 2) * nb;
+      const int bb = e % nb, pt = e / nb;  // pt 0: cell qa = 0 at xi = 0; 1: qa = NQ-1 at xi = -1
       const int qa = pt * (NQ - 1);
       const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
       double* dst = pt ? sQM : sQP;
@@ -306,10 +309,10 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   __syncthreads();
 
   // ---- phase 2: faces ----
-  for (int it = tid; it < TN * TT; it += NT) {
+  for (int it = tid; it < TN * tt; it += NT) {
     int fa, tb;
     if (DIR == 0) { fa = it % TN; tb = it / TN; }
-    else { tb = it % TT; fa = it / TT; }
+    else { tb = it % tt; fa = it / tt; }
     const int f = a0 + fa, b = b0 + tb;
     if (f > n || b >= mlin) continue;
     double st[2][G][C];
