@@ -282,11 +282,15 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
-    ms, prof, flags = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush, profile=True)
-    clocks = sampler.stop()
+    ms, _, flags = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush)
     torch.cuda.synchronize()
     barrier(world)
     ms_max = max_over_ranks(ms, world)
+    # Launch durations of the kernels: the same K steps once more with an event pair around
+    # every launch.  The pairs add a few microseconds at each launch boundary (~2 % of a
+    # 1024^2 step), so the headline above is timed without them.
+    ms_prof, prof, _ = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush, profile=True)
+    clocks = sampler.stop()
     ms7, _, _ = time_steps(A, torch, pb7, W7, args.steps, args.warmup, flush)
     ms7_max = max_over_ranks(ms7, world)
     e2e_ms, bi, bo = time_e2e(A, torch, pb, W0, args.steps, args.warmup)
@@ -350,6 +354,8 @@ def run_ours(args, world, rank, local):
             "frac_of_microbench": round(achieved / (2.0 * fma_rate / 1e12), 4),
             "flops_per_launch": flops_per_launch,
             "launch_ms": round(sweep_ms / sweep_n, 4),
+            "launch_ms_source": "CUDA event pair around every launch, in a second timed pass of the same K steps "
+                                "(%.4f ms/step with the pairs)" % (ms_prof / args.steps),
             "share_of_step_time": round(sweep_ms / total_prof_ms, 4) if total_prof_ms > 0 else None,
             "step_frac_of_fp64_peak": round(step_flops * args.steps / (ms_max * 1e-3) / 1e12 / peak_tflops, 4),
             "hbm": {"achieved_gbs": round(hbm_achieved, 2), "peak_gbs": hbm_gbs,
@@ -360,7 +366,7 @@ def run_ours(args, world, rank, local):
                 "method": "every step copies its input from pinned host memory and its result back; two device "
                           "state buffers and a copy stream overlap the copies with the neighbouring steps; no L2 "
                           "flush (the copied input passes through L2, unlike the device-timed steps)"},
-        "gpu_launches": int(sum(prof[1])),
+        "gpu_launches": int(sum(prof[1])),  # counted in the profiled pass: the same K steps, the same launches
         "clocks": clocks,
         "status_flags": flags,
     }
@@ -651,8 +657,9 @@ def suite_bench(args):
     # vortex 1024^2 at r = 5, 7, 9 (GPU), oracle on 256^2
     for r in (5, 7, 9):
         pb, W0 = P.isentropic_vortex(1024, r)
-        ms, prof, flags = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush, profile=True)
+        ms, _, flags = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush)
         value = pb.ncells * 3 * args.steps / (ms * 1e-3) / 1e6
+        _, prof, _ = time_steps(A, torch, pb, W0, args.steps, args.warmup, flush, profile=True)  # launch times
         sweep_ms, sweep_n = prof[0][0] + prof[0][1], prof[1][0] + prof[1][1]
         faces = 0.5 * ((pb.nx + 1) * pb.ny + (pb.ny + 1) * pb.nx)
         achieved = algorithmic_flops_per_face(2, r) * faces / (sweep_ms / sweep_n * 1e-3) / 1e12
