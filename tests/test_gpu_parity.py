@@ -231,6 +231,21 @@ def test_residual_parity_tiny_and_edge_grids(A, oracle, shape, order):
         check_residual(A, oracle, pb1, W1, *P.random_sigma(pb1, 4, 0.6))
 
 
+@pytest.mark.parametrize("order", [3, 5, 7, 9])
+def test_residual_parity_both_tile_grids(A, oracle, order):
+    """The two launch forms of the 2D sweep on a 152-SM GPU, every face against the oracle.
+    - 256^2: the wave-filling plan, with tile columns of 9 and 10 line blocks of 25 - 29 lines.
+    - 7990 x 70: the uniform 8 x 64 grid in both directions (more than three waves of tiles),
+      with ragged last blocks of 6 and 54 lines.
+    Smooth data with random sigma, which takes the linear and the WENO/DF branches of the
+    order; a face's arithmetic does not depend on the tile that computes it."""
+    for nx, ny in ((256, 256), (7990, 70)):
+        pb = P.Problem(ndim=2, nx=nx, ny=ny, order=order, bc=("outflow",) * 4)
+        W = P.smooth_random(pb, 70 + order)
+        # order 3 sums two faces: sigma up to 2 takes both of its branches
+        check_residual(A, oracle, pb, W, *P.random_sigma(pb, 80 + order, 2.0 if order == 3 else 1.0))
+
+
 def test_residual_parity_at_the_largest_1d_grid(A, oracle):
     """nx = 2^20 (the largest grid the context accepts along one direction): every face
     against the oracle at the standard tolerances, random sigma straddling the threshold."""
