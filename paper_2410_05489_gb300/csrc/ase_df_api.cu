@@ -47,6 +47,9 @@ struct ase_df_ctx {
   double g_dt;
   cudaStream_t cap_stream;
   cudaStream_t last_stream;
+  // 2D: the stream and events of the y-sweep, which runs beside the x-sweep (face_fluxes)
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
   // kernel timing (ase_df_profile_*)
   bool prof_on;
   std::vector<cudaEvent_t>* prof_ev;  // pairs (start, stop)
@@ -268,6 +271,9 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
   }
   cudaError_t e = cudaMemset(c->zsx, 0, nsx * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->zsy, 0, nsy * sizeof(double));
+  if (e == cudaSuccess && p.ndim == 2) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && p.ndim == 2) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && p.ndim == 2) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemset(c->st, 0, sizeof(DevState));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -290,6 +296,9 @@ void ase_df_destroy(ase_df_ctx* c) {
   if (c->mark) cudaFree(c->mark);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   prof_clear(c);
   delete c->prof_ev;
   delete c->prof_kind;
@@ -323,12 +332,27 @@ static cudaError_t sweep(ase_df_ctx* c, int dir, const double* W, const double* 
 }
 
 // Face fluxes of both directions of W with sigma_in = (sx, sy), sigma_out -> (sxo, syo);
-// time-dependent ghosts at the device time t + tfrac dt.
+// time-dependent ghosts at the device time t + tfrac dt.  The two sweeps read the same
+// inputs and write separate outputs, so in 2D the y-sweep runs on the context's side stream
+// (forked from and joined back to s, also under graph capture): its tiles take the SMs that
+// the x-sweep's last tiles leave.  With kernel timing on, the sweeps run one after the other
+// so that each launch is timed alone.
 static cudaError_t face_fluxes(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
                                double* sxo, double* syo, cudaStream_t s, double tfrac = 0.0) {
-  cudaError_t e = sweep(c, 0, W, sx, sy, c->Fx, sxo, s, tfrac);
-  if (e != cudaSuccess || c->dim == 1) return e;
-  return sweep(c, 1, W, sx, sy, c->Fy, syo, s, tfrac);
+  if (c->dim == 1 || c->prof_on) {
+    cudaError_t e = sweep(c, 0, W, sx, sy, c->Fx, sxo, s, tfrac);
+    if (e != cudaSuccess || c->dim == 1) return e;
+    return sweep(c, 1, W, sx, sy, c->Fy, syo, s, tfrac);
+  }
+  cudaError_t e = cudaEventRecord(c->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  if (e != cudaSuccess) return e;
+  cudaError_t ex = sweep(c, 0, W, sx, sy, c->Fx, sxo, s, tfrac);
+  cudaError_t ey = sweep(c, 1, W, sx, sy, c->Fy, syo, c->side, tfrac);
+  // the join is made whatever happened, so that s never runs ahead of the side stream
+  e = cudaEventRecord(c->ev_join, c->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+  return ex != cudaSuccess ? ex : (ey != cudaSuccess ? ey : e);
 }
 
 // Time offsets of the SSP-RK3 stage values (Sec. 2.3): W^n at t, W^(1) at t + dt, W^(2) at

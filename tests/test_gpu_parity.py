@@ -281,7 +281,9 @@ def test_free_stream_is_exact_on_gpu(A):
         # every face does the same arithmetic: the flux difference vanishes exactly; the
         # two states of a face come from mirror-image weights, equal up to rounding
         assert np.all(L == 0.0)
-        assert sx.max() < 1e-14 and sy.max() < 1e-14
+        assert sx.max() < 1e-14
+        if ndim == 2:  # 1D has no y-faces (its sy is a placeholder the library does not write)
+            assert sy.max() < 1e-14
 
 
 def run_gpu(A, pb, W, nsteps, dt=0.0, t_end=0.0, graph=False):
