@@ -30,7 +30,10 @@
  *   - stream is a cudaStream_t (NULL = the legacy default stream).  Calls are
  *     stream-ordered and asynchronous; the status readers (ase_df_get_status,
  *     ase_df_get_repair_stats, ase_df_batch_get_status), the benchmark helpers and the
- *     batch schedule setters synchronise, as their comments say.
+ *     batch schedule setters synchronise, as their comments say.  A 2D context runs
+ *     its y-face sweeps on a stream of its own, forked from and joined back to the
+ *     caller's stream within each call (also under graph capture), so the ordering
+ *     seen from the caller's stream is unchanged.
  *   - The context owns its scratch memory (face fluxes, RK stage states, sigma
  *     ping-pong buffers); one context per host thread.
  *   - Errors: argument and launch errors are returned at once (ase_df_last_error gives
@@ -214,7 +217,8 @@ const char* ase_df_last_error(const ase_df_ctx* ctx);
 
 /* Kernel timing with CUDA events recorded on the launching stream around every sweep,
  * combine and wave-speed launch of this context (enable != 0 starts a new record, 0
- * stops recording).  ase_df_profile_read synchronises, then returns per kernel kind
+ * stops recording; while it records, the two sweeps of a stage run one after the
+ * other on the caller's stream, so that each launch is timed alone).  ase_df_profile_read synchronises, then returns per kernel kind
  * (0: x-face sweep, 1: y-face sweep, 2: combine, 3: wave-speed reduction, 4: positivity
  * repair pass) the summed milliseconds ms[5] and the launch counts n[5]; at most 65536
  * launches are recorded. */
