@@ -18,9 +18,8 @@
 
 #include <cuda_runtime.h>
 
-#include <algorithm>
-
 #include "ase_df_sweep_body.cuh"
+#include "ase_df_tileplan.h"
 
 #ifndef ASE_DF_ORDER
 #error "ASE_DF_ORDER must be defined"
@@ -28,31 +27,6 @@
 
 namespace asedf {
 namespace {
-
-// Tiles of a 2D sweep: the tile columns (TN faces along the sweep) split their lines into
-// nb_lo blocks (columns 0 .. n1-1) or nb_lo + 1 blocks (the others), block k of nbk covering
-// lines floor(k m / nbk) .. floor((k+1) m / nbk) - 1.  CTA x takes, in order, the n1 nb_lo
-// tiles of the first columns (the larger tiles, so that the last wave is of the smaller
-// ones), then the others; within each group consecutive CTAs are neighbours along the sweep.
-// 1D: one line, one block per column.
-struct TilePlan {
-  int n1, n2;  // columns with nb_lo / nb_lo + 1 blocks
-  int nb_lo;
-  int m;       // lines
-};
-
-__device__ __forceinline__ void plan_tile(const TilePlan& p, int x, int& col, int& b0, int& tt) {
-  const int g1 = p.n1 * p.nb_lo;
-  int k, nbk;
-  if (x < g1) {
-    col = x % p.n1; k = x / p.n1; nbk = p.nb_lo;
-  } else {
-    x -= g1;
-    col = p.n1 + x % p.n2; k = x / p.n2; nbk = p.nb_lo + 1;
-  }
-  b0 = (int)(((long long)k * p.m) / nbk);
-  tt = (int)(((long long)(k + 1) * p.m) / nbk) - b0;
-}
 
 // PLAN = false: a uniform grid (x: tile column, y: blocks of TT lines, the last one ragged).
 template <int R, int DIM, int DIR, int TT, bool PLAN>
@@ -70,24 +44,6 @@ sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tab
   } else {
     sweep_tile<R, DIM, DIR, TT>(g, args, T, blockIdx.x * Tile<R, DIM, TT>::TN, blockIdx.y * TT, TT, smem);
   }
-}
-
-// Plan of the tiles of one 2D sweep on `slots` CTA slots (two per SM).  Tiles of up to TT
-// lines need q = ceil(m / TT) blocks per column and w = ceil(cols q / slots) waves; the plan
-// fills all w waves (w slots tiles, at most ceil(m / 16) blocks per column so that no tile
-// is under ~16 lines), which shortens the tiles and with them the w waves.
-TilePlan make_plan(long long cols, int m, int tt_max, int slots, long long& tiles) {
-  const long long q = (m + tt_max - 1) / tt_max;
-  const long long t0 = cols * q;
-  const long long target = (t0 + slots - 1) / slots * slots;
-  const long long nb_max = std::max(q, (long long)(m + 15) / 16);
-  tiles = std::min(target, cols * nb_max);
-  TilePlan p;
-  p.nb_lo = (int)(tiles / cols);
-  p.n2 = (int)(tiles % cols);
-  p.n1 = (int)(cols - p.n2);
-  p.m = m;
-  return p;
 }
 
 template <int R, int DIM, int DIR, int TT, bool PLAN>
@@ -118,9 +74,9 @@ cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaS
   if constexpr (DIM == 2) {
     const int slots = 2 * device_sm_count();
     const long long q = (m + TT - 1) / TT;
-    if (cols * q <= 3LL * slots) {
+    if (use_tile_plan(cols, m, TT, slots)) {
       long long tiles;
-      const TilePlan p = make_plan(cols, m, TT, slots, tiles);
+      const TilePlan p = make_tile_plan(cols, m, TT, slots, tiles);
       return launch_grid<R, DIM, DIR, TT, true>(g, a, t, s, dim3((unsigned)tiles), p);
     }
     if (cols > 0x7fffffffLL || q > 65535) return cudaErrorInvalidConfiguration;
