@@ -253,6 +253,14 @@ def test_residual_parity_at_the_largest_1d_grid(A, oracle):
     check_residual(A, oracle, pb, P.smooth_random(pb, 31), *P.random_sigma(pb, 32, 1.0))
 
 
+def test_residual_parity_at_the_largest_2d_extent(A, oracle):
+    """2^20 x 2 cells, the largest extent the context accepts along x: the x-sweep launches
+    131073 tile columns, the y-sweep one column of 16384 line blocks.  Every face against the
+    oracle at the standard tolerances (smooth data, random sigma straddling the threshold)."""
+    pb = P.Problem(ndim=2, nx=1 << 20, ny=2, order=9, bc=("outflow",) * 4)
+    check_residual(A, oracle, pb, P.smooth_random(pb, 33), *P.random_sigma(pb, 34, 1.0))
+
+
 def test_residual_parity_at_the_largest_1d_grid_white_noise(A, oracle):
     """2^20 faces of per-cell white noise; about half of the reconstructions take the
     WENOZ-AO(5,3)+DF fallback (Sec. 3.2).  Its weights d (1 + tau_Z^2 / (beta + eps)^2) are
