@@ -721,7 +721,16 @@ static ase_df_status ensure_gks(ase_df_ctx* c) {
 static cudaError_t gks_face_fluxes(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
                                    double* sxo, double* syo, double dt_fixed, cudaStream_t s,
                                    double tfrac = 0.0) {
-  for (int dir = 0; dir < c->dim; ++dir) {
+  // as face_fluxes: in 2D the y-sweep runs on the side stream unless kernel timing is on
+  const bool fork = c->dim == 2 && !c->prof_on;
+  if (fork) {
+    cudaError_t e = cudaEventRecord(c->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t err = cudaSuccess;
+  for (int dir = 0; dir < c->dim && err == cudaSuccess; ++dir) {
+    const cudaStream_t sd = (fork && dir == 1) ? c->side : s;
     GksSweepArgs a;
     a.tfrac = tfrac;
     a.W = W;
@@ -736,17 +745,20 @@ static cudaError_t gks_face_fluxes(ase_df_ctx* c, const double* W, const double*
     a.inv_dt = (dir == 0) ? c->inv_dy : c->inv_dx;
     a.c1 = c->p.gks_c1 > 0.0 ? c->p.gks_c1 : 0.05;
     a.c2 = c->p.gks_c2 > 0.0 ? c->p.gks_c2 : 1.0;
-    cudaError_t e;
-    ProfScope prof(c, s, dir);
+    ProfScope prof(c, sd, dir);
     switch (c->p.order) {
-      case 3: e = launch_gks_sweep_r3(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
-      case 5: e = launch_gks_sweep_r5(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
-      case 7: e = launch_gks_sweep_r7(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
-      default: e = launch_gks_sweep_r9(c->dim, dir, c->g, a, c->tab, c->dtab, s); break;
+      case 3: err = launch_gks_sweep_r3(c->dim, dir, c->g, a, c->tab, c->dtab, sd); break;
+      case 5: err = launch_gks_sweep_r5(c->dim, dir, c->g, a, c->tab, c->dtab, sd); break;
+      case 7: err = launch_gks_sweep_r7(c->dim, dir, c->g, a, c->tab, c->dtab, sd); break;
+      default: err = launch_gks_sweep_r9(c->dim, dir, c->g, a, c->tab, c->dtab, sd); break;
     }
-    if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  if (fork) {  // the join is made whatever happened, so that s never runs ahead of the side stream
+    cudaError_t e = cudaEventRecord(c->ev_join, c->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+    if (err == cudaSuccess) err = e;
+  }
+  return err;
 }
 
 static cudaError_t gks_combine(ase_df_ctx* c, int stage, const double* Wn, double* out, double* Lt_out,
