@@ -47,15 +47,22 @@ SWEEP_DRAM_BYTES_1024_R9 = 58.19e6
 SWEEP_FP64_PIPE_ACTIVE_1024_R9 = 0.8455
 
 
+# FP64 operations of one Gauss point: both sides' primitives, the Lax-Friedrichs flux
+# 1/2 (F_L + F_R - lambda (q_R - q_L)) and sigma (Sec. 2.3, Sec. 3.1).  This is the oracle's
+# operation count for one point less one multiplication per component: the oracle scales
+# both halves of the flux by 1/2 (74 and 59 operations in 2D and 1D; tests/test_flop_model.py).
+GAUSS_POINT_FLOPS = {2: 70, 1: 56}
+
+
 def algorithmic_flops_per_face(ndim: int, r: int) -> float:
     """FP64 operations (add, sub, mul, div, sqrt: 1 each) of one face of one sweep on the
     all-smooth branch: the normal reconstruction of the face's cell evaluated at both of
     its faces (2 C (2r-1)), the tangential reconstruction at the G Gauss points of both
     states (2 C G (2r-1)), and per Gauss point the Lax-Friedrichs flux with primitives
-    and sigma (70 in 2D, 54 in 1D) plus the Gauss sum (2 C + 1); + 1 for the face sigma."""
+    and sigma (GAUSS_POINT_FLOPS) plus the Gauss sum (2 C + 1); + 1 for the face sigma."""
     C = 4 if ndim == 2 else 3
     G = ((r - 1) // 2 if r > 3 else 1) if ndim == 2 else 1
-    phi = 70 if ndim == 2 else 54
+    phi = GAUSS_POINT_FLOPS[ndim]
     normal = 2 * C * (2 * r - 1)
     tang = 2 * C * G * (2 * r - 1) if ndim == 2 else 0
     return normal + tang + G * (phi + 2 * C + 1) + 1
