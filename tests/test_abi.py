@@ -86,3 +86,21 @@ def test_init_rejects_bad_parameters_without_a_device(lib):
         with pytest.raises(A.AseDfError) as ei:
             A.ase_df_init(A.params_from_problem(Problem(**kw)))
         assert ei.value.status == 1
+
+
+def test_batch_init_rejects_bad_sets_without_a_device(lib):
+    """An empty batch, a batch with an invalid problem and one with a problem too large for
+    its 32-bit offsets are refused before any CUDA call."""
+    from paper_2410_05489_gb300 import ase_df as A
+    from paper_2410_05489_gb300 import batch as B
+    from paper_2410_05489_gb300.problems import Problem
+
+    with pytest.raises(A.AseDfError) as ei:
+        B.ase_df_batch_init([])
+    assert ei.value.status == 1
+    ok = A.params_from_problem(Problem(ndim=2, nx=8, ny=8, order=5))
+    for bad, status in ((Problem(ndim=2, nx=0, ny=8, order=5), 1), (Problem(ndim=2, nx=8, ny=8, order=6), 1),
+                        (Problem(ndim=2, nx=1 << 20, ny=1 << 12, order=5), 6)):
+        with pytest.raises(A.AseDfError) as ei:
+            B.ase_df_batch_init([ok, A.params_from_problem(bad)])
+        assert ei.value.status == status
