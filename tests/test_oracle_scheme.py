@@ -335,3 +335,17 @@ def test_vortex_convergence_order(oracle, r, min_order):
         W, *_ = oracle.run(pb, W0, nsteps=nsteps, dt=T / nsteps)
         errs.append(np.abs(W[0] - P.vortex_exact(pb, T)[0]).mean())
     assert np.log2(errs[0] / errs[1]) >= min_order, errs
+
+
+def test_ssp_rk3_is_third_order_in_time(oracle):
+    """SSP-RK3 (Sec. 2.3) on a fixed grid: the 1D sine wave on 40 cells at r = 9 (smooth,
+    so the linear branch throughout), marched to t = 0.4 with dt = 0.02, 0.01, 0.005 and
+    0.0025 (CFL 0.93 down to 0.12) against 1280 steps of the same scheme.  The spatial error
+    is common to all runs, so the differences are the time error.  They fall by 2^3 per
+    halving of dt; a wrong stage weight would leave the scheme first or second order."""
+    pb, W0 = P.sin_wave_1d(40, 9)
+    T = 0.4
+    ref = oracle.run(pb, W0, nsteps=1280, dt=T / 1280)[0]
+    errs = [np.abs(oracle.run(pb, W0, nsteps=n, dt=T / n)[0] - ref).max() for n in (20, 40, 80, 160)]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(2.9 < q < 3.1 for q in orders), orders
