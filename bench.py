@@ -119,23 +119,34 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons, power = [], [], set(), []
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
-                power.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+        return summarise_clocks(self.lines)
+
+
+def summarise_clocks(lines):
+    """Median SM clock, highest maximum SM clock, the throttle reasons seen active in any
+    sample, the sample count and the peak power, from nvidia-smi CSV lines in the order of
+    ClockSampler.FIELDS (no header, no units); lines that do not parse are skipped."""
+    sm, smax, reasons, power = [], [], set(), []
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 8:
+            continue
+        try:
+            clk, clk_max = float(parts[0]), float(parts[1])
+        except ValueError:
+            continue
+        sm.append(clk)
+        smax.append(clk_max)
+        try:
+            power.append(float(parts[2]))
+        except ValueError:  # "[N/A]" on parts without a power sensor
+            pass
+        for nm, v in zip(names, parts[4:8]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
 # ----------------------------------------------------------------------------------
