@@ -71,3 +71,21 @@ def test_batched_workload_follows_its_recipe():
         assert len(np.unique(rho)) <= (2 if pb.ndim == 1 else 4)
     again = P.batched_problems()
     assert all(np.array_equal(a[1], b[1]) for a, b in zip(probs[:8], again[:8]))
+
+
+def test_jet_configuration():
+    """The Mach-20000 jet (a re-scaled Sec. 4.3, Example 6): [0,1] x [-0.25,0.25] at 1600 x 800,
+    gamma 5/3, ambient (0.5, 0, 0, 0.4127) at rest, inflow band |y| < 0.05 at x = 0 with
+    rho = 5, p = 0.4127 and u = 20000 sqrt(gamma p / rho); the band edges fall on cell faces."""
+    pb, W = P.high_mach_jet(1600, 800, 9)
+    assert (pb.nx, pb.ny, pb.x0, pb.x1, pb.y0, pb.y1) == (1600, 800, 0.0, 1.0, -0.25, 0.25)
+    assert abs(pb.gamma - 5.0 / 3.0) < 1e-15 and pb.bc == ("inflow", "outflow", "outflow", "outflow")
+    rho_in, u_in, v_in, p_in = pb.inflow
+    assert (rho_in, v_in, p_in) == (5.0, 0.0, 0.4127)
+    assert abs(u_in / np.sqrt(pb.gamma * p_in / rho_in) - 20000.0) < 1e-6
+    assert abs(u_in - 7417.996) < 1e-3
+    for edge in (pb.inflow_lo, pb.inflow_hi):
+        k = (edge - pb.y0) / pb.dy
+        assert abs(k - round(k)) < 1e-9  # 80 cells on each side of y = 0
+    rho, u, v, p = _primitives(pb, W)
+    assert np.all(rho == 0.5) and np.all(u == 0.0) and np.allclose(p, 0.4127, rtol=0, atol=1e-15)
