@@ -213,6 +213,8 @@ def test_beta_matches_its_definition(oracle):
         b = beta[:3]
         b5 = (b[0] + 4 * b[1] + b[2]) / 6 + abs(b[0] - b[2])
         assert abs(beta[3] - b5) < 1e-13 * max(1, b5)
+        tau = (abs(b5 - b[0]) + abs(b5 - b[1]) + abs(b5 - b[2])) / 3
+        assert abs(beta[4] - tau) < 1e-13 * max(1, b5)
 
 
 def test_beta_remark3_leading_terms(oracle):
@@ -234,3 +236,74 @@ def test_beta_remark3_leading_terms(oracle):
         wp = np.cos(xc - 0.5 * h)
         errs.append(abs(beta[1] / h ** 2 - wp ** 2))
     assert errs[1] < errs[0] / 3.0
+
+
+def test_weno_reconstruction_is_mirror_equivariant(oracle):
+    """The reflection x -> -x maps cell 0 = [-1, 0] onto itself (xi -> -1 - xi), reverses
+    the stencil and swaps the DF factors of S3_{-1} and S3_1. A reconstruction has no
+    preferred direction, so the WENOZ-AO(5,3)+DF value must commute with it. With the linear
+    weights d3_{-1} = d3_1 this holds only if the global indicator tau_Z treats beta3_{-1}
+    and beta3_1 alike (reading G5); the printed form, with |beta5 - beta3_1| twice and no
+    beta3_0 term, breaks it by O(1) on rough data."""
+    rng = np.random.default_rng(12)
+    xi = np.array([0.0, -1.0, -0.3, -0.5, -0.8873])
+    cases = [rng.normal(size=5) for _ in range(150)]
+    cases += [np.array([0, 0, 0, 1, 1.0]), np.array([1, 2, 2, 2, 7.0]), np.array([0.1, 10, 0.1, 0.1, 0.2])]
+    cases += [rng.lognormal(size=5) * rng.choice([1e-3, 1.0, 1e3]) for _ in range(50)]
+    swapped = 0
+    for v in cases:
+        alpha = rng.uniform(0.02, 1.0, 4)
+        if rng.uniform() < 0.3:
+            alpha[:] = 1.0
+        out, beta = oracle.weno_ao53(v, alpha, xi)
+        outm, betam = oracle.weno_ao53(v[::-1].copy(), alpha[[2, 1, 0, 3]].copy(), -1.0 - xi)
+        scale = np.abs(v).max()
+        # the indicators are mirror images of each other (beta3_{-1} <-> beta3_1)
+        np.testing.assert_allclose(betam[[2, 1, 0, 3, 4]], beta, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(outm, out, rtol=0, atol=1e-13 * scale)
+        swapped += abs(beta[0] - beta[2]) > 0.1 * max(beta[0], beta[2])
+    assert swapped > 100  # most cases have clearly different beta3_{-1} and beta3_1
+
+
+def _sine_averages(F, x0, h):
+    """Cell averages over the five cells [x0 + (m-1)h, x0 + m h], m = -2..2, of f = F';
+    cell 0 is [x0 - h, x0] and its right face is x0."""
+    return np.array([(F(x0 + m * h) - F(x0 + (m - 1) * h)) / h for m in range(-2, 3)])
+
+
+@pytest.mark.parametrize("profile", ["monotone", "extremum_at_face", "extremum_inside_stencil"])
+def test_weno_fallback_is_fifth_order_on_smooth_data(oracle, profile):
+    """Sec. 3.2: the WENOZ-AO(5,3) combination with alpha = 1 reaches fifth order at the
+    face in smooth regions, also next to a critical point (f' = 0), where a global indicator
+    tau_Z that is not a difference of the betas, or weights that react to beta3_k alone,
+    fall back to third order."""
+    f, F, x0 = {
+        "monotone": (np.sin, lambda x: -np.cos(x), 0.3),
+        "extremum_at_face": (np.cos, np.sin, 0.0),
+        "extremum_inside_stencil": (np.cos, np.sin, 0.05),
+    }[profile]
+    hs = np.array([0.2, 0.1, 0.05, 0.025, 0.0125])
+    errs = []
+    for h in hs:
+        out, _ = oracle.weno_ao53(_sine_averages(F, x0, h), [1, 1, 1, 1], [0.0])
+        errs.append(abs(out[0] - f(x0)))
+    # error / h^5 stays bounded (third order would grow it 256-fold from h = 0.2 to 0.0125);
+    # a fitted slope is not used because the error changes sign near the extremum
+    ratio = np.array(errs) / hs ** 5
+    assert ratio[2:].max() <= 4.0 * ratio[:2].max(), ratio
+    assert errs[-1] < 1e-11
+
+
+def test_weno_epsilon_sets_the_linear_amplitude(oracle):
+    """The absolute epsilon = 1e-6 of the WENO-Z weights (Sec. 3.2, reading G22) fixes the
+    amplitude below which the fallback stays on the linear weights: a step of height delta
+    has beta ~ delta^2, so for delta = 1e-4 (beta ~ 1e-8, far below epsilon) the value is the
+    linear fifth-order one, 0.4 delta above the base (weights (2, -13, 47, 27, -3)/60 on
+    (0, 0, 0, 1, 1)), while for delta = 1e-2 (beta ~ 1e-4, far above epsilon) the weights are
+    non-oscillatory and the value stays on the smooth side of the step. A much smaller
+    epsilon makes both non-oscillatory; a much larger one makes both linear."""
+    base = 2.5
+    step = np.array([0, 0, 0, 1, 1.0])
+    for delta, expect, tol in ((1e-4, 0.4, 1e-3), (1e-5, 0.4, 1e-5), (1e-2, 0.0, 2e-3), (1.0, 0.0, 1e-9)):
+        out, beta = oracle.weno_ao53(base + delta * step, [1, 1, 1, 1], [0.0])
+        assert abs((out[0] - base) / delta - expect) < tol, (delta, (out[0] - base) / delta)

@@ -80,16 +80,27 @@ def test_conservation_periodic(oracle, r):
         np.testing.assert_array_equal(Fy[:, 0, :], Fy[:, -1, :])
 
 
+def _rough_share(hist, r):
+    """Share of reconstructions that left the linear branches: the WENOZ-AO(5,3)+DF fallback
+    (order 3: the DF-damped quadratic)."""
+    return hist[5 if r == 3 else 3] / hist[:6].sum()
+
+
 @pytest.mark.parametrize("r", [5, 9])
-def test_transpose_symmetry(oracle, r):
-    """Swapping x <-> y together with u <-> v transposes the residual."""
+@pytest.mark.parametrize("sigma_scale", [0.5, 1.0])
+def test_transpose_symmetry(oracle, r, sigma_scale):
+    """Swapping x <-> y together with u <-> v transposes the residual. With face strengths
+    up to 1.0 the 4-face sums straddle sigma_thres = 2, so a large share of the
+    reconstructions take the WENOZ-AO(5,3)+DF fallback."""
     pb = P.Problem(ndim=2, nx=12, ny=12, order=r, bc=("periodic", "periodic", "outflow", "outflow"))
     pbt = pb.replace(bc=("outflow", "outflow", "periodic", "periodic"))
     W = P.white_noise(pb, 7)
-    sx, sy = P.random_sigma(pb, 7, 0.5)
+    sx, sy = P.random_sigma(pb, 7, sigma_scale)
     sy[-1, :] = sy[0, :]  # periodic in y for pbt's x
     Wt = np.ascontiguousarray(W[[0, 2, 1, 3]].transpose(0, 2, 1))
-    L, sxo, syo, *_ = oracle.residual(pb, W, sx, sy)
+    L, sxo, syo, *_, hist = oracle.residual(pb, W, sx, sy)
+    if sigma_scale == 1.0:
+        assert _rough_share(hist, r) > 0.3
     Lt, sxt, syt, *_ = oracle.residual(pbt, Wt, np.ascontiguousarray(sy.T), np.ascontiguousarray(sx.T))
     np.testing.assert_allclose(Lt, L[[0, 2, 1, 3]].transpose(0, 2, 1), rtol=0, atol=1e-12 * np.abs(L).max())
     np.testing.assert_allclose(sxt, syo.T, rtol=1e-12, atol=0)
@@ -97,15 +108,23 @@ def test_transpose_symmetry(oracle, r):
 
 @pytest.mark.parametrize("ndim", [1, 2])
 @pytest.mark.parametrize("r", [3, 5, 9])
-def test_mirror_symmetry(oracle, ndim, r):
+@pytest.mark.parametrize("sigma_scale", [0.45, 1.0])
+def test_mirror_symmetry(oracle, ndim, r, sigma_scale):
     """x -> -x with u -> -u mirrors the residual (the right state is the mirror image of
-    the left one)."""
-    pb = P.Problem(ndim=ndim, nx=15, ny=9, order=r, bc=("outflow",) * 4)
+    the left one). In 2D the mirror also reverses the tangential reconstruction of the
+    y-faces, which the oracle evaluates at the Gauss points directly (not through a mirrored
+    stencil); with face strengths up to 1.0 a large share of it takes the WENOZ-AO(5,3)+DF
+    fallback, whose weights are then pinned to treat beta3_{-1} and beta3_1 alike (reading
+    G5)."""
+    pb = P.Problem(ndim=ndim, nx=15 if ndim == 2 else 64, ny=9, order=r, bc=("outflow",) * 4)
     W = P.white_noise(pb, 11)
-    sx, sy = P.random_sigma(pb, 11, 0.45)
+    # order 3 sums two faces: strengths up to 2.0 straddle sigma_thres there
+    sx, sy = P.random_sigma(pb, 11, sigma_scale * (2.0 if r == 3 and sigma_scale == 1.0 else 1.0))
     Wm = W[:, :, ::-1].copy()
     Wm[1] *= -1
-    L, sxo, syo, *_ = oracle.residual(pb, W, sx, sy)
+    L, sxo, syo, *_, hist = oracle.residual(pb, W, sx, sy)
+    if sigma_scale == 1.0:
+        assert _rough_share(hist, r) > 0.3
     Lm, sxm, sym_, *_ = oracle.residual(pb, Wm, np.ascontiguousarray(sx[:, ::-1]), np.ascontiguousarray(sy[:, ::-1]))
     Lref = L[:, :, ::-1].copy()
     Lref[1] *= -1
