@@ -211,8 +211,8 @@ ase_df_status ase_df_get_repair_stats(ase_df_ctx* ctx, uint32_t* last_stage, uin
 /* Clears the device status word and sets the device time t. */
 ase_df_status ase_df_reset(ase_df_ctx* ctx, double t, void* stream);
 
-/* Message of the last error on this context (or of the last failed ase_df_init when
- * ctx is NULL). */
+/* Message of the last error on this context (or, when ctx is NULL, of the last failed
+ * ase_df_init or ase_df_residual_noalloc). */
 const char* ase_df_last_error(const ase_df_ctx* ctx);
 
 /* Kernel timing with CUDA events recorded on the launching stream around every sweep,
@@ -232,13 +232,19 @@ ase_df_status ase_df_profile_read(ase_df_ctx* ctx, double* ms, int64_t* n);
  * It takes no context: the face-flux scratch is one file-scope __device__ array of
  * 2^21 doubles (16 MiB, held by every GPU that loads the library until exit), so it
  * calls no cudaMalloc / cudaFree and no allocating library routine.  Arguments as
- * ase_df_residual plus the problem p.  Limit: C*ny*(nx+1) + C*(ny+1)*nx (2D) or
- * 3*(nx+1) (1D) face-flux doubles <= 2^21 - 32, e.g. 2D grids up to 511 x 511; larger
- * grids return ASE_DF_E_BOUNDS.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress with that device current): make it before any
- * stream capture.  All calls share the array, which keeps the last call's contents:
- * calls that overlap on the GPU race and must not be issued.  Device-side conditions
- * (status flags) are not reported; errors are the returned status only. */
+ * ase_df_residual plus the problem p, validated exactly as ase_df_init validates it;
+ * the results equal ase_df_residual's bit for bit.  Every boundary of ase_df_bc is
+ * accepted except ASE_DF_BC_MOVING_SHOCK, which needs the solver time that only a
+ * context holds (ASE_DF_E_INVAL).  Limit: C*ny*(nx+1) + C*(ny+1)*nx (2D) or 3*(nx+1)
+ * (1D) face-flux doubles <= 2^21 - 32, e.g. 2D grids up to 511 x 511; larger grids
+ * return ASE_DF_E_BOUNDS.  Each call outside stream capture looks up the array's device
+ * address (cudaGetSymbolAddress, with the caller's device current; this also follows the
+ * array to a new address after cudaDeviceReset); a call during capture uses the address
+ * found by an earlier call on that device, so make one call on each device before
+ * capturing (otherwise ASE_DF_E_INVAL).  All calls share the array, which keeps the last
+ * call's contents: calls that overlap on the GPU race and must not be issued.
+ * Device-side conditions (status flags) are not reported.  On failure the message is
+ * in ase_df_last_error(NULL) (one process-wide buffer, shared with ase_df_init). */
 ase_df_status ase_df_residual_noalloc(const ase_df_params* p, const double* W, const double* sx_in,
                                       const double* sy_in, double* L, double* sx_out, double* sy_out,
                                       void* stream);

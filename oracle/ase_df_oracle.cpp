@@ -70,6 +70,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 // ---------------------------------------------------------------------------------
@@ -795,6 +796,38 @@ void face_fluxes(const Grid& g, const real* Wd, const real* sx_in, const real* s
   }
 }
 
+// Host threads for the face loops of the plain build: 1 unless oracle_set_threads says
+// otherwise (the operation-counting and tape builds stay serial).  The lines of a
+// direction are dealt out in contiguous blocks, one per thread; every face is computed
+// by the same code from the same inputs whatever the split, so the results do not
+// depend on it (tests/test_oracle_threads.py checks this bit for bit).
+int g_threads = 1;
+
+void face_fluxes_lines(const Grid& g, const real* Wd, const real* sx_in, const real* sy_in, int dir,
+                       real* Fout, real* sig_out, int64_t* hist, int64_t f_lo, int64_t f_hi,
+                       int64_t b_lo, int64_t b_hi) {
+  const int64_t nb = b_hi - b_lo + 1;
+  int T = g_threads;
+#if defined(ORACLE_COUNT_OPS) || defined(ORACLE_TAPE)
+  T = 1;
+#endif
+  if (T > nb) T = (int)nb;
+  if (T <= 1) {
+    face_fluxes(g, Wd, sx_in, sy_in, dir, Fout, sig_out, hist, f_lo, f_hi, b_lo, b_hi);
+    return;
+  }
+  std::vector<int64_t> h((size_t)T * BR_COUNT, 0);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < T; ++t) {
+    const int64_t lo = b_lo + nb * t / T, hi = b_lo + nb * (t + 1) / T - 1;
+    pool.emplace_back(face_fluxes, std::cref(g), Wd, sx_in, sy_in, dir, Fout, sig_out, &h[(size_t)t * BR_COUNT],
+                      f_lo, f_hi, lo, hi);
+  }
+  for (auto& th : pool) th.join();
+  for (int t = 0; t < T; ++t)
+    for (int b = 0; b < BR_COUNT; ++b) hist[b] += h[(size_t)t * BR_COUNT + b];
+}
+
 // Sec. 2.1, Eq. (2.3): L = -(1/|Omega|) sum over faces |l| * (Gauss-averaged flux . n).
 // Rows row_lo..row_hi of L (all rows: 0..ny-1); sigma_out and the face fluxes are
 // written for the faces those rows need.
@@ -806,10 +839,10 @@ int residual(const OracleParams* p, const real* W, const real* sx_in, const real
   const int64_t nx = g.nx, ny = g.ny;
   std::vector<real> Fx((size_t)(C * ny * (nx + 1)));
   std::vector<real> Fy;
-  face_fluxes(g, W, sx_in, sy_in, 0, Fx.data(), sx_out, hist, 0, nx, row_lo, row_hi);
+  face_fluxes_lines(g, W, sx_in, sy_in, 0, Fx.data(), sx_out, hist, 0, nx, row_lo, row_hi);
   if (p->ndim == 2) {
     Fy.resize((size_t)(C * (ny + 1) * nx));
-    face_fluxes(g, W, sx_in, sy_in, 1, Fy.data(), sy_out, hist, row_lo, row_hi + 1, 0, nx - 1);
+    face_fluxes_lines(g, W, sx_in, sy_in, 1, Fy.data(), sy_out, hist, row_lo, row_hi + 1, 0, nx - 1);
   }
   for (int c = 0; c < C; ++c)
     for (int64_t j = row_lo; j <= row_hi; ++j)
@@ -887,6 +920,14 @@ double max_speed(const OracleParams* p, const double* W, int* bad) {
 extern "C" {
 
 int oracle_version() { return 1; }
+
+// Host threads for the face loops of the plain build (n >= 1; the default is 1).
+// Returns the previous setting.
+int oracle_set_threads(int n) {
+  const int old = g_threads;
+  g_threads = n < 1 ? 1 : n;
+  return old;
+}
 
 // One residual evaluation.  hist[BR_COUNT] accumulates branch counts (may be NULL);
 // Fx / Fy (may be NULL) receive the Gauss-averaged face fluxes.

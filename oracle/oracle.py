@@ -30,7 +30,7 @@ BRANCHES = ("lin9", "lin7", "lin5", "weno_df", "lin3", "df3", "first_order", "re
 def _compile(out: str, extra=()) -> None:
     os.makedirs(_BUILD, exist_ok=True)
     tmp = out + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
            *extra, _SRC, "-o", tmp]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
@@ -87,6 +87,8 @@ def _setup(lib):
     lib.oracle_gauss01.restype = None
     lib.oracle_lf_flux.argtypes = [ctypes.c_int, ctypes.c_double, _P, _P, _P, _P, _P, _P]
     lib.oracle_lf_flux.restype = ctypes.c_int
+    lib.oracle_set_threads.argtypes = [ctypes.c_int]
+    lib.oracle_set_threads.restype = ctypes.c_int
     return lib
 
 
@@ -146,6 +148,26 @@ def _ptr(a: Optional[np.ndarray]):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def set_threads(n: int) -> int:
+    """Host threads for the face loops of the plain build (default 1; the results do not
+    depend on it).  Returns the previous setting."""
+    return _lib().oracle_set_threads(int(n))
+
+
+class threads:
+    """Context manager: run the plain oracle's face loops on n host threads."""
+
+    def __init__(self, n: int):
+        self.n = n
+
+    def __enter__(self):
+        self.old = set_threads(self.n)
+        return self
+
+    def __exit__(self, *exc):
+        set_threads(self.old)
 
 
 def residual(pb, W, sx, sy, counting: bool = False, t: float = 0.0):

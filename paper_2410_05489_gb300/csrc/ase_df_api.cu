@@ -127,61 +127,130 @@ static void to_conservative(const double* q, double gamma, int C, double* out) {
   }
 }
 
-extern "C" {
+namespace asedf {
 
-ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
-  if (!out) return fail(nullptr, ASE_DF_E_INVAL, "out is NULL");
-  *out = nullptr;
-  if (!pin) return fail(nullptr, ASE_DF_E_INVAL, "params is NULL");
+char* init_error_buffer() { return g_init_err; }
+
+ase_df_status setup_problem(const ase_df_params* pin, ProblemSetup* out, char* err, size_t err_len) {
+  auto bad = [&](ase_df_status st, const char* fmt, auto... args) {
+    if (err && err_len) snprintf(err, err_len, fmt, args...);
+    return st;
+  };
+  if (!pin) return bad(ASE_DF_E_INVAL, "params is NULL");
   ase_df_params p = *pin;
-  if (p.ndim != 1 && p.ndim != 2) return fail(nullptr, ASE_DF_E_INVAL, "ndim must be 1 or 2 (got %d)", p.ndim);
+  if (p.ndim != 1 && p.ndim != 2) return bad(ASE_DF_E_INVAL, "ndim must be 1 or 2 (got %d)", p.ndim);
   if (p.order != 3 && p.order != 5 && p.order != 7 && p.order != 9)
-    return fail(nullptr, ASE_DF_E_INVAL, "order must be 3, 5, 7 or 9 (got %d)", p.order);
+    return bad(ASE_DF_E_INVAL, "order must be 3, 5, 7 or 9 (got %d)", p.order);
   if (p.ndim == 1) p.ny = 1;
-  if (p.nx < 1 || p.ny < 1) return fail(nullptr, ASE_DF_E_INVAL, "nx, ny must be >= 1");
-  if (p.nx > (1 << 20) || p.ny > (1 << 20)) return fail(nullptr, ASE_DF_E_BOUNDS, "nx, ny must be <= 2^20");
+  if (p.nx < 1 || p.ny < 1) return bad(ASE_DF_E_INVAL, "nx, ny must be >= 1");
+  if (p.nx > (1 << 20) || p.ny > (1 << 20)) return bad(ASE_DF_E_BOUNDS, "nx, ny must be <= 2^20");
   const int C = (p.ndim == 1) ? 3 : 4;
   if ((double)C * (double)(p.nx + 1) * (double)(p.ny + 1) >= 2147483648.0)
-    return fail(nullptr, ASE_DF_E_BOUNDS, "C*(nx+1)*(ny+1) must be < 2^31");
-  if (!(p.x1 > p.x0) || (p.ndim == 2 && !(p.y1 > p.y0)))
-    return fail(nullptr, ASE_DF_E_INVAL, "empty domain");
-  if (!(p.gamma > 1.0) || !std::isfinite(p.gamma)) return fail(nullptr, ASE_DF_E_INVAL, "gamma must be > 1");
-  if (!(p.sigma_thres > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "sigma_thres must be > 0");
-  if (!(p.cfl > 0.0)) return fail(nullptr, ASE_DF_E_INVAL, "cfl must be > 0");
+    return bad(ASE_DF_E_BOUNDS, "C*(nx+1)*(ny+1) must be < 2^31");
+  if (!(p.x1 > p.x0) || (p.ndim == 2 && !(p.y1 > p.y0))) return bad(ASE_DF_E_INVAL, "empty domain");
+  if (!(p.gamma > 1.0) || !std::isfinite(p.gamma)) return bad(ASE_DF_E_INVAL, "gamma must be > 1");
+  if (!(p.sigma_thres > 0.0)) return bad(ASE_DF_E_INVAL, "sigma_thres must be > 0");
+  if (!(p.cfl > 0.0)) return bad(ASE_DF_E_INVAL, "cfl must be > 0");
   for (int s = 0; s < 4; ++s) {
-    if (p.bc[s] < 0 || p.bc[s] > 5) return fail(nullptr, ASE_DF_E_INVAL, "bad boundary code %d", p.bc[s]);
+    if (p.bc[s] < 0 || p.bc[s] > 5) return bad(ASE_DF_E_INVAL, "bad boundary code %d", p.bc[s]);
     if (p.bc[s] == ASE_DF_BC_INFLOW_BAND && s != 0)
-      return fail(nullptr, ASE_DF_E_INVAL, "the inflow band is supported on x-lo only");
+      return bad(ASE_DF_E_INVAL, "the inflow band is supported on x-lo only");
     if (p.bc[s] == ASE_DF_BC_WALL_AFTER && (s != 2 || p.ndim != 2))
-      return fail(nullptr, ASE_DF_E_INVAL, "the split wall is supported on y-lo of a 2D grid only");
+      return bad(ASE_DF_E_INVAL, "the split wall is supported on y-lo of a 2D grid only");
     if (p.bc[s] == ASE_DF_BC_MOVING_SHOCK && (s != 3 || p.ndim != 2))
-      return fail(nullptr, ASE_DF_E_INVAL, "the moving-shock boundary is supported on y-hi of a 2D grid only");
+      return bad(ASE_DF_E_INVAL, "the moving-shock boundary is supported on y-hi of a 2D grid only");
     if (p.ndim == 1 && s >= 2) p.bc[s] = ASE_DF_BC_OUTFLOW;
   }
   {
     const int64_t need = (p.order + 1) / 2;
     if ((p.bc[0] == ASE_DF_BC_REFLECT || p.bc[1] == ASE_DF_BC_REFLECT) && p.nx < need)
-      return fail(nullptr, ASE_DF_E_INVAL, "a reflecting x-wall needs nx >= %lld", (long long)need);
+      return bad(ASE_DF_E_INVAL, "a reflecting x-wall needs nx >= %lld", (long long)need);
     if (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_REFLECT || p.bc[3] == ASE_DF_BC_REFLECT ||
                         p.bc[2] == ASE_DF_BC_WALL_AFTER) && p.ny < need)
-      return fail(nullptr, ASE_DF_E_INVAL, "a reflecting y-wall needs ny >= %lld", (long long)need);
+      return bad(ASE_DF_E_INVAL, "a reflecting y-wall needs ny >= %lld", (long long)need);
   }
   if ((p.bc[0] == ASE_DF_BC_PERIODIC) != (p.bc[1] == ASE_DF_BC_PERIODIC))
-    return fail(nullptr, ASE_DF_E_INVAL, "periodic boundaries must come in pairs (x)");
+    return bad(ASE_DF_E_INVAL, "periodic boundaries must come in pairs (x)");
   if (p.ndim == 2 && (p.bc[2] == ASE_DF_BC_PERIODIC) != (p.bc[3] == ASE_DF_BC_PERIODIC))
-    return fail(nullptr, ASE_DF_E_INVAL, "periodic boundaries must come in pairs (y)");
+    return bad(ASE_DF_E_INVAL, "periodic boundaries must come in pairs (y)");
   const bool uses_inflow = p.bc[0] == ASE_DF_BC_INFLOW_BAND || p.bc[2] == ASE_DF_BC_WALL_AFTER ||
                            p.bc[3] == ASE_DF_BC_MOVING_SHOCK;
   if (uses_inflow && !(p.inflow_state[0] > 0.0 && p.inflow_state[3] > 0.0))
-    return fail(nullptr, ASE_DF_E_INVAL, "inflow state must have rho > 0 and p > 0");
+    return bad(ASE_DF_E_INVAL, "inflow state must have rho > 0 and p > 0");
   if (p.bc[3] == ASE_DF_BC_MOVING_SHOCK) {
     if (!(p.state_b[0] > 0.0 && p.state_b[3] > 0.0))
-      return fail(nullptr, ASE_DF_E_INVAL, "state_b must have rho > 0 and p > 0");
+      return bad(ASE_DF_E_INVAL, "state_b must have rho > 0 and p > 0");
     if (!std::isfinite(p.shock_x0) || !std::isfinite(p.shock_speed))
-      return fail(nullptr, ASE_DF_E_INVAL, "shock_x0 and shock_speed must be finite");
+      return bad(ASE_DF_E_INVAL, "shock_x0 and shock_speed must be finite");
   }
   if (p.bc[2] == ASE_DF_BC_WALL_AFTER && !std::isfinite(p.wall_x))
-    return fail(nullptr, ASE_DF_E_INVAL, "wall_x must be finite");
+    return bad(ASE_DF_E_INVAL, "wall_x must be finite");
+
+  ProblemSetup& o = *out;
+  o = ProblemSetup{};
+  o.p = p;
+  o.C = C;
+  o.K = (p.order - 1) / 2;
+  o.dx = (p.x1 - p.x0) / (double)p.nx;
+  o.dy = (p.ndim == 2) ? (p.y1 - p.y0) / (double)p.ny : 1.0;
+  o.inv_dx = 1.0 / o.dx;
+  o.inv_dy = (p.ndim == 2) ? 1.0 / o.dy : 0.0;
+  o.inflow_speed = 0.0;
+  GridInfo& g = o.g;
+  g.nx = (int)p.nx;
+  g.ny = (int)p.ny;
+  for (int s = 0; s < 4; ++s) g.bc[s] = p.bc[s];
+  g.band_j0 = 1;
+  g.band_j1 = 0;  // empty
+  if (p.bc[0] == ASE_DF_BC_INFLOW_BAND) {
+    // rows whose centre y0 + (j + 1/2) dy lies strictly inside (inflow_lo, inflow_hi)
+    int j0 = -1, j1 = -2;
+    for (int j = 0; j < g.ny; ++j) {
+      const double yc = p.y0 + ((double)j + 0.5) * o.dy;
+      if (yc > p.inflow_lo && yc < p.inflow_hi) {
+        if (j0 < 0) j0 = j;
+        j1 = j;
+      }
+    }
+    if (j0 >= 0) { g.band_j0 = j0; g.band_j1 = j1; }
+    o.inflow_speed = sound_speed_sum(p, o.inv_dx, o.inv_dy);
+  }
+  if (uses_inflow) to_conservative(p.inflow_state, p.gamma, C, g.inflow_cons);
+  if (p.bc[3] == ASE_DF_BC_MOVING_SHOCK) to_conservative(p.state_b, p.gamma, C, g.state_b_cons);
+  g.x0 = p.x0;
+  g.dx = o.dx;
+  g.shock_x0 = p.shock_x0;
+  g.shock_speed = p.shock_speed;
+  if (p.bc[2] == ASE_DF_BC_WALL_AFTER) {
+    // the first column whose centre x0 + (i + 1/2) dx is at or past wall_x; ghost columns
+    // reach k + 1 cells beyond the grid, so the search is confined to that range
+    const int lo = -(o.K + 2), hi = g.nx + o.K + 2;
+    auto centre = [&](int i) { return p.x0 + ((double)i + 0.5) * o.dx; };
+    const double est = std::floor((p.wall_x - p.x0) / o.dx - 0.5) - 2.0;
+    int i0 = (int)std::max((double)lo, std::min((double)hi, est));
+    while (i0 > lo && centre(i0) >= p.wall_x) --i0;
+    while (i0 < hi && centre(i0) < p.wall_x) ++i0;
+    g.wall_i0 = i0;
+  }
+  g.gamma = p.gamma;
+  g.thres = p.sigma_thres;
+  return ASE_DF_OK;
+}
+
+}  // namespace asedf
+
+extern "C" {
+
+ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
+  if (!out) return fail(nullptr, ASE_DF_E_INVAL, "out is NULL");
+  *out = nullptr;
+  ProblemSetup ps;
+  {
+    const ase_df_status v = setup_problem(pin, &ps, g_init_err, sizeof(g_init_err));
+    if (v != ASE_DF_OK) return v;
+  }
+  const ase_df_params& p = ps.p;
+  const int C = ps.C;
 
   ase_df_ctx* c = new (std::nothrow) ase_df_ctx;
   if (!c) return fail(nullptr, ASE_DF_E_NOMEM, "host allocation failed");
@@ -196,50 +265,15 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
   }
   c->p = p;
   c->C = C;
-  c->K = (p.order - 1) / 2;
+  c->K = ps.K;
   c->dim = p.ndim;
-  c->dx = (p.x1 - p.x0) / (double)p.nx;
-  c->dy = (p.ndim == 2) ? (p.y1 - p.y0) / (double)p.ny : 1.0;
-  c->inv_dx = 1.0 / c->dx;
-  c->inv_dy = (p.ndim == 2) ? 1.0 / c->dy : 0.0;
-  GridInfo& g = c->g;
-  g.nx = (int)p.nx;
-  g.ny = (int)p.ny;
-  for (int s = 0; s < 4; ++s) g.bc[s] = p.bc[s];
-  g.band_j0 = 1;
-  g.band_j1 = 0;  // empty
-  if (p.bc[0] == ASE_DF_BC_INFLOW_BAND) {
-    // rows whose centre y0 + (j + 1/2) dy lies strictly inside (inflow_lo, inflow_hi)
-    int j0 = -1, j1 = -2;
-    for (int j = 0; j < g.ny; ++j) {
-      const double yc = p.y0 + ((double)j + 0.5) * c->dy;
-      if (yc > p.inflow_lo && yc < p.inflow_hi) {
-        if (j0 < 0) j0 = j;
-        j1 = j;
-      }
-    }
-    if (j0 >= 0) { g.band_j0 = j0; g.band_j1 = j1; }
-    c->inflow_speed = sound_speed_sum(p, c->inv_dx, c->inv_dy);
-  }
-  if (uses_inflow) to_conservative(p.inflow_state, p.gamma, C, g.inflow_cons);
-  if (p.bc[3] == ASE_DF_BC_MOVING_SHOCK) to_conservative(p.state_b, p.gamma, C, g.state_b_cons);
-  g.x0 = p.x0;
-  g.dx = c->dx;
-  g.shock_x0 = p.shock_x0;
-  g.shock_speed = p.shock_speed;
-  if (p.bc[2] == ASE_DF_BC_WALL_AFTER) {
-    // the first column whose centre x0 + (i + 1/2) dx is at or past wall_x; ghost columns
-    // reach k + 1 cells beyond the grid, so the search is confined to that range
-    const int lo = -(c->K + 2), hi = g.nx + c->K + 2;
-    auto centre = [&](int i) { return p.x0 + ((double)i + 0.5) * c->dx; };
-    const double est = std::floor((p.wall_x - p.x0) / c->dx - 0.5) - 2.0;
-    int i0 = (int)std::max((double)lo, std::min((double)hi, est));
-    while (i0 > lo && centre(i0) >= p.wall_x) --i0;
-    while (i0 < hi && centre(i0) < p.wall_x) ++i0;
-    g.wall_i0 = i0;
-  }
-  g.gamma = p.gamma;
-  g.thres = p.sigma_thres;
+  c->dx = ps.dx;
+  c->dy = ps.dy;
+  c->inv_dx = ps.inv_dx;
+  c->inv_dy = ps.inv_dy;
+  c->inflow_speed = ps.inflow_speed;
+  c->g = ps.g;
+  const GridInfo& g = c->g;
   build_tables(p.order, p.ndim, &c->tab);
   build_dtables(p.order, p.ndim, &c->dtab);
 

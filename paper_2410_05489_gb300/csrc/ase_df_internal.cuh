@@ -11,6 +11,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/ase_df.h"
+
 namespace asedf {
 
 // Raises a kernel's dynamic shared-memory limit once per device (the attribute belongs to
@@ -162,6 +164,24 @@ struct SpeedArgs {
   double inv_dx, inv_dy;
 };
 
+// A validated problem and what the kernels derive from it; shared by ase_df_init and
+// ase_df_residual_noalloc, so that both accept the same problems and describe them to the
+// kernels identically.
+struct ProblemSetup {
+  ase_df_params p;       // normalised: ny = 1 and outflow y-sides in 1D
+  int C, K;              // components, stencil half-width (r - 1) / 2
+  double dx, dy, inv_dx, inv_dy;
+  double inflow_speed;   // (|u|+c)/dx (+ (|v|+c)/dy) of the inflow band's state, else 0
+  GridInfo g;
+};
+
+// Validates *p and fills *out (host arithmetic only, no allocation).  On failure returns
+// the status and writes a message into err[0 .. err_len) (err may be NULL).
+ase_df_status setup_problem(const ase_df_params* p, ProblemSetup* out, char* err, size_t err_len);
+
+// The process-wide message buffer that ase_df_last_error(NULL) returns (512 bytes).
+char* init_error_buffer();
+
 // Host-side launchers, one set per scheme order (ase_df_sweep.cu is compiled once per
 // order).  dim = 1 or 2; dir = 0 (x-faces) or 1 (y-faces).
 cudaError_t launch_sweep_r3(int dim, int dir, const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s);
@@ -175,8 +195,9 @@ cudaError_t launch_repair(int dim, const GridInfo& g, const RepairArgs& a, cudaS
 cudaError_t launch_freeze(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s);
 cudaError_t launch_state_kernel(DevState* st, int op, double t, cudaStream_t s);
 
-// Tables of scheme order r (host, exact rational arithmetic).
-void build_tables(int r, int ndim, Tables* out);
-void build_dtables(int r, int ndim, DTables* out);
+// Tables of scheme order r (host, exact rational arithmetic, no allocation); false only if a
+// moment matrix were singular, which the fixed stencils rule out.
+bool build_tables(int r, int ndim, Tables* out);
+bool build_dtables(int r, int ndim, DTables* out);
 
 }  // namespace asedf

@@ -7,13 +7,12 @@
 // p's coefficients are c = M^{-1} W, so the value at a point xi is
 // sum_i (sum_q xi^q M^{-1}[q][i]) W_i.  M^{-1} is computed exactly with 128-bit
 // rationals; point weights at rational points are exact, at the irrational Gauss
-// points they are summed in long double and rounded once.
+// points they are summed in long double and rounded once.  Nothing here allocates
+// (fixed-size arrays on the stack), so every entry point may call it.
 
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <stdexcept>
-#include <vector>
 
 #include "ase_df_internal.cuh"
 
@@ -56,11 +55,17 @@ i128 ipow(i128 b, int e) {
   return r;
 }
 
-// Inverse of the moment matrix of the cells with the given offsets:
-// inv[q][i] = coefficient of xi^q contributed by a unit average in cell i.
-std::vector<std::vector<Rat>> moment_inverse(const std::vector<int>& offs) {
-  const int n = (int)offs.size();
-  std::vector<std::vector<Rat>> A(n, std::vector<Rat>(2 * n));
+// Inverse of the moment matrix of n <= 9 cells with the given offsets:
+// inv.m[q][i] = coefficient of xi^q contributed by a unit average in cell i.  Fixed-size
+// arrays only (no heap), so that the no-allocation residual can build its tables too.
+struct Inverse {
+  int n;
+  Rat m[9][9];
+};
+
+bool moment_inverse(const int* offs, int n, Inverse* inv) {
+  if (n < 1 || n > 9) return false;
+  Rat A[9][18];
   for (int i = 0; i < n; ++i) {
     for (int q = 0; q < n; ++q) {
       i128 o = offs[i];
@@ -71,8 +76,12 @@ std::vector<std::vector<Rat>> moment_inverse(const std::vector<int>& offs) {
   for (int col = 0; col < n; ++col) {
     int piv = col;
     while (piv < n && A[piv][col].n == 0) ++piv;
-    if (piv == n) throw std::runtime_error("singular moment matrix");
-    std::swap(A[piv], A[col]);
+    if (piv == n) return false;  // singular (cannot happen for distinct offsets)
+    for (int j = 0; j < 2 * n; ++j) {
+      Rat t = A[piv][j];
+      A[piv][j] = A[col][j];
+      A[col][j] = t;
+    }
     Rat pv = A[col][col];
     for (int j = 0; j < 2 * n; ++j) A[col][j] = dvd(A[col][j], pv);
     for (int r = 0; r < n; ++r) {
@@ -82,10 +91,17 @@ std::vector<std::vector<Rat>> moment_inverse(const std::vector<int>& offs) {
     }
   }
   // A = [I | M^{-1}] with rows indexed by q (the unknown) after elimination
-  std::vector<std::vector<Rat>> inv(n, std::vector<Rat>(n));
+  inv->n = n;
   for (int q = 0; q < n; ++q)
-    for (int i = 0; i < n; ++i) inv[q][i] = A[q][n + i];
-  return inv;
+    for (int i = 0; i < n; ++i) inv->m[q][i] = A[q][n + i];
+  return true;
+}
+
+// Centred stencil of 2h+1 cells.
+bool centred_inverse(int h, Inverse* inv) {
+  int offs[9];
+  for (int i = 0; i < 2 * h + 1; ++i) offs[i] = i - h;
+  return moment_inverse(offs, 2 * h + 1, inv);
 }
 
 // Gauss-Legendre nodes/weights on [0, 1] by Newton iteration on P_G (three-term
@@ -116,69 +132,68 @@ void gauss_legendre(int G, long double* t, long double* w) {
 
 // Value weights of the polynomial of the given stencil at point xi (exact for rational
 // xi given as a Rat, else long double).
-void point_weights_rat(const std::vector<std::vector<Rat>>& inv, Rat xi, double* w) {
-  const int n = (int)inv.size();
+void point_weights_rat(const Inverse& inv, Rat xi, double* w) {
+  const int n = inv.n;
   for (int i = 0; i < n; ++i) {
     Rat s = mk(0, 1);
     Rat xp = mk(1, 1);
     for (int q = 0; q < n; ++q) {
-      s = add(s, mul(xp, inv[q][i]));
+      s = add(s, mul(xp, inv.m[q][i]));
       xp = mul(xp, xi);
     }
     w[i] = to_d(s);
   }
 }
 
-void point_weights_ld(const std::vector<std::vector<Rat>>& inv, long double xi, double* w) {
-  const int n = (int)inv.size();
+void point_weights_ld(const Inverse& inv, long double xi, double* w) {
+  const int n = inv.n;
   for (int i = 0; i < n; ++i) {
     long double s = 0;
-    for (int q = n - 1; q >= 0; --q) s = s * xi + to_ld(inv[q][i]);  // Horner
+    for (int q = n - 1; q >= 0; --q) s = s * xi + to_ld(inv.m[q][i]);  // Horner
     w[i] = (double)s;
   }
 }
 
 // Derivative weights d/dxi of the polynomial at point xi: sum_q q xi^(q-1) inv[q][i].
-void deriv_weights_rat(const std::vector<std::vector<Rat>>& inv, Rat xi, double* w) {
-  const int n = (int)inv.size();
+void deriv_weights_rat(const Inverse& inv, Rat xi, double* w) {
+  const int n = inv.n;
   for (int i = 0; i < n; ++i) {
     Rat s = mk(0, 1);
     Rat xp = mk(1, 1);
     for (int q = 1; q < n; ++q) {
-      s = add(s, mul(mul(mk(q, 1), xp), inv[q][i]));
+      s = add(s, mul(mul(mk(q, 1), xp), inv.m[q][i]));
       xp = mul(xp, xi);
     }
     w[i] = to_d(s);
   }
 }
 
-void deriv_weights_ld(const std::vector<std::vector<Rat>>& inv, long double xi, double* w) {
-  const int n = (int)inv.size();
+void deriv_weights_ld(const Inverse& inv, long double xi, double* w) {
+  const int n = inv.n;
   for (int i = 0; i < n; ++i) {
     long double s = 0;
-    for (int q = n - 1; q >= 1; --q) s = s * xi + (long double)q * to_ld(inv[q][i]);  // Horner
+    for (int q = n - 1; q >= 1; --q) s = s * xi + (long double)q * to_ld(inv.m[q][i]);  // Horner
     w[i] = (double)s;
   }
 }
 
 }  // namespace
 
-void build_dtables(int r, int ndim, DTables* D) {
+bool build_dtables(int r, int ndim, DTables* D) {
   std::memset(D, 0, sizeof(DTables));
   const int G = (ndim == 2) ? (r == 3 ? 1 : (r - 1) / 2) : 1;
   long double gt[4], gwt[4];
   gauss_legendre(G, gt, gwt);
   const int npts = 2 + G;
-  auto eval_all = [&](const std::vector<std::vector<Rat>>& inv, int p, double* w) {
+  auto eval_all = [&](const Inverse& inv, int p, double* w) {
     if (p == 0) deriv_weights_rat(inv, mk(0, 1), w);
     else if (p == 1) deriv_weights_rat(inv, mk(-1, 1), w);
     else deriv_weights_ld(inv, gt[p - 2] - 1.0L, w);
   };
+  Inverse inv;
   for (int b = 0; b < 4; ++b) {
     const int h = b + 1;
-    std::vector<int> offs;
-    for (int o = -h; o <= h; ++o) offs.push_back(o);
-    auto inv = moment_inverse(offs);
+    if (!centred_inverse(h, &inv)) return false;
     for (int p = 0; p < npts; ++p) {
       double w[9];
       eval_all(inv, p, w);
@@ -186,13 +201,14 @@ void build_dtables(int r, int ndim, DTables* D) {
     }
   }
   for (int k = 0; k < 3; ++k) {
-    std::vector<int> offs = {k - 2, k - 1, k};
-    auto inv = moment_inverse(offs);
+    const int offs[3] = {k - 2, k - 1, k};
+    if (!moment_inverse(offs, 3, &inv)) return false;
     for (int p = 0; p < npts; ++p) eval_all(inv, p, D->dsub[k][p]);
   }
+  return true;
 }
 
-void build_tables(int r, int ndim, Tables* T) {
+bool build_tables(int r, int ndim, Tables* T) {
   std::memset(T, 0, sizeof(Tables));
   const int G = (ndim == 2) ? (r == 3 ? 1 : (r - 1) / 2) : 1;
   long double gt[4], gwt[4];
@@ -203,18 +219,17 @@ void build_tables(int r, int ndim, Tables* T) {
   }
   const int npts = 2 + G;
 
-  auto eval_all = [&](const std::vector<std::vector<Rat>>& inv, int p, double* w) {
+  auto eval_all = [&](const Inverse& inv, int p, double* w) {
     if (p == 0) point_weights_rat(inv, mk(0, 1), w);
     else if (p == 1) point_weights_rat(inv, mk(-1, 1), w);
     else point_weights_ld(inv, gt[p - 2] - 1.0L, w);
   };
 
+  Inverse inv;
   // centred stencils of 3, 5, 7, 9 cells
   for (int b = 0; b < 4; ++b) {
     const int h = b + 1;
-    std::vector<int> offs;
-    for (int o = -h; o <= h; ++o) offs.push_back(o);
-    auto inv = moment_inverse(offs);
+    if (!centred_inverse(h, &inv)) return false;
     for (int p = 0; p < npts; ++p) {
       double w[9];
       eval_all(inv, p, w);
@@ -225,15 +240,13 @@ void build_tables(int r, int ndim, Tables* T) {
   // (the reflection about the cell centre maps eta to -1 - eta and W_t to W_-t)
   {
     const int h = (r - 1) / 2;
-    std::vector<int> offs;
-    for (int o = -h; o <= h; ++o) offs.push_back(o);
-    auto inv = moment_inverse(offs);
+    if (!centred_inverse(h, &inv)) return false;
     for (int g = 0; g < (G + 1) / 2 && g < 2; ++g) {
       long double w[9];
       const long double xi = gt[g] - 1.0L;
       for (int i = 0; i < 2 * h + 1; ++i) {
         long double sacc = 0;
-        for (int q = 2 * h; q >= 0; --q) sacc = sacc * xi + to_ld(inv[q][i]);
+        for (int q = 2 * h; q >= 0; --q) sacc = sacc * xi + to_ld(inv.m[q][i]);
         w[i] = sacc;
       }
       T->se[g][0] = (double)w[h];
@@ -245,11 +258,11 @@ void build_tables(int r, int ndim, Tables* T) {
   }
   // 3-cell sub-stencils S3_{-1}, S3_0, S3_1
   for (int k = 0; k < 3; ++k) {
-    std::vector<int> offs = {k - 2, k - 1, k};
-    auto inv = moment_inverse(offs);
+    const int offs[3] = {k - 2, k - 1, k};
+    if (!moment_inverse(offs, 3, &inv)) return false;
     for (int p = 0; p < npts; ++p) eval_all(inv, p, T->sub[k][p]);
     for (int q = 0; q < 2; ++q)
-      for (int j = 0; j < 3; ++j) T->cq[k][q][j] = to_d(inv[q + 1][j]);
+      for (int j = 0; j < 3; ++j) T->cq[k][q][j] = to_d(inv.m[q + 1][j]);
   }
   // Sec. 3.2: d5 = d_Hi, d3_{+-1} = (1-d_Hi)(1-d_Lo)/2, d3_0 = (1-d_Hi) d_Lo with
   // d_Hi = d_Lo = 0.85 (exact decimal values rounded once)
@@ -258,6 +271,7 @@ void build_tables(int r, int ndim, Tables* T) {
   T->d3[1] = to_d(mk(15 * 85, 100 * 100));
   T->d3[2] = T->d3[0];
   T->eps = 1e-6;
+  return true;
 }
 
 }  // namespace asedf

@@ -6,6 +6,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+TESTS = os.path.dirname(os.path.abspath(__file__))
+if TESTS not in sys.path:
+    sys.path.insert(0, TESTS)
 
 
 def pytest_configure(config):
@@ -30,3 +33,13 @@ def golden():
             return json.load(f)
 
     return load
+
+
+def pytest_terminal_summary(terminalreporter):
+    import parity_report
+
+    lines = parity_report.summary_lines()
+    if lines:
+        terminalreporter.write_sep("-", "parity: worst measured error / bound per test")
+        for line in lines:
+            terminalreporter.write_line(line)

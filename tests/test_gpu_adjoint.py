@@ -17,6 +17,7 @@ Tolerances:
 import numpy as np
 import pytest
 
+from parity_report import check
 from paper_2410_05489_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
@@ -105,7 +106,7 @@ def test_residual_adjoint_matches_oracle_tape(A, oracle, name):
         Wb, sxi, syi = s.residual_adjoint(dev(W), dev(sx), dev(sy), dev(Lbar), dev(sxb), dev(syb))
         torch.cuda.synchronize()
         floor = 1e-4 * np.abs(Lbar).max() * (1.0 / pb.dx + (1.0 / pb.dy if pb.ndim == 2 else 0.0))
-        assert rel_err(Wb.cpu().numpy(), Wb_cpu, floor) <= 1e-10
+        check("Wbar", rel_err(Wb.cpu().numpy(), Wb_cpu, floor), 1e-10)
         assert np.abs(sxi.cpu().numpy() - sxi_cpu).max() <= 1e-10 * max(np.abs(sxi_cpu).max(), floor)
         if pb.ndim == 2:
             assert np.abs(syi.cpu().numpy() - syi_cpu).max() <= 1e-10 * max(np.abs(syi_cpu).max(), floor)
@@ -177,11 +178,11 @@ def test_rollout_adjoint_matches_oracle_tape(A, oracle, case):
     try:
         W0t = dev(W0).requires_grad_(True)
         Wft = rollout(s, W0t, nsteps, dt, every=every)
-        assert rel_err(Wft.detach().cpu().numpy(), Wf) <= 1e-12
+        check("W final", rel_err(Wft.detach().cpu().numpy(), Wf), 1e-12)
         J = (Wft[0] ** 2).sum()
         (G,) = torch.autograd.grad(J, [W0t])
         G = G.cpu().numpy()
-        assert rel_err(G, G_cpu) <= 1e-9, rel_err(G, G_cpu)
+        check("gradient", rel_err(G, G_cpu), 1e-9)
     finally:
         s.close()
 

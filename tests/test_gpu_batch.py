@@ -3,6 +3,7 @@ dimension and order): same results as the one-problem path and as the oracle."""
 import numpy as np
 import pytest
 
+from parity_report import check
 from paper_2410_05489_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
@@ -58,7 +59,7 @@ def test_batch_matches_one_problem_path(B):
                 s.step()
             f1, dt1, t1 = s.status()
             assert abs(t[i] - t1) <= 1e-15 * t1 and flags[i] == f1
-            assert comp_err(bt.state(i), s.W.cpu().numpy()) <= 1e-13, i
+            check("W vs single", comp_err(bt.state(i), s.W.cpu().numpy()), 1e-13, i)
             s.close()
     finally:
         bt.close()
@@ -75,7 +76,7 @@ def test_batch_matches_oracle(B, oracle):
         for i, (pb, W) in enumerate(probs):
             Wc, _, _, tc, _ = oracle.run(pb, W, nsteps=5)
             assert abs(t[i] - tc) <= 1e-12 * tc
-            assert comp_err(bt.state(i), Wc) <= 1e-9, i
+            check("W vs oracle", comp_err(bt.state(i), Wc), 1e-9, i)
     finally:
         bt.close()
 
@@ -142,7 +143,7 @@ def test_full_batched_workload_sampled_problems(B, oracle):
             pb, W = probs[i]
             Wc, _, _, tc, _ = oracle.run(pb, W, nsteps=2)
             assert abs(t[i] - tc) <= 1e-12 * tc
-            assert comp_err(bt.state(i), Wc) <= 1e-9, i
+            check("W vs oracle", comp_err(bt.state(i), Wc), 1e-9, i)
         rng = np.random.default_rng(5)
         spread = list(rng.choice(len(probs), 6, replace=False)) + [int(np.argmax(size))]
         for i in spread:
@@ -150,7 +151,7 @@ def test_full_batched_workload_sampled_problems(B, oracle):
             s = A.Solver(pb, W)
             for _ in range(2):
                 s.step()
-            assert comp_err(bt.state(i), s.W.cpu().numpy()) <= 1e-13, i
+            check("W vs single", comp_err(bt.state(i), s.W.cpu().numpy()), 1e-13, i)
             s.close()
     finally:
         bt.close()

@@ -8,6 +8,7 @@ the paper shows this problem as a figure only."""
 import numpy as np
 import pytest
 
+from parity_report import check
 from paper_2410_05489_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
@@ -65,15 +66,15 @@ def test_residual_parity_at_several_times(A, oracle, r):
             s.set_time(t)
             Lg, sxg, syg = s.residual(dev(W), dev(sx), dev(sy))
             torch.cuda.synchronize()
-            assert comp_err(Lg.cpu().numpy(), L, floor_of(pb, Fx, Fy)) <= 1e-12
+            check("L", comp_err(Lg.cpu().numpy(), L, floor_of(pb, Fx, Fy)), 1e-12)
             assert sigma_ok(sxg.cpu().numpy(), sxo) and sigma_ok(syg.cpu().numpy(), syo)
             # the gas-kinetic face kernel sees the same boundaries
             dt = 0.5 * oracle.cfl_dt(pb, W)
             Lk, Ltk, *_ = oracle.gks_residual(pb, W, sx, sy, dt, t=t)
             Lkg, Ltkg, _, _ = s.gks_residual(dt, dev(W), dev(sx), dev(sy))
             fl = floor_of(pb, Fx, Fy)
-            assert comp_err(Lkg.cpu().numpy(), Lk, fl) <= 1e-11
-            assert comp_err(Ltkg.cpu().numpy(), Ltk, [f / dt for f in fl]) <= 1e-11
+            check("L (GKS)", comp_err(Lkg.cpu().numpy(), Lk, fl), 1e-11)
+            check("L_t (GKS)", comp_err(Ltkg.cpu().numpy(), Ltk, [f / dt for f in fl]), 1e-11)
     finally:
         s.close()
 
@@ -109,7 +110,7 @@ def test_steps_see_the_boundary_at_their_stage_times(A, oracle):
             flags, _, tg = s.status()
             assert flags & 1 == 0 and abs(tg - t) <= 1e-14 * t
             err = np.abs(s.W.cpu().numpy() - Wc).max() / np.abs(Wc).max()
-            assert err <= 1e-11, (gks, err)
+            check("W after steps", err, 1e-11, gks)
         finally:
             s.close()
 
@@ -138,7 +139,7 @@ def test_lax_friedrichs_run_to_t02_matches_the_oracle(A, oracle):
     rho = W[0]
     assert rho.min() > 1.0 and 8.0 < rho.max() < 30.0  # pre-shock 1.4; Mach stem and jet above 8
     Wc, *_ = oracle.run(pb, W0, t_end=0.2)
-    assert np.abs(rho - Wc[0]).mean() <= 1e-6 * np.abs(Wc[0]).mean()
+    check("rho L1 end state", np.abs(rho - Wc[0]).mean() / np.abs(Wc[0]).mean(), 1e-6)
 
 
 def test_gas_kinetic_run_matches_the_oracle(A, oracle):
@@ -146,7 +147,7 @@ def test_gas_kinetic_run_matches_the_oracle(A, oracle):
     W, flags, t = run_gpu(A, pb, W0, 0.03, gks=True)
     assert abs(t - 0.03) < 1e-12 and flags & 1 == 0
     Wc, *_ = oracle.gks_run(pb, W0, t_end=0.03)
-    assert np.abs(W[0] - Wc[0]).mean() <= 1e-6 * np.abs(Wc[0]).mean()
+    check("rho L1 end state", np.abs(W[0] - Wc[0]).mean() / np.abs(Wc[0]).mean(), 1e-6)
 
 
 @pytest.mark.parametrize("gks", [False, True])

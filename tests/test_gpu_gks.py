@@ -17,6 +17,7 @@ import math
 import numpy as np
 import pytest
 
+from parity_report import check
 from paper_2410_05489_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
@@ -92,8 +93,8 @@ def test_gks_residual_matches_oracle(A, oracle, name):
         _, _, _, Fx, Fy, _ = oracle.residual(pb, W, sx, sy)  # the flux scale (Lax-Friedrichs)
         inv = 1.0 / pb.dx + (1.0 / pb.dy if pb.ndim == 2 else 0.0)
         Fmax = max(np.abs(Fx).max(), np.abs(Fy).max() if Fy is not None else 0.0)
-        assert comp_err(Lg.cpu().numpy(), L, 1e-3 * Fmax * inv) <= 1e-11
-        assert comp_err(Ltg.cpu().numpy(), Lt, 1e-3 * Fmax * inv / dt) <= 1e-11
+        check("L (GKS)", comp_err(Lg.cpu().numpy(), L, 1e-3 * Fmax * inv), 1e-11)
+        check("L_t (GKS)", comp_err(Ltg.cpu().numpy(), Lt, 1e-3 * Fmax * inv / dt), 1e-11)
         for a, b in ((sxg.cpu().numpy(), sxo), (syg.cpu().numpy(), syo)):
             if pb.ndim == 1 and b is syo:
                 continue
@@ -121,7 +122,7 @@ def test_gks_steps_match_oracle(A, oracle, name, nsteps):
         torch.cuda.synchronize()
         assert flags & 1 == 0
         assert abs(tg - t) <= 1e-11 * t  # CFL dt from sqrt and division on both sides
-        assert comp_err(s.W.cpu().numpy(), Wc, 0.0) <= 1e-10
+        check("W after steps", comp_err(s.W.cpu().numpy(), Wc, 0.0), 1e-10)
     finally:
         s.close()
 

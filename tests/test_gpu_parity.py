@@ -27,6 +27,7 @@ reciprocal multiplications).
 import numpy as np
 import pytest
 
+from parity_report import check
 from paper_2410_05489_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
@@ -96,11 +97,10 @@ def gpu_residual(A, pb, W, sx, sy):
 def check_residual(A, oracle, pb, W, sx, sy):
     Lc, sxc, syc, Fxc, Fyc, hist = oracle.residual(pb, W, sx, sy)
     Lg, sxg, syg, Fxg, Fyg, _ = gpu_residual(A, pb, W, sx, sy)
-    assert comp_err(Fxg, Fxc) <= TOL_F
+    check("F_x", comp_err(Fxg, Fxc), TOL_F)
     if pb.ndim == 2:
-        assert comp_err(Fyg, Fyc) <= TOL_F
-    err = comp_err(Lg, Lc, residual_floor(pb, Fxc, Fyc))
-    assert err <= TOL_L, err
+        check("F_y", comp_err(Fyg, Fyc), TOL_F)
+    check("L", comp_err(Lg, Lc, residual_floor(pb, Fxc, Fyc)), TOL_L)
     check_sigma(sxg, sxc)
     if pb.ndim == 2:
         check_sigma(syg, syc)
@@ -275,8 +275,8 @@ def test_residual_parity_at_the_largest_1d_grid_white_noise(A, oracle):
     Lc, sxc, _, Fxc, _, hist = oracle.residual(pb, W, sx, sy)
     Lg, sxg, _, Fxg, _, _ = gpu_residual(A, pb, W, sx, sy)
     assert hist[3] > 0.3 * hist.sum()
-    assert comp_err(Fxg, Fxc) <= 1e-11
-    assert comp_err(Lg, Lc, residual_floor(pb, Fxc, None)) <= 1e-11
+    check("F_x", comp_err(Fxg, Fxc), 1e-11)
+    check("L", comp_err(Lg, Lc, residual_floor(pb, Fxc, None)), 1e-11)
     assert np.all(np.abs(sxg - sxc) <= 1e-11 * (1 + np.abs(sxc)) + 1e-13 * sxc * sxc)
 
 
@@ -335,7 +335,7 @@ def test_100_steps_parity_vortex(A, oracle, order):
     Wg, _, _, flags, _, t = run_gpu(A, pb, W, 100, dt)
     assert flags & A.FLAG_NONPHYSICAL == 0
     assert abs(t - 100 * dt) < 1e-12
-    assert comp_err(Wg, Wc) <= TOL_STEPS
+    check("W after steps", comp_err(Wg, Wc), TOL_STEPS)
 
 
 def test_100_steps_parity_sod_cfl(A, oracle):
@@ -344,7 +344,7 @@ def test_100_steps_parity_sod_cfl(A, oracle):
     Wc, sxc, _, tc, n = oracle.run(pb, W, nsteps=100)
     Wg, sxg, _, flags, _, t = run_gpu(A, pb, W, 100)
     assert abs(t - tc) <= 1e-12 * tc
-    assert comp_err(Wg, Wc) <= TOL_STEPS
+    check("W after steps", comp_err(Wg, Wc), TOL_STEPS)
 
 
 def test_graph_run_matches_steps(A):
@@ -381,7 +381,7 @@ def test_t_end_clamps_the_last_step(A, oracle):
     Wc, _, _, tc, n = oracle.run(pb, W, t_end=0.05)
     Wg, _, _, flags, _, t = run_gpu(A, pb, W, n + 3, t_end=0.05)  # extra steps are no-ops
     assert abs(t - 0.05) < 1e-15 and abs(tc - 0.05) < 1e-15
-    assert comp_err(Wg, Wc) <= TOL_STEPS
+    check("W after steps", comp_err(Wg, Wc), TOL_STEPS)
 
 
 def test_nonphysical_state_is_flagged(A):
@@ -422,7 +422,7 @@ def test_positivity_repair_parity_near_vacuum(A, oracle):
     assert hist[oracle.BRANCHES.index("repaired")] > 0
     Wg, _, _, flags, _, _ = run_gpu(A, pb, W, 30)
     assert not flags & A.FLAG_NONPHYSICAL
-    assert comp_err(Wg, Wc) <= TOL_STEPS
+    check("W after steps", comp_err(Wg, Wc), TOL_STEPS)
 
 
 def test_jet_coarse_to_t_end_parity(A, oracle):
@@ -435,7 +435,7 @@ def test_jet_coarse_to_t_end_parity(A, oracle):
     Wg, _, _, flags, _, t = run_gpu(A, pb, W, n + 2, t_end=1e-5)
     assert not flags & A.FLAG_NONPHYSICAL
     assert abs(t - tc) <= 1e-15
-    assert comp_err(Wg, Wc) <= TOL_STEPS
+    check("W after steps", comp_err(Wg, Wc), TOL_STEPS)
 
 
 def test_jet_coarse_r5_is_robust(A):

@@ -12,6 +12,7 @@ flux floor; sigma: 1e-12 (1 + |s|) + 1e-14 s^2).
 import numpy as np
 import pytest
 
+from parity_report import check
 from paper_2410_05489_gb300 import problems as P
 
 pytestmark = pytest.mark.gpu
@@ -65,7 +66,7 @@ def test_wall_residuals_match_oracle(A, oracle, name):
         torch.cuda.synchronize()
         inv = 1.0 / pb.dx + (1.0 / pb.dy if pb.ndim == 2 else 0.0)
         Fmax = max(np.abs(Fx).max(), np.abs(Fy).max() if Fy is not None else 0.0)
-        assert comp_err(Lg.cpu().numpy(), L, 1e-3 * Fmax * inv) <= 1e-12
+        check("L", comp_err(Lg.cpu().numpy(), L, 1e-3 * Fmax * inv), 1e-12)
         b = sxo
         a = sxg.cpu().numpy()
         assert np.all(np.abs(a - b) <= 1e-12 * (1 + np.abs(b)) + 1e-14 * b * b)
@@ -73,8 +74,8 @@ def test_wall_residuals_match_oracle(A, oracle, name):
         dt = 0.5 * oracle.cfl_dt(pb, W)
         Lk, Ltk, *_ = oracle.gks_residual(pb, W, sx, sy, dt)
         Lkg, Ltkg, _, _ = s.gks_residual(dt, dev(W), dev(sx), dev(sy))
-        assert comp_err(Lkg.cpu().numpy(), Lk, 1e-3 * Fmax * inv) <= 1e-11
-        assert comp_err(Ltkg.cpu().numpy(), Ltk, 1e-3 * Fmax * inv / dt) <= 1e-11
+        check("L (GKS)", comp_err(Lkg.cpu().numpy(), Lk, 1e-3 * Fmax * inv), 1e-11)
+        check("L_t (GKS)", comp_err(Ltkg.cpu().numpy(), Ltk, 1e-3 * Fmax * inv / dt), 1e-11)
     finally:
         s.close()
 
@@ -110,7 +111,7 @@ def test_blast_wave(A, oracle, solver):
     assert rho.min() > 0.0 and 4.0 < rho.max() < 8.0  # the collision peak (about 6 at t = 0.038)
     if solver == "lf":
         Wc, *_ = oracle.run(pb, W0, t_end=0.038)
-        assert np.abs(rho - Wc[0, 0]).mean() <= 1e-6 * np.abs(Wc[0, 0]).mean()
+        check("rho L1 end state", np.abs(rho - Wc[0, 0]).mean() / np.abs(Wc[0, 0]).mean(), 1e-6)
 
 
 @pytest.mark.parametrize("solver,r", [("lf", 9), ("gks", 5)])
@@ -124,7 +125,7 @@ def test_shu_osher(A, oracle, solver, r):
         Wc, *_ = oracle.run(pb, W0, t_end=1.8)
     else:
         Wc, *_ = oracle.gks_run(pb, W0, t_end=1.8)
-    assert np.abs(rho - Wc[0, 0]).mean() <= 1e-6 * np.abs(Wc[0, 0]).mean()
+    check("rho L1 end state", np.abs(rho - Wc[0, 0]).mean() / np.abs(Wc[0, 0]).mean(), 1e-6)
 
 
 @pytest.mark.parametrize("solver,r", [("lf", 9), ("lf", 5), ("gks", 5)])
