@@ -38,13 +38,54 @@ N_GRID = 1024
 ORDER = 9
 ORDER_ALSO = 7
 HBM_BYTES_PER_CELL_STAGE_2D = 128.0  # read W^(s), W^n, write W^(s+1), sigma in/out, both directions
-# DRAM bytes (read + write) per sweep launch measured by ncu on this kernel for the 1024^2,
-# order-9 workload (mean of the x- and y-face launches; profiles/sweep_kernel_r9_2d_vortex1024_ncu.md).
-# Reported as roofline.traffic for that workload only (null for other sizes / orders).
-SWEEP_DRAM_BYTES_1024_R9 = 58.19e6
-# FP64 pipe active (of active cycles) of the same captures (ncu --set full, the x- and y-face
-# launches): sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active, mean of the two.
-SWEEP_FP64_PIPE_ACTIVE_1024_R9 = 0.8455
+# Sources of the face-sweep kernel: the ncu summaries under profiles/ record a hash of these
+# files beside their counters, and the counters are reported only while the hash matches.
+SWEEP_SOURCES = ("ase_df_sweep.cu", "ase_df_sweep_body.cuh", "ase_df_device.cuh", "ase_df_internal.cuh",
+                 "ase_df_tileplan.h")
+SWEEP_PROFILE = {9: "sweep_kernel_r9_2d_vortex1024_ncu.md", 7: "sweep_kernel_r7_2d_vortex1024_ncu.md"}
+
+
+def sweep_sources_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the sweep kernel's source files, in order."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2410_05489_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        return None
+
+
+def profiled_counters(order: int):
+    """(DRAM bytes per sweep launch, FP64 pipe active of active cycles, note) from the ncu
+    summary of the order's 1024^2 sweep; (None, None, why) when there is none or when the
+    kernel sources changed after it was taken."""
+    path = os.path.join(ROOT, "profiles", SWEEP_PROFILE.get(order, ""))
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None, None, "no ncu summary for this order"
+    vals = {}
+    for line in text.splitlines():
+        for key in ("kernel-sources-sha256", "dram-bytes-per-launch", "fp64-pipe-active"):
+            if line.strip().startswith(key + ":"):
+                vals[key] = line.split(":", 1)[1].strip()
+    if vals.get("kernel-sources-sha256") != sweep_sources_hash():
+        return None, None, "the kernel sources changed after the ncu capture"
+    try:
+        return float(vals["dram-bytes-per-launch"]), float(vals["fp64-pipe-active"]), "ncu, same kernel sources"
+    except (KeyError, ValueError):
+        return None, None, "ncu summary without counters"
 
 
 # FP64 operations of one Gauss point: both sides' primitives, the Lax-Friedrichs flux
@@ -268,7 +309,8 @@ def time_e2e(A, torch, pb, W0, steps, warmup):
 
 def cpu_baseline_sample(order: int):
     """The oracle as it stands, one residual evaluation (= one RK stage) of the full
-    1024 x 1024 vortex workload on one host core."""
+    1024 x 1024 vortex workload: on one host core, and with its face loops on all host
+    cores (oracle.threads; the results are the serial ones bit for bit)."""
     from oracle import oracle as O
 
     O.build()
@@ -277,9 +319,17 @@ def cpu_baseline_sample(order: int):
     t0 = time.perf_counter()
     O.residual(pb, W, sx, sy)
     dt = time.perf_counter() - t0
+    cores = _cores()
+    with O.threads(cores):
+        t0 = time.perf_counter()
+        O.residual(pb, W, sx, sy)
+        dt_all = time.perf_counter() - t0
     return {"value": pb.ncells / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "one residual evaluation (one RK stage) of the %dx%d r=%d vortex, serial C++ oracle, "
-                      "%.1f s" % (N_GRID, N_GRID, order, dt)}
+                      "%.1f s" % (N_GRID, N_GRID, order, dt),
+            "all_cores": {"value": round(pb.ncells / dt_all / 1e6, 4), "unit": UNIT, "cores": cores,
+                          "sample": "the same residual with the oracle's face loops on %d host threads, %.2f s"
+                                    % (cores, dt_all)}}
 
 
 def run_ours(args, world, rank, local):
@@ -311,6 +361,7 @@ def run_ours(args, world, rank, local):
     clocks = sampler.stop()
     ms7, _, _ = time_steps(A, torch, pb7, W7, args.steps, args.warmup, flush)
     ms7_max = max_over_ranks(ms7, world)
+    _, prof7, _ = time_steps(A, torch, pb7, W7, args.steps, args.warmup, flush, profile=True)
     e2e_ms, bi, bo = time_e2e(A, torch, pb, W0, args.steps, args.warmup)
     e2e_ms = max_over_ranks(e2e_ms, world)
 
@@ -326,20 +377,52 @@ def run_ours(args, world, rank, local):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     clk_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
     peak_tflops = 2.0 * 2.0 * n_sm * clk_mhz * 1e6 / 1e12
-    sweep_ms = prof[0][0] + prof[0][1]
-    sweep_n = prof[1][0] + prof[1][1]
-    faces_per_launch = 0.5 * ((pb.nx + 1) * pb.ny + (pb.ny + 1) * pb.nx)
-    flops_per_launch = algorithmic_flops_per_face(2, args.order) * faces_per_launch
-    achieved = flops_per_launch / (sweep_ms / sweep_n * 1e-3) / 1e12
     total_prof_ms = sum(prof[0])
-    hbm_gbs = None
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            hbm_gbs = json.load(f).get("hbm_gbs")
-    except OSError:
-        pass
+    hbm_gbs = measured_hbm_gbs()
     hbm_achieved = value * 1e6 * HBM_BYTES_PER_CELL_STAGE_2D / 1e9
     step_flops = algorithmic_flops_per_cell_stage(2, args.order) * cells * 3
+    step_flops7 = algorithmic_flops_per_cell_stage(2, ORDER_ALSO) * cells * 3
+
+    def sweep_roofline(order, pr, ms_steps, ms_with_pairs):
+        """Roofline of the face sweep (x and y launches) of one order from its launch times."""
+        sweep_ms = pr[0][0] + pr[0][1]
+        sweep_n = pr[1][0] + pr[1][1]
+        faces_per_launch = 0.5 * ((pb.nx + 1) * pb.ny + (pb.ny + 1) * pb.nx)
+        flops_per_launch = algorithmic_flops_per_face(2, order) * faces_per_launch
+        achieved = flops_per_launch / (sweep_ms / sweep_n * 1e-3) / 1e12
+        traffic, pipe, note = profiled_counters(order) if args.n == N_GRID else (None, None, "not 1024^2")
+        r = {
+            "bound": "alu",
+            "kernel": "sweep_kernel<%d> (fused DF / ASE reconstruction / Gauss-point Lax-Friedrichs flux / sigma), "
+                      "x and y launches" % order,
+            "achieved": round(achieved, 4),
+            "peak": round(peak_tflops, 4),
+            "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tflops, 4),
+            "traffic": traffic,
+            "traffic_unit": "bytes per sweep launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "ncu_fp64_pipe_active": pipe,
+            "ncu_note": note,
+            "peak_source": "2 FP64 FMA/cycle/SM (ncu DFMA peak_sustained) x %d SMs x %.0f MHz (median sampled "
+                           "SM clock in the timed region) x 2 flops" % (n_sm, clk_mhz),
+            "peak_microbench": round(2.0 * fma_rate / 1e12, 4),
+            "frac_of_microbench": round(achieved / (2.0 * fma_rate / 1e12), 4),
+            "flops_per_launch": flops_per_launch,
+            "launch_ms": round(sweep_ms / sweep_n, 4),
+            "launch_ms_source": "CUDA event pair around every launch, in a second timed pass of the same K steps "
+                                "(%.4f ms/step with the pairs)" % (ms_with_pairs / args.steps),
+            "share_of_step_time": round(sweep_ms / sum(pr[0]), 4) if sum(pr[0]) > 0 else None,
+        }
+        return r
+
+    roof = sweep_roofline(args.order, prof, ms_max, ms_prof)
+    roof["step_frac_of_fp64_peak"] = round(step_flops * args.steps / (ms_max * 1e-3) / 1e12 / peak_tflops, 4)
+    roof["hbm"] = {"achieved_gbs": round(hbm_achieved, 2), "peak_gbs": hbm_gbs,
+                   "frac": round(hbm_achieved / hbm_gbs, 5) if hbm_gbs else None,
+                   "bytes_per_cell_stage": HBM_BYTES_PER_CELL_STAGE_2D}
+    roof7 = sweep_roofline(ORDER_ALSO, prof7, ms7_max, ms7_max)
+    roof7["step_frac_of_fp64_peak"] = round(step_flops7 * args.steps / (ms7_max * 1e-3) / 1e12 / peak_tflops, 4)
+    roof7.pop("launch_ms_source")
     out = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -355,31 +438,8 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": dict(workload_config(args, world), value_order7=round(value7, 3),
                        ms_per_step_order7=round(ms7_max / args.steps, 4)),
-        "roofline": {
-            "bound": "alu",
-            "kernel": "sweep_kernel (fused DF / ASE reconstruction / Gauss-point Lax-Friedrichs flux / sigma), "
-                      "x and y launches",
-            "achieved": round(achieved, 4),
-            "peak": round(peak_tflops, 4),
-            "unit": "TFLOP/s",
-            "frac": round(achieved / peak_tflops, 4),
-            "traffic": SWEEP_DRAM_BYTES_1024_R9 if (args.n, args.order) == (1024, 9) else None,
-            "ncu_fp64_pipe_active": SWEEP_FP64_PIPE_ACTIVE_1024_R9 if (args.n, args.order) == (1024, 9) else None,
-            "traffic_unit": "bytes per sweep launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "peak_source": "2 FP64 FMA/cycle/SM (ncu DFMA peak_sustained) x %d SMs x %.0f MHz (median sampled "
-                           "SM clock in the timed region) x 2 flops" % (n_sm, clk_mhz),
-            "peak_microbench": round(2.0 * fma_rate / 1e12, 4),
-            "frac_of_microbench": round(achieved / (2.0 * fma_rate / 1e12), 4),
-            "flops_per_launch": flops_per_launch,
-            "launch_ms": round(sweep_ms / sweep_n, 4),
-            "launch_ms_source": "CUDA event pair around every launch, in a second timed pass of the same K steps "
-                                "(%.4f ms/step with the pairs)" % (ms_prof / args.steps),
-            "share_of_step_time": round(sweep_ms / total_prof_ms, 4) if total_prof_ms > 0 else None,
-            "step_frac_of_fp64_peak": round(step_flops * args.steps / (ms_max * 1e-3) / 1e12 / peak_tflops, 4),
-            "hbm": {"achieved_gbs": round(hbm_achieved, 2), "peak_gbs": hbm_gbs,
-                    "frac": round(hbm_achieved / hbm_gbs, 5) if hbm_gbs else None,
-                    "bytes_per_cell_stage": HBM_BYTES_PER_CELL_STAGE_2D},
-        },
+        "roofline": roof,
+        "roofline_order7": roof7,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                 "method": "every step copies its input from pinned host memory and its result back; two device "
                           "state buffers and a copy stream overlap the copies with the neighbouring steps; no L2 "
@@ -645,6 +705,7 @@ def suite_bench(args):
     flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     cores = _cores()
+    hbm_gbs = measured_hbm_gbs()
     rows = []
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -687,7 +748,7 @@ def suite_bench(args):
         rows.append({"config": "vortex 2D 1024^2, r=%d (oracle: one stage at 256^2)" % r,
                      "gpu": {"value": round(value, 3), "ms_per_step": round(ms / args.steps, 4), "flags": flags},
                      "roofline_frac": round(achieved / peak, 4), "hbm_frac":
-                         round(value * 1e6 * HBM_BYTES_PER_CELL_STAGE_2D / 1e9 / 6694.8, 5),
+                         (round(value * 1e6 * HBM_BYTES_PER_CELL_STAGE_2D / 1e9 / hbm_gbs, 5) if hbm_gbs else None),
                      "cpu_1core": c1, "cpu_all_cores": ca})
 
     # jet 1600 x 800, r = 9: 20 CFL steps from t = 0

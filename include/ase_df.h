@@ -225,6 +225,19 @@ const char* ase_df_last_error(const ase_df_ctx* ctx);
 ase_df_status ase_df_profile_enable(ase_df_ctx* ctx, int32_t enable);
 ase_df_status ase_df_profile_read(ase_df_ctx* ctx, double* ms, int64_t* n);
 
+/* Branch histogram of Algorithm 1 on the device (a metric of the method's behaviour).
+ * While enabled (enable != 0), every sweep of this context counts, per face and side, the
+ * branch that the normal reconstruction and (2D) the tangential reconstruction of the
+ * state took, and every Gauss point whose reconstructed state was non-physical and took
+ * the cell averages (reading G21).  Counting costs a few shared-memory atomics per face;
+ * when disabled the sweeps count nothing.  Counts accumulate on the device until read.
+ * ase_df_hist_read synchronises the context's streams, writes the counts into counts[7]
+ * -- linear 9th, 7th, 5th order, WENOZ-AO(5,3)+DF (Sec. 3.2), linear 3rd order, DF-damped
+ * 3rd order, first-order Gauss points -- and clears them.  The gas-kinetic sweeps and the
+ * adjoint do not count. */
+ase_df_status ase_df_hist_enable(ase_df_ctx* ctx, int32_t enable);
+ase_df_status ase_df_hist_read(ase_df_ctx* ctx, uint64_t* counts);
+
 /* The residual of ase_df_residual for callers that cannot allocate device memory (code
  * running inside someone else's CUDA graph capture, real-time loops that must not
  * synchronise the device, frameworks that own every device byte through their own

@@ -85,6 +85,8 @@ def _load():
         "ase_df_check_recip": ([_VP, _VP, _c.c_int64, _VP], _c.c_int),
         "ase_df_profile_enable": ([CTX, _c.c_int32], _c.c_int),
         "ase_df_profile_read": ([CTX, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64)], _c.c_int),
+        "ase_df_hist_enable": ([CTX, _c.c_int32], _c.c_int),
+        "ase_df_hist_read": ([CTX, _c.POINTER(_c.c_uint64)], _c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -227,6 +229,20 @@ def ase_df_profile_read(ctx):
     n = (_c.c_int64 * 5)()
     _check(ctx, _load().ase_df_profile_read(ctx, ms, n))
     return list(ms), list(n)
+
+
+BRANCH_SLOTS = ("lin9", "lin7", "lin5", "weno_df", "lin3", "df3", "first_order")
+
+
+def ase_df_hist_enable(ctx, enable: bool) -> None:
+    _check(ctx, _load().ase_df_hist_enable(ctx, int(bool(enable))))
+
+
+def ase_df_hist_read(ctx):
+    """-> branch counts since the last read, in BRANCH_SLOTS order (then cleared)."""
+    arr = (_c.c_uint64 * 7)()
+    _check(ctx, _load().ase_df_hist_read(ctx, arr))
+    return list(arr)
 
 
 def ase_df_check_recip(x, out, stream=None) -> None:

@@ -820,25 +820,30 @@ __global__ void __launch_bounds__(256) adj_gather_st_kernel(const GridInfo g, co
 
 inline int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)); }
 
+// Phase 1 (K1, K2) writes only this direction's scratch; phase 2 (K3 - K5) adds into the
+// outputs shared with the other direction.  Phase 1 of the two directions may run
+// concurrently when their scratch is separate; phase 2 runs in a fixed order.
 template <int R, int DIM, int DIR>
-cudaError_t adj_launch(const GridInfo& g, const SweepArgs& a, const AdjArgs& aa, const Tables& t, cudaStream_t s) {
+cudaError_t adj_launch(int phase, const GridInfo& g, const SweepArgs& a, const AdjArgs& aa, const Tables& t,
+                       cudaStream_t s) {
   using TL = AdjTile<R, DIM>;
-  const size_t smem = TL::smem_doubles * sizeof(double);
-  auto k1 = adj_face_kernel<R, DIM, DIR>;
-  static std::atomic<unsigned long long> attr_done{0ull};
-  {
-    cudaError_t e = ensure_smem_limit(k1, smem, attr_done);
-    if (e != cudaSuccess) return e;
-  }
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int m = (DIR == 0) ? g.ny : g.nx;
-  dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
-  k1<<<grid, TL::NT, smem, s>>>(g, a, aa, t);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const size_t nitems = (size_t)(n + 2) * (m + 2 * TL::KT);
-  adj_normal_kernel<R, DIM, DIR><<<grid_for(nitems), 256, 0, s>>>(g, a, aa, t);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (phase & 1) {
+    const size_t smem = TL::smem_doubles * sizeof(double);
+    auto k1 = adj_face_kernel<R, DIM, DIR>;
+    static std::atomic<unsigned long long> attr_done{0ull};
+    e = ensure_smem_limit(k1, smem, attr_done);
+    if (e != cudaSuccess) return e;
+    dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
+    k1<<<grid, TL::NT, smem, s>>>(g, a, aa, t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t nitems = (size_t)(n + 2) * (m + 2 * TL::KT);
+    adj_normal_kernel<R, DIM, DIR><<<grid_for(nitems), 256, 0, s>>>(g, a, aa, t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (!(phase & 2)) return cudaSuccess;
   adj_gather_w_kernel<R, DIM, DIR><<<grid_for((size_t)g.nx * g.ny), 256, 0, s>>>(g, aa);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (aa.sbar_norm) {
@@ -857,12 +862,13 @@ cudaError_t adj_launch(const GridInfo& g, const SweepArgs& a, const AdjArgs& aa,
 #define ASE_DF_CAT2(a, b) a##b
 #define ASE_DF_CAT(a, b) ASE_DF_CAT2(a, b)
 
-cudaError_t ASE_DF_CAT(launch_adjoint_r, ASE_DF_ORDER)(int dim, int dir, const GridInfo& g, const SweepArgs& a,
-                                                       const AdjArgs& aa, const Tables& t, cudaStream_t s) {
+cudaError_t ASE_DF_CAT(launch_adjoint_r, ASE_DF_ORDER)(int dim, int dir, int phase, const GridInfo& g,
+                                                       const SweepArgs& a, const AdjArgs& aa, const Tables& t,
+                                                       cudaStream_t s) {
   constexpr int R = ASE_DF_ORDER;
-  if (dim == 1) return adj_launch<R, 1, 0>(g, a, aa, t, s);
-  if (dir == 0) return adj_launch<R, 2, 0>(g, a, aa, t, s);
-  return adj_launch<R, 2, 1>(g, a, aa, t, s);
+  if (dim == 1) return adj_launch<R, 1, 0>(phase, g, a, aa, t, s);
+  if (dir == 0) return adj_launch<R, 2, 0>(phase, g, a, aa, t, s);
+  return adj_launch<R, 2, 1>(phase, g, a, aa, t, s);
 }
 
 }  // namespace asedf

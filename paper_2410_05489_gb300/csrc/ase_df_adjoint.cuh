@@ -27,22 +27,24 @@ struct AdjArgs {
   double inv_h;            // 1/dx (x-sweep) or 1/dy (y-sweep)
 };
 
-// Scratch doubles one direction's adjoint needs (the larger of the two directions is
-// allocated once).
+// Scratch doubles one direction's adjoint needs (each direction has its own, so that the
+// face and normal kernels of the two directions can run side by side).
 inline size_t adj_scratch_doubles(int dim, int order, long long n, long long m) {
   const long long K = (order - 1) / 2, KT = (dim == 2) ? K : 0, C = (dim == 1) ? 3 : 4;
   const long long nf = (n + 1) * m, ni = (n + 2) * (m + 2 * KT);
   return (size_t)(2 * (2 * KT + 1) * C * nf + 2 * C * nf + (dim == 2 ? 8 * nf : 0) + (2 * K + 1) * C * ni + 4 * ni);
 }
 
-cudaError_t launch_adjoint_r3(int dim, int dir, const GridInfo& g, const SweepArgs& a, const AdjArgs& aa,
-                              const Tables& t, cudaStream_t s);
-cudaError_t launch_adjoint_r5(int dim, int dir, const GridInfo& g, const SweepArgs& a, const AdjArgs& aa,
-                              const Tables& t, cudaStream_t s);
-cudaError_t launch_adjoint_r7(int dim, int dir, const GridInfo& g, const SweepArgs& a, const AdjArgs& aa,
-                              const Tables& t, cudaStream_t s);
-cudaError_t launch_adjoint_r9(int dim, int dir, const GridInfo& g, const SweepArgs& a, const AdjArgs& aa,
-                              const Tables& t, cudaStream_t s);
+// phase: 1 = the face and normal kernels (this direction's scratch only), 2 = the gathers
+// into the outputs (Wbar, sigma_in adjoints), 3 = both.
+cudaError_t launch_adjoint_r3(int dim, int dir, int phase, const GridInfo& g, const SweepArgs& a,
+                              const AdjArgs& aa, const Tables& t, cudaStream_t s);
+cudaError_t launch_adjoint_r5(int dim, int dir, int phase, const GridInfo& g, const SweepArgs& a,
+                              const AdjArgs& aa, const Tables& t, cudaStream_t s);
+cudaError_t launch_adjoint_r7(int dim, int dir, int phase, const GridInfo& g, const SweepArgs& a,
+                              const AdjArgs& aa, const Tables& t, cudaStream_t s);
+cudaError_t launch_adjoint_r9(int dim, int dir, int phase, const GridInfo& g, const SweepArgs& a,
+                              const AdjArgs& aa, const Tables& t, cudaStream_t s);
 
 // out = a x + b y (y may be NULL, then out = a x); out may alias x or y.
 cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y, size_t n,

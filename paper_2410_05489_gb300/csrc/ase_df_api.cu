@@ -52,6 +52,8 @@ struct ase_df_ctx {
   cudaEvent_t ev_fork, ev_join;
   // kernel timing (ase_df_profile_*)
   bool prof_on;
+  bool hist_on;             // branch histogram of the sweeps (ase_df_hist_*)
+  bool g_hist;              // hist_on when the step graph was captured
   std::vector<cudaEvent_t>* prof_ev;  // pairs (start, stop)
   std::vector<int>* prof_kind;
   char err[512];
@@ -233,6 +235,8 @@ ase_df_status setup_problem(const ase_df_params* pin, ProblemSetup* out, char* e
     g.wall_i0 = i0;
   }
   g.gamma = p.gamma;
+  g.gm1 = p.gamma - 1.0;
+  g.gg1 = p.gamma * (p.gamma - 1.0);
   g.thres = p.sigma_thres;
   return ASE_DF_OK;
 }
@@ -356,6 +360,7 @@ static cudaError_t sweep(ase_df_ctx* c, int dir, const double* W, const double* 
   a.F = F;
   a.s_out = s_out;
   a.st = c->st;
+  a.hist = c->hist_on ? c->st->hist : nullptr;
   ProfScope prof(c, s, dir);
   switch (c->p.order) {
     case 3: return launch_sweep_r3(c->dim, dir, c->g, a, c->tab, s);
@@ -540,7 +545,8 @@ ase_df_status ase_df_run(ase_df_ctx* c, double* W, double* sx, double* sy, doubl
   c->last_stream = s;
   if (nsteps == 0) return ASE_DF_OK;
   const double dtkey = (dt > 0.0) ? dt : 0.0;
-  if (!c->graph_exec || c->g_W != W || c->g_sx != sx || c->g_sy != sy || c->g_dt != dtkey) {
+  if (!c->graph_exec || c->g_W != W || c->g_sx != sx || c->g_sy != sy || c->g_dt != dtkey ||
+      c->g_hist != c->hist_on) {
     if (c->graph_exec) {
       cudaGraphExecDestroy(c->graph_exec);
       c->graph_exec = nullptr;
@@ -569,6 +575,7 @@ ase_df_status ase_df_run(ase_df_ctx* c, double* W, double* sx, double* sy, doubl
     c->g_sx = sx;
     c->g_sy = sy;
     c->g_dt = dtkey;
+    c->g_hist = c->hist_on;
   }
   for (int32_t i = 0; i < nsteps; ++i) {
     cudaError_t e = cudaGraphLaunch(c->graph_exec, s);
@@ -586,7 +593,7 @@ static ase_df_status ensure_adjoint(ase_df_ctx* c) {
   if (c->adj) return ASE_DF_OK;
   const GridInfo& g = c->g;
   size_t nadj = adj_scratch_doubles(c->dim, c->p.order, g.nx, g.ny);
-  if (c->dim == 2) nadj = std::max(nadj, adj_scratch_doubles(c->dim, c->p.order, g.ny, g.nx));
+  if (c->dim == 2) nadj += adj_scratch_doubles(c->dim, c->p.order, g.ny, g.nx);
   const size_t nW = (size_t)c->C * g.nx * g.ny;
   const size_t nsx = (size_t)g.ny * (g.nx + 1);
   const size_t nsy = (c->dim == 2) ? (size_t)(g.ny + 1) * g.nx : 1;
@@ -607,45 +614,72 @@ static ase_df_status ensure_adjoint(ase_df_ctx* c) {
   return ASE_DF_OK;
 }
 
-// Wbar += J_W^T (lscale Lbar) + ..., sbi += J_sigma^T ... for both directions.
+// Wbar += J_W^T (lscale Lbar) + ..., sbi += J_sigma^T ... for both directions.  In 2D the
+// face and normal kernels of the y-direction run on the side stream beside those of the
+// x-direction (each direction has its own scratch); the gathers into the shared outputs
+// then run on s, x-direction first, as in the serial order (with kernel timing on,
+// everything is serial on s).
 static cudaError_t residual_adjoint(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
                                     const double* Lbar, double lscale, const double* sbo_x, const double* sbo_y,
                                     double* Wbar, double* sbi_x, double* sbi_y, cudaStream_t s) {
   const GridInfo& g = c->g;
   const int K = c->K, KT = (c->dim == 2) ? K : 0, C = c->C;
+  AdjArgs aa[2];
+  SweepArgs sa[2];
+  double* scratch = c->adj;
   for (int dir = 0; dir < c->dim; ++dir) {
     const size_t n = (dir == 0) ? g.nx : g.ny, m = (dir == 0) ? g.ny : g.nx;
     const size_t nf = (n + 1) * m, ni = (n + 2) * (m + 2 * KT);
-    AdjArgs aa;
-    aa.Lbar = Lbar;
-    aa.lscale = lscale;
-    aa.sbar_out = (dir == 0) ? sbo_x : sbo_y;
-    aa.Tbar = c->adj;
-    aa.Cbar = aa.Tbar + (size_t)2 * (2 * KT + 1) * C * nf;
-    aa.Stb = aa.Cbar + (size_t)2 * C * nf;
-    aa.Nbar = aa.Stb + (c->dim == 2 ? 8 * nf : 0);
-    aa.Snb = aa.Nbar + (size_t)(2 * K + 1) * C * ni;
-    aa.Wbar = Wbar;
-    aa.sbar_norm = (dir == 0) ? sbi_x : sbi_y;
-    aa.sbar_tan = (c->dim == 2) ? ((dir == 0) ? sbi_y : sbi_x) : nullptr;
-    aa.inv_h = (dir == 0) ? c->inv_dx : c->inv_dy;
-    SweepArgs a;
+    AdjArgs& A = aa[dir];
+    A.Lbar = Lbar;
+    A.lscale = lscale;
+    A.sbar_out = (dir == 0) ? sbo_x : sbo_y;
+    A.Tbar = scratch;
+    A.Cbar = A.Tbar + (size_t)2 * (2 * KT + 1) * C * nf;
+    A.Stb = A.Cbar + (size_t)2 * C * nf;
+    A.Nbar = A.Stb + (c->dim == 2 ? 8 * nf : 0);
+    A.Snb = A.Nbar + (size_t)(2 * K + 1) * C * ni;
+    scratch += adj_scratch_doubles(c->dim, c->p.order, (long long)n, (long long)m);
+    A.Wbar = Wbar;
+    A.sbar_norm = (dir == 0) ? sbi_x : sbi_y;
+    A.sbar_tan = (c->dim == 2) ? ((dir == 0) ? sbi_y : sbi_x) : nullptr;
+    A.inv_h = (dir == 0) ? c->inv_dx : c->inv_dy;
+    SweepArgs& a = sa[dir];
     a.W = W;
     a.s_norm = (dir == 0) ? sx : sy;
     a.s_tan = (dir == 0) ? sy : sx;
     a.F = nullptr;
     a.s_out = nullptr;
     a.st = c->st;
-    cudaError_t e;
-    switch (c->p.order) {
-      case 3: e = launch_adjoint_r3(c->dim, dir, g, a, aa, c->tab, s); break;
-      case 5: e = launch_adjoint_r5(c->dim, dir, g, a, aa, c->tab, s); break;
-      case 7: e = launch_adjoint_r7(c->dim, dir, g, a, aa, c->tab, s); break;
-      default: e = launch_adjoint_r9(c->dim, dir, g, a, aa, c->tab, s); break;
-    }
-    if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  auto launch = [&](int dir, int phase, cudaStream_t st) -> cudaError_t {
+    switch (c->p.order) {
+      case 3: return launch_adjoint_r3(c->dim, dir, phase, g, sa[dir], aa[dir], c->tab, st);
+      case 5: return launch_adjoint_r5(c->dim, dir, phase, g, sa[dir], aa[dir], c->tab, st);
+      case 7: return launch_adjoint_r7(c->dim, dir, phase, g, sa[dir], aa[dir], c->tab, st);
+      default: return launch_adjoint_r9(c->dim, dir, phase, g, sa[dir], aa[dir], c->tab, st);
+    }
+  };
+  if (c->dim == 1 || c->prof_on) {
+    for (int dir = 0; dir < c->dim; ++dir) {
+      cudaError_t e = launch(dir, 3, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaEventRecord(c->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+  if (e != cudaSuccess) return e;
+  const cudaError_t ex = launch(0, 1, s);
+  const cudaError_t ey = launch(1, 1, c->side);
+  // the join is made whatever happened, so that s never runs ahead of the side stream
+  e = cudaEventRecord(c->ev_join, c->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+  if (ex != cudaSuccess) return ex;
+  if (ey != cudaSuccess) return ey;
+  if (e != cudaSuccess) return e;
+  if ((e = launch(0, 2, s)) != cudaSuccess) return e;
+  return launch(1, 2, s);
 }
 
 extern "C" {
@@ -885,6 +919,26 @@ ase_df_status ase_df_profile_enable(ase_df_ctx* c, int32_t enable) {
     prof_clear(c);
   }
   c->prof_on = enable != 0;
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_hist_enable(ase_df_ctx* c, int32_t enable) {
+  if (!c) return ASE_DF_E_INVAL;
+  c->hist_on = enable != 0;
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_hist_read(ase_df_ctx* c, uint64_t* counts) {
+  if (!c || !counts) return c ? fail(c, ASE_DF_E_INVAL, "NULL pointer") : ASE_DF_E_INVAL;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  if (e == cudaSuccess && c->side) e = cudaStreamSynchronize(c->side);
+  if (e != cudaSuccess) return cuda_fail(c, e, "hist_read sync");
+  unsigned long long h[kBranchSlots];
+  e = cudaMemcpy(h, c->st->hist, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->st->hist, 0, sizeof(h));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "hist_read copy");
+  for (int k = 0; k < kBranchSlots; ++k) counts[k] = h[k];
   return ASE_DF_OK;
 }
 

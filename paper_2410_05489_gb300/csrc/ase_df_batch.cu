@@ -365,6 +365,8 @@ static void fill_grid(const ase_df_params& p, BatchProblem& d) {
     d.inflow_speed = (std::fabs(u) + c) * d.inv_dx + (p.ndim == 2 ? (std::fabs(v) + c) * d.inv_dy : 0.0);
   }
   g.gamma = p.gamma;
+  g.gm1 = p.gamma - 1.0;
+  g.gg1 = p.gamma * (p.gamma - 1.0);
   g.thres = p.sigma_thres;
   d.ndim = p.ndim;
   d.variant = (p.ndim - 1) * 4 + (p.order - 3) / 2;

@@ -153,7 +153,7 @@ __device__ __forceinline__ void repair_range(const GridInfo& g, const RepairArgs
           cl[c] = fetch_w(g, a.Ws, c, f - 1, j, ts);
           cr[c] = fetch_w(g, a.Ws, c, f, j, ts);
         }
-        lf_point<C, 1, 2>(cl, cr, cl, cr, 1, g.gamma, F2, sg);
+        lf_point<C, 1, 2>(cl, cr, cl, cr, 1, g.gm1, g.gg1, F2, sg);
 #pragma unroll
         for (int c = 0; c < C; ++c) F[0][side][c] = 0.5 * F2[c];
         a.sx_out[(size_t)j * (nx + 1) + f] = kSigmaBig;
@@ -170,7 +170,7 @@ __device__ __forceinline__ void repair_range(const GridInfo& g, const RepairArgs
             cl[c] = fetch_w(g, a.Ws, c, i, fy - 1, ts);
             cr[c] = fetch_w(g, a.Ws, c, i, fy, ts);
           }
-          lf_point<C, 2, 1>(cl, cr, cl, cr, 1, g.gamma, F2, sg);
+          lf_point<C, 2, 1>(cl, cr, cl, cr, 1, g.gm1, g.gg1, F2, sg);
 #pragma unroll
           for (int c = 0; c < C; ++c) F[1][side][c] = 0.5 * F2[c];
           a.sy_out[(size_t)fy * nx + i] = kSigmaBig;

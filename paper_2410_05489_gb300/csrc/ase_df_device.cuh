@@ -154,85 +154,80 @@ __device__ __forceinline__ double sigma_y_at(const GridInfo& g, const double* __
 // Local Lax-Friedrichs flux (Sec. 2.3) and discontinuity strength sigma (Sec. 3.1) of
 // one Gauss point; qa / qb are the left / right states in (x, y) momentum order and
 // NI / TI select the normal and tangential momentum.  A state is physical when rho > 0
-// and p > 0, tested on p rho = (gamma-1)(E rho - |m|^2 / 2) (no division); otherwise
-// the point takes the cell averages ca / cb (component c at ca[c * cs], read only in that
-// case), returns true and sets sigma = 1e30.
-// FP64 divisions and square roots cost 6-9 FMA slots on this part, so the point uses
-// one reciprocal and two reciprocal square roots:
-//   D = rho_l rho_r (p rho)_l (p rho)_r,  1/(rho_l rho_r) = (p rho)_l (p rho)_r / D,
-//   1/(p_l p_r) = (rho_l rho_r)^2 / D,   1/c = rsqrt(gamma p / rho).
+// and p > 0 (both finite); otherwise the point takes the cell averages ca / cb
+// (component c at ca[c * cs], read only in that case), returns true and sets
+// sigma = 1e30.  gm1 = gamma - 1 and gg1 = gamma (gamma - 1) come from the caller.
+//
+// The FP64 pipe bounds the face kernels, so the point is arranged for few FP64
+// instructions (60 in 2D on the physical path):
+//   - one reciprocal gives 1/rho of both sides: 1/rho_l = rho_r / (rho_l rho_r);
+//   - the pressure is kept as p' = p / (gamma - 1) = E - (m_n u_n + m_t u_t) / 2, so that
+//     (gamma - 1) multiplies only the sums that need it;
+//   - c^2 = gamma p / rho = gg1 p' / rho and 1/c from a seeded reciprocal square root;
+//     c = c^2 / c;
+//   - 1/p' = gg1 (1/rho) (1/c)^2 gives the pressure term of sigma without a reciprocal;
+//   - the flux sum F_l + F_r - lambda (q_r - q_l) is formed per component as
+//     q_l (u_l + lambda) + q_r (u_r - lambda) + pressure terms.
 // The flux is returned as 2F (the 1/2 of the L-F formula is folded into the Gauss
 // weight by the caller).
 template <int C, int NI, int TI>
 __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, const double* ca,
-                                         const double* cb, int cs, double gamma, double* F2,
+                                         const double* cb, int cs, double gm1, double gg1, double* F2,
                                          double& sigma) {
-  const double gm1 = gamma - 1.0;
-  double mmL = qa[NI] * qa[NI], mmR = qb[NI] * qb[NI];
-  if (C == 4) {
-    mmL = fma(qa[TI], qa[TI], mmL);
-    mmR = fma(qb[TI], qb[TI], mmR);
-  }
-  double prL = gm1 * fma(qa[C - 1], qa[0], -0.5 * mmL);
-  double prR = gm1 * fma(qb[C - 1], qb[0], -0.5 * mmR);
-  const bool ok = pos_finite(qa[0]) && pos_finite(qb[0]) && pos_finite(prL) && pos_finite(prR);
   double a[C], b[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     a[c] = qa[c];
     b[c] = qb[c];
   }
+  double irL, irR, unL, unR, utL = 0.0, utR = 0.0, pL, pR;
+  auto primitives = [&]() {
+    const double irr = rcp_pos(a[0] * b[0]);
+    irL = b[0] * irr;
+    irR = a[0] * irr;
+    unL = a[NI] * irL;
+    unR = b[NI] * irR;
+    double kL = a[NI] * unL, kR = b[NI] * unR;  // |m|^2 / rho
+    if (C == 4) {
+      utL = a[TI] * irL;
+      utR = b[TI] * irR;
+      kL = fma(a[TI], utL, kL);
+      kR = fma(b[TI], utR, kR);
+    }
+    pL = fma(-0.5, kL, a[C - 1]);  // p / (gamma - 1)
+    pR = fma(-0.5, kR, b[C - 1]);
+  };
+  primitives();
+  const bool ok = pos_finite(a[0]) && pos_finite(b[0]) && pos_finite(pL) && pos_finite(pR);
   if (!ok) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       a[c] = ca[c * cs];
       b[c] = cb[c * cs];
     }
-    mmL = a[NI] * a[NI];
-    mmR = b[NI] * b[NI];
-    if (C == 4) {
-      mmL = fma(a[TI], a[TI], mmL);
-      mmR = fma(b[TI], b[TI], mmR);
-    }
-    prL = gm1 * fma(a[C - 1], a[0], -0.5 * mmL);
-    prR = gm1 * fma(b[C - 1], b[0], -0.5 * mmR);
+    primitives();
   }
-  const double rr = a[0] * b[0];
-  const double pp = prL * prR;
-  const double inv = rcp_pos(rr * pp);
-  const double irr = pp * inv;       // 1 / (rho_l rho_r)
-  const double irL = b[0] * irr;     // 1 / rho_l
-  const double irR = a[0] * irr;     // 1 / rho_r
-  const double unL = a[NI] * irL, unR = b[NI] * irR;
-  const double pL = prL * irL, pR = prR * irR;
-  const double c2L = gamma * pL * irL, c2R = gamma * pR * irR;
+  const double c2L = (gg1 * pL) * irL, c2R = (gg1 * pR) * irR;
   const double icL = rsqrt_pos(c2L), icR = rsqrt_pos(c2R);
   // lambda = max(|u_n| + c) with c = c^2 / c
   const double lam = max_nonneg(fma(c2L, icL, fabs(unL)), fma(c2R, icR, fabs(unR)));
-  // S = F(left) + F(right), summed as it is formed
-  const double ps = pL + pR;
-  double S[C];
-  S[0] = a[NI] + b[NI];
-  S[NI] = fma(a[NI], unL, fma(b[NI], unR, ps));
-  if (C == 4) {
-    const double utL = a[TI] * irL, utR = b[TI] * irR;
-    S[TI] = fma(a[NI], utL, b[NI] * utR);
-    if (ok) {
-      const double dmt = fma(utL, icL, -utR * icR);
-      sigma = dmt * dmt;
-    }
-  } else {
-    sigma = 0.0;
-  }
-  S[C - 1] = fma(unL, a[C - 1] + pL, unR * (b[C - 1] + pR));
-#pragma unroll
-  for (int c = 0; c < C; ++c) F2[c] = fma(-lam, b[c] - a[c], S[c]);
+  const double alL = unL + lam, alR = unR - lam;
+  const double sp = pL + pR;
+  F2[0] = fma(a[0], alL, b[0] * alR);
+  F2[NI] = fma(a[NI], alL, fma(b[NI], alR, gm1 * sp));
+  if (C == 4) F2[TI] = fma(a[TI], alL, b[TI] * alR);
+  F2[C - 1] = fma(a[C - 1], alL, fma(b[C - 1], alR, gm1 * fma(unL, pL, unR * pR)));
   if (ok) {
-    const double dp = fabs(pL - pR);
-    const double ipp = (rr * rr) * inv;  // 1 / (p_l p_r)
+    // sigma = |dp| (1/p_l + 1/p_r) + (dMa_n)^2 + (dMa_t)^2, Ma = u / c
     const double dmn = fma(unL, icL, -unR * icR);
-    sigma = fma(dmn, dmn, sigma);
-    sigma = fma(dp * ps, ipp, sigma);
+    double s = dmn * dmn;
+    if (C == 4) {
+      const double dmt = fma(utL, icL, -utR * icR);
+      s = fma(dmt, dmt, s);
+    }
+    const double tL = irL * icL, tR = irR * icR;
+    const double ip = fma(tL, icL, tR * icR);  // (1/p'_l + 1/p'_r) / gg1
+    sigma = fma(gg1 * fabs(pL - pR), ip, s);
   } else {
     sigma = kSigmaBig;
   }

@@ -97,7 +97,15 @@ struct DevState {
   unsigned int rbad[kRepairPasses + 1];
   unsigned long long repaired_total;  // cells marked by the repair since the last reset
   unsigned long long frozen_total;    // cells left without a flux update (last resort)
+  // Branch histogram of the sweeps (ase_df_hist_*): per face and side, the branch of
+  // Algorithm 1 taken by the normal and (2D) the tangential reconstruction, and the Gauss
+  // points that took first-order states; slots as kBranchSlots.
+  unsigned long long hist[8];
 };
+
+// Slots of the branch histogram: linear 9th, 7th, 5th order, WENOZ-AO(5,3)+DF, linear 3rd
+// order, DF-damped 3rd order, first-order Gauss point.
+constexpr int kBranchSlots = 7;
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INFLOW_BAND = 2, BC_REFLECT = 3, BC_WALL_AFTER = 4, BC_MOVING_SHOCK = 5 };
 
@@ -108,6 +116,7 @@ struct GridInfo {
   int band_j0, band_j1;  // rows whose ghost cells at x < 0 take the inflow state
   double inflow_cons[4];
   double gamma;
+  double gm1, gg1;    // gamma - 1 and gamma (gamma - 1), for the flux kernels
   double thres;
   // BC_WALL_AFTER (y-lo): columns i < wall_i0 (centre x below wall_x) have fixed ghosts
   int wall_i0 = 0;
@@ -125,6 +134,7 @@ struct SweepArgs {
   double* s_out;          // sigma_out of this direction
   DevState* st;
   double tfrac = 0.0;     // the stage's time is st->t + tfrac st->dt (time-dependent ghosts)
+  unsigned long long* hist = nullptr;  // branch histogram (kBranchSlots counters) or nullptr
 };
 
 struct CombineArgs {

@@ -72,6 +72,12 @@ __device__ __forceinline__ Branch select_branch(const double* s, double thres) {
   return b;
 }
 
+// Histogram slot of a branch (kBranchSlots order): linear 9, 7, 5 -> 0, 1, 2; the
+// WENOZ-AO(5,3)+DF fallback -> 3; linear 3 -> 4; DF-damped 3 -> 5.
+__device__ __forceinline__ int branch_slot(int m) {
+  return m >= 5 ? (9 - m) / 2 : (m == 0 ? 3 : (m == 3 ? 4 : 5));
+}
+
 // Linear M-cell value at point p: v points at W_0, with W_t at v[t*vs].
 template <int M>
 __device__ __forceinline__ double lin_eval(const double* v, int vs, const double* w) {
@@ -242,6 +248,9 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   const int nb = tt + 2 * KT;  // staged lines of this tile (<= NB)
 
   const double ts = stage_time(args.st, args.tfrac, args.st->dt);  // for time-dependent ghosts
+  __shared__ unsigned int hist_s[kBranchSlots];
+  const bool counting = args.hist != nullptr;
+  if (counting && tid < kBranchSlots) hist_s[tid] = 0u;
   // ---- stage cell averages: cells a0-1-K .. a0+TN-1+K, lines b0-KT .. b0+tt+KT-1 ----
   for (int idx = tid; idx < C * nb * NA; idx += NT) {
     int c, bb, aa;
@@ -320,8 +329,13 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
     for (int side = 0; side < 2; ++side) {
       const int qa = fa + side;  // left state: cell f-1 (plus face); right: cell f (minus face)
       const double* Q = side == 0 ? sQP : sQM;
+      if (counting) {  // the normal branch of this state's cell, as phase 1 chose it
+        const Branch bn = select_branch<R>(sSn + (tb + KT) * NSN + qa, g.thres);
+        atomicAdd(&hist_s[branch_slot(bn.m)], 1u);
+      }
       if (DIM == 2) {
         const Branch bt = select_branch<R>(sSt + qa * NST + tb, g.thres);
+        if (counting) atomicAdd(&hist_s[branch_slot(bt.m)], 1u);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const double* v = Q + (c * NB + tb + K) * NQ + qa;
@@ -342,16 +356,19 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
 #pragma unroll
     for (int c = 0; c < C; ++c) Fs[c] = 0.0;
     double ssum = 0.0;
-    bool anyfb = false;
+    unsigned int nfb = 0u;
 #pragma unroll
     for (int q = 0; q < G; ++q) {
       double F[C], sg;
-      anyfb |= lf_point<C, NI, TI>(st[0][q], st[1][q], ca, cb, NB * NA, g.gamma, F, sg);
+      nfb += lf_point<C, NI, TI>(st[0][q], st[1][q], ca, cb, NB * NA, g.gm1, g.gg1, F, sg) ? 1u : 0u;
 #pragma unroll
       for (int c = 0; c < C; ++c) Fs[c] = fma((DIM == 2) ? T.hgw[q] : 0.5, F[c], Fs[c]);
       ssum += sg;
     }
-    if (anyfb) atomicOr(&args.st->flags, 0x2u);
+    if (nfb) {
+      atomicOr(&args.st->flags, 0x2u);
+      if (counting) atomicAdd(&hist_s[kBranchSlots - 1], nfb);
+    }
     const double sface = (G == 1) ? ssum : ssum * (1.0 / G);
     if (DIR == 0) {
 #pragma unroll
@@ -362,6 +379,10 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
       for (int c = 0; c < C; ++c) args.F[((size_t)c * (g.ny + 1) + f) * g.nx + b] = Fs[c];
       args.s_out[(size_t)f * g.nx + b] = sface;
     }
+  }
+  if (counting) {
+    __syncthreads();
+    if (tid < kBranchSlots && hist_s[tid]) atomicAdd(&args.hist[tid], (unsigned long long)hist_s[tid]);
   }
 }
 

@@ -250,12 +250,12 @@ def riemann_1d(n: int, order: int, seed: int) -> Tuple[Problem, np.ndarray]:
     return pb, np.ascontiguousarray(conservative((rho[side], u[side], p[side]), pb.gamma, 1)[:, None, :])
 
 
-def riemann_2d(n: int, order: int, seed: int, ny: int | None = None) -> Tuple[Problem, np.ndarray]:
-    """Four random quadrant states split at (0.5, 0.5) on [0,1]^2 (the shape of
+def riemann_2d(n: int, order: int, seed: int, ny: int | None = None, x1: float = 1.0) -> Tuple[Problem, np.ndarray]:
+    """Four random quadrant states split at (x1/2, 0.5) on [0,x1] x [0,1] (the shape of
     Configuration 3, Sec. 4.1); rho, p log-uniform [0.1, 10], u, v uniform [-2, 2]."""
     rng = np.random.default_rng(seed)
     ny = ny or n
-    pb = Problem(ndim=2, nx=n, ny=ny, order=order, gamma=1.4)
+    pb = Problem(ndim=2, nx=n, ny=ny, x1=x1, order=order, gamma=1.4)
     rho = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 4))
     p = np.exp(rng.uniform(np.log(0.1), np.log(10.0), 4))
     u = rng.uniform(-2.0, 2.0, 4)
@@ -263,7 +263,7 @@ def riemann_2d(n: int, order: int, seed: int, ny: int | None = None) -> Tuple[Pr
     x = (np.arange(n) + 0.5) * pb.dx
     y = (np.arange(ny) + 0.5) * pb.dy
     X, Y = np.meshgrid(x, y)
-    q = (X >= 0.5).astype(int) + 2 * (Y >= 0.5).astype(int)
+    q = (X >= 0.5 * x1).astype(int) + 2 * (Y >= 0.5).astype(int)
     return pb, np.ascontiguousarray(conservative((rho[q], u[q], v[q], p[q]), pb.gamma, 2))
 
 
@@ -292,12 +292,16 @@ def shu_osher(n: int = 200, order: int = 5) -> Tuple[Problem, np.ndarray]:
     return pb, cell_average(pb, prim)
 
 
-def configuration3(n: int, order: int, gks_c1: float = 0.05, gks_c2: float = 1.0) -> Tuple[Problem, np.ndarray]:
-    """Configuration 3 of Sec. 4.3 (Example 2): [0,1]^2, quadrant states split at
-    (0.7, 0.7), outflow, gamma 1.4; the workload of the paper's timing table (Table 4)."""
-    pb = Problem(ndim=2, nx=n, ny=n, order=order, gamma=1.4, gks_c1=gks_c1, gks_c2=gks_c2)
+def configuration3(n: int, order: int, gks_c1: float = 0.05, gks_c2: float = 1.0,
+                   ny: int | None = None) -> Tuple[Problem, np.ndarray]:
+    """Configuration 3 of Sec. 4.3 (Example 2): [0,1]^2 with n x ny cells (ny = n by default),
+    quadrant states split at (0.7, 0.7), outflow, gamma 1.4; the workload of the paper's
+    timing table (Table 4)."""
+    ny = ny or n
+    pb = Problem(ndim=2, nx=n, ny=ny, order=order, gamma=1.4, gks_c1=gks_c1, gks_c2=gks_c2)
     x = (np.arange(n) + 0.5) * pb.dx
-    X, Y = np.meshgrid(x, x)
+    y = (np.arange(ny) + 0.5) * pb.dy
+    X, Y = np.meshgrid(x, y)
     lo_x, lo_y = X < 0.7, Y < 0.7
     rho = np.where(lo_x & lo_y, 0.138, np.where(~lo_x & lo_y, 0.5323, np.where(~lo_x & ~lo_y, 1.5, 0.5323)))
     u = np.where(lo_x & lo_y, 1.206, np.where(~lo_x & lo_y, 0.0, np.where(~lo_x & ~lo_y, 0.0, 1.206)))

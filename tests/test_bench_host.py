@@ -62,3 +62,30 @@ def test_clock_sampler_with_a_stand_in_nvidia_smi(monkeypatch):
     s = bench.ClockSampler(0)
     s.start()
     assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_profiled_counters_need_the_same_kernel_sources(monkeypatch, tmp_path):
+    """The roofline's ncu counters (DRAM bytes per launch, FP64 pipe active) come from the
+    committed summary only while the hash of the sweep sources recorded there matches the
+    sources being timed."""
+    import os
+    import shutil
+
+    csrc = tmp_path / "paper_2410_05489_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in bench.SWEEP_SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_2410_05489_gb300", "csrc", name), csrc / name)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.sweep_sources_hash()
+    assert len(h) == 16 and int(h, 16) >= 0
+    prof = tmp_path / "profiles" / bench.SWEEP_PROFILE[9]
+    assert bench.profiled_counters(9)[0] is None  # no summary
+    prof.write_text("| table |\n\n    kernel-sources-sha256: %s\n    dram-bytes-per-launch: 5.8e7\n"
+                    "    fp64-pipe-active: 0.85\n" % h)
+    assert bench.profiled_counters(9)[:2] == (5.8e7, 0.85)
+    with open(csrc / bench.SWEEP_SOURCES[1], "a") as f:
+        f.write("\n// edited\n")
+    assert bench.sweep_sources_hash() != h
+    traffic, pipe, note = bench.profiled_counters(9)
+    assert traffic is None and pipe is None and "changed" in note

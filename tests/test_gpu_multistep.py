@@ -2,15 +2,23 @@
 100 SSP-RK3 steps with CFL time steps (computed on the device), GPU against the oracle,
 every cell of the final state within 1e-9 of that component's largest magnitude.
 
-- Configuration 3 (Sec. 4.3, Example 2) on 256^2: the wave-filling tile plan.
-- Random four-quadrant Riemann data (Configuration 3's shape with rho, p log-uniform in
-  [0.1, 10] and u, v uniform in [-2, 2]) on 7990 x 70: the uniform 8 x 64 tile grid in
-  both directions; with seed 1 the stage repair (reading G21b) acts at order 5.
+The workload is Configuration 3 (Sec. 4.3, Example 2; shocks, contacts and their
+interactions from four quadrant states):
+- on 256^2 cells: the wave-filling tile plan;
+- on 1024 x 512 cells (cells twice as wide as high): the uniform 8 x 64 tile grid in both
+  directions.
 
-Each runs at orders 5 and 9. The WENOZ-AO(5,3)+DF fallback takes part in every run
-(its share is asserted on the oracle's branch histogram). The GPU runs the steps as the
+Each runs at orders 5 and 9. The WENOZ-AO(5,3)+DF fallback takes part in every run (its
+count is asserted on the oracle's branch histogram). The GPU runs the steps as the
 captured CUDA-graph replay of ase_df_run. The oracle runs its face loops on all host
 threads, which gives its serial results bit for bit.
+
+Random quadrant states are not used here. Some draws drive the flow unstable (on
+7990 x 70 cells of [0, 1]^2, aspect ratio 114, the CFL step swings between 9.2e-6 and
+4.8e-6 within 30 steps and Gauss points keep falling back to first order). There, rounding
+differences of 1e-16 grow until two correct FP64 trajectories part (the simulated time
+after 100 steps differed by 2-4 %). The stage repair's multi-step parity is covered in 1D
+near vacuum and by the coarse Ma-20000 jet (tests/test_gpu_parity.py).
 """
 import os
 
@@ -69,7 +77,7 @@ def gpu_steps(A, pb, W, nsteps):
 
 CASES = {
     "configuration3_256": lambda r: P.configuration3(256, r),
-    "riemann_quadrants_7990x70": lambda r: P.riemann_2d(7990, r, 1, ny=70),
+    "configuration3_1024x512": lambda r: P.configuration3(1024, r, ny=512),
 }
 
 
@@ -80,12 +88,9 @@ def test_100_steps_parity_on_shock_data(A, oracle, case, order):
     Wc, tc, hist = oracle_steps(oracle, pb, W0, NSTEPS)
     Wg, tg, flags, repaired, frozen = gpu_steps(A, pb, W0, NSTEPS)
     assert flags & A.FLAG_NONPHYSICAL == 0
-    weno = hist[oracle.BRANCHES.index("weno_df")] / hist[:6].sum()
-    assert weno > 1e-3, hist  # the fallback took part
+    assert hist[oracle.BRANCHES.index("weno_df")] > 1000, hist  # the fallback took part
     oracle_repaired = hist[oracle.BRANCHES.index("repaired")]
     # the repair acted on both sides or on neither
     assert (repaired > 0) == (oracle_repaired > 0), (repaired, oracle_repaired)
-    if case.startswith("riemann") and order == 5:
-        assert repaired > 0  # this case exercises the stage repair
     check("t after steps", abs(tg - tc) / tc, 1e-12)
     check("W after steps", comp_err(Wg, Wc), TOL_STEPS)
