@@ -109,6 +109,27 @@ def algorithmic_flops_per_face(ndim: int, r: int) -> float:
     return normal + tang + G * (phi + 2 * C + 1) + 1
 
 
+# Edges per operation of the oracle's reverse-mode graph of one 2D residual (smooth data,
+# 32^2 periodic; tests/test_flop_model.py): the reverse sweep does one multiply-add per edge
+# (the cost model of reverse mode), so the residual adjoint's algorithmic flops are taken as
+# those of the forward residual times 1 + 2 e.
+VJP_EDGES_PER_OP = {5: 1.4197, 7: 1.4451, 9: 1.4552}
+
+
+def residual_flops(ndim: int, r: int, nx: int, ny: int) -> float:
+    """Algorithmic flops of one residual: every face of both sweeps and the flux difference
+    (two differences, two products and an add per component and cell)."""
+    C = 4 if ndim == 2 else 3
+    faces = (nx + 1) * ny + ((ny + 1) * nx if ndim == 2 else 0)
+    return algorithmic_flops_per_face(ndim, r) * faces + 5 * C * nx * ny
+
+
+def residual_adjoint_flops(ndim: int, r: int, nx: int, ny: int) -> float:
+    """Algorithmic flops of one residual VJP: the forward recomputed, and one multiply-add
+    per edge of its graph in the reverse sweep (VJP_EDGES_PER_OP edges per operation)."""
+    return residual_flops(ndim, r, nx, ny) * (1.0 + 2.0 * VJP_EDGES_PER_OP[r])
+
+
 def fp64_peak_tflops(torch, clk_mhz: float = 2070.0) -> float:
     """2 FP64 FMA per cycle per SM x SMs x SM clock x 2 flops (default: the maximum clock)."""
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -512,6 +533,19 @@ def batched_bench(A, torch, args):
     }
 
 
+def adjoint_roofline(torch, pb, order, adj_ms):
+    flops = residual_adjoint_flops(pb.ndim, order, pb.nx, pb.ny)
+    peak = fp64_peak_tflops(torch)
+    achieved = flops / (adj_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "residual adjoint: face, normal and gather kernels of both directions",
+            "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "flops": flops,
+            "model": "the forward residual's algorithmic flops x (1 + 2 x %.4f): one multiply-add per edge of "
+                     "the reverse-mode graph, the oracle tape's %.4f edges per operation at order %d"
+                     % (VJP_EDGES_PER_OP[order], VJP_EDGES_PER_OP[order], order),
+            "peak_source": "2 FP64 FMA/cycle/SM x SMs x 2070 MHz x 2 flops"}
+
+
 def adjoint_bench(A, torch, args):
     """The adjoint workload: vortex 256^2 with a seeded 1% density perturbation, order 7,
     50 SSP-RK3 steps at the t = 0 CFL dt, checkpoints every 10 steps, J = sum rho_final^2.
@@ -600,6 +634,7 @@ def adjoint_bench(A, torch, args):
         "residual_ms": round(res_ms, 4),
         "residual_adjoint_ms": round(adj_ms, 4),
         "residual_adjoint_over_residual": round(adj_ms / res_ms, 3),
+        "residual_adjoint_roofline": adjoint_roofline(torch, pb, order, adj_ms),
         "grad_norm": float(torch.linalg.vector_norm(G)),
         "repaired_cells": marked,
     }

@@ -1717,6 +1717,10 @@ std::vector<real> tape_inputs(const double* a, int64_t n) {
 }
 
 // adjoint accumulation from the seeds (id, weight)
+// Edges (operation, non-constant operand) of the graph of the last residual VJP: the
+// reverse sweep does one multiply-add per edge.
+int64_t g_last_edges = 0;
+
 std::vector<double> backward(const std::vector<std::pair<int64_t, double>>& seeds) {
   std::vector<double> adj(g_tape.size(), 0.0);
   for (auto& sd : seeds)
@@ -1764,10 +1768,16 @@ int64_t oracle_residual_vjp(const OracleParams* p, const double* W, const double
   gather(sxi, adj, sxbar_in);
   if (p->ndim == 2) gather(syi, adj, sybar_in);
   const int64_t n = (int64_t)g_tape.size();
+  g_last_edges = 0;
+  for (const TapeNode& t : g_tape) g_last_edges += (t.a >= 0) + (t.b >= 0);
   g_tape.clear();
   g_tape.shrink_to_fit();
   return n;
 }
+
+// Edges of the graph of the last oracle_residual_vjp (one multiply-add each in its
+// reverse sweep).
+int64_t oracle_last_vjp_edges() { return g_last_edges; }
 
 // Reverse mode through sigma^0 = prime(W0) and nsteps SSP-RK3 steps of fixed dt:
 // Wbar0 += (dW_final/dW0)^T Wbar_final.  Returns the tape length (or -1 if a step went

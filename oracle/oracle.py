@@ -114,6 +114,8 @@ def _lib(counting: bool = False, tape: bool = False):
             lib.oracle_residual_vjp.restype = ctypes.c_int64
             lib.oracle_run_vjp.argtypes = [ctypes.POINTER(_Params), _P, ctypes.c_int32, ctypes.c_double, _P, _P]
             lib.oracle_run_vjp.restype = ctypes.c_int64
+            lib.oracle_last_vjp_edges.argtypes = []
+            lib.oracle_last_vjp_edges.restype = ctypes.c_int64
         _libs[key] = lib
     return _libs[key]
 
@@ -312,6 +314,11 @@ def op_counts_residual(pb, W, sx, sy):
     out = (ctypes.c_longlong * 4)()
     lib.oracle_op_counts(out)
     return tuple(int(v) for v in out)
+
+
+def last_vjp_edges() -> int:
+    """Edges (operation, non-constant operand) of the graph of the last residual_vjp."""
+    return int(_lib(tape=True).oracle_last_vjp_edges())
 
 
 def residual_vjp(pb, W, sx, sy, Lbar, sxbar_out=None, sybar_out=None):

@@ -280,6 +280,7 @@ ase_df_status ase_df_init(const ase_df_params* pin, ase_df_ctx** out) {
   const GridInfo& g = c->g;
   build_tables(p.order, p.ndim, &c->tab);
   build_dtables(p.order, p.ndim, &c->dtab);
+  set_flux_weights(c->g, c->tab);
 
   const size_t nW = (size_t)C * g.nx * g.ny;
   const size_t nFx = (size_t)C * g.ny * (g.nx + 1);

@@ -562,6 +562,7 @@ ase_df_status ase_df_batch_init(const ase_df_params* p, int32_t n, ase_df_batch*
   }
   std::vector<Tables> tabs(8);
   for (int v = 0; v < 8; ++v) build_tables(3 + 2 * (v % 4), 1 + v / 4, &tabs[v]);
+  for (int i = 0; i < n; ++i) set_flux_weights(desc[i].g, tabs[desc[i].variant]);
   const size_t yw = (size_t)std::max<long long>(1, y);
   struct { void** ptr; size_t bytes; } allocs[] = {
     {(void**)&b->d_prob, sizeof(BatchProblem) * n}, {(void**)&b->d_state, sizeof(DevState) * n},

@@ -29,15 +29,15 @@ __device__ __forceinline__ double flux_div(double dFx, double inv_dx, double dFy
   return -__dadd_rn(__dmul_rn(dFx, inv_dx), __dmul_rn(dFy, inv_dy));
 }
 
-// rho > 0 and p > 0 (tested on p rho = (gamma-1)(E rho - |m|^2/2)), all finite; the
-// comparisons run on the bit patterns (pos_finite), which decide exactly as
-// (rho > 0) && (p rho > 0) && isfinite(p rho) (an infinite rho makes p rho non-finite).
+// rho > 0 and p > 0, all finite, tested on p rho / (gamma - 1) = E rho - |m|^2 / 2 (no
+// division; gamma > 1, so the sign is that of p); the comparisons run on the bit patterns
+// (pos_finite), which decide exactly as (rho > 0) && (x > 0) && isfinite(x) for
+// x = E rho - |m|^2 / 2 (an infinite rho makes x non-finite).
 template <int C>
-__device__ __forceinline__ bool physical_state(const double* q, double gamma) {
+__device__ __forceinline__ bool physical_state(const double* q, double /*gamma*/) {
   double mm = q[1] * q[1];
   if (C == 4) mm = fma(q[2], q[2], mm);
-  const double pr = (gamma - 1.0) * fma(q[C - 1], q[0], -0.5 * mm);
-  return pos_finite(q[0]) && pos_finite(pr);
+  return pos_finite(q[0]) && pos_finite(fma(q[C - 1], q[0], -0.5 * mm));
 }
 
 // isfinite on the bit pattern (exponent field not all ones)
@@ -73,19 +73,28 @@ __device__ __forceinline__ void combine_range(const GridInfo& g, const CombineAr
   }
   bool bad = false;
   unsigned int nmarked = 0;
+  // The stage's weight of dt L (1, 1/4, 2/3 for SSP-RK3 stages 1, 2, 3; stage 0 gives L
+  // itself) is folded into the inverse spacings, so that -(dFx kx + dFy ky) is that
+  // weighted update, formed as one rounded product per direction and one add (symmetric in
+  // x and y bit for bit when dx = dy).
+  const double wdt = (a.stage == 0) ? 1.0 : (a.stage == 1) ? dt : (a.stage == 2) ? 0.25 * dt : (2.0 / 3.0) * dt;
+  const double kx = wdt * a.inv_dx, ky = wdt * a.inv_dy;
   for (size_t n = first; n < last; n += stride) {
     const int i = (int)(n % nx), j = (int)(n / nx);
     double q[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const size_t fx = ((size_t)c * ny + j) * (nx + 1) + i;
-      double L = -(a.Fx[fx + 1] - a.Fx[fx]) * a.inv_dx;
+      double t = -(a.Fx[fx + 1] - a.Fx[fx]) * kx;
       if (DIM == 2) {
         const size_t fy = ((size_t)c * (ny + 1) + j) * nx + i;
-        L = flux_div(a.Fx[fx + 1] - a.Fx[fx], a.inv_dx, a.Fy[fy + nx] - a.Fy[fy], a.inv_dy);
+        t = flux_div(a.Fx[fx + 1] - a.Fx[fx], kx, a.Fy[fy + nx] - a.Fy[fy], ky);
       }
       const size_t w = (size_t)c * ncell + n;
-      q[c] = (a.stage == 0) ? L : rk_stage(a.stage, dt, a.Wn[w], a.Ws[w], L);
+      if (a.stage == 0) q[c] = t;
+      else if (a.stage == 1) q[c] = a.Ws[w] + t;
+      else if (a.stage == 2) q[c] = fma(0.75, a.Wn[w], fma(0.25, a.Ws[w], t));
+      else q[c] = fma(1.0 / 3.0, a.Wn[w], fma(2.0 / 3.0, a.Ws[w], t));
       a.out[w] = q[c];
       if (!finite_bits(q[c])) bad = true;
     }

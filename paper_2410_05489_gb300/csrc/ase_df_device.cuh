@@ -159,7 +159,7 @@ __device__ __forceinline__ double sigma_y_at(const GridInfo& g, const double* __
 // sigma = 1e30.  gm1 = gamma - 1 and gg1 = gamma (gamma - 1) come from the caller.
 //
 // The FP64 pipe bounds the face kernels, so the point is arranged for few FP64
-// instructions (60 in 2D on the physical path):
+// instructions (58 in 2D on the physical path, its Gauss-weighted accumulation included):
 //   - one reciprocal gives 1/rho of both sides: 1/rho_l = rho_r / (rho_l rho_r);
 //   - the pressure is kept as p' = p / (gamma - 1) = E - (m_n u_n + m_t u_t) / 2, so that
 //     (gamma - 1) multiplies only the sums that need it;
@@ -167,56 +167,74 @@ __device__ __forceinline__ double sigma_y_at(const GridInfo& g, const double* __
 //     c = c^2 / c;
 //   - 1/p' = gg1 (1/rho) (1/c)^2 gives the pressure term of sigma without a reciprocal;
 //   - the flux sum F_l + F_r - lambda (q_r - q_l) is formed per component as
-//     q_l (u_l + lambda) + q_r (u_r - lambda) + pressure terms.
-// The flux is returned as 2F (the 1/2 of the L-F formula is folded into the Gauss
-// weight by the caller).
+//     q_l (u_l + lambda) + q_r (u_r - lambda) + pressure terms, and accumulated into the
+//     caller's Gauss sum in the same FMAs.
+// The point adds w (2F) to Fs (w: the Gauss weight with the 1/2 of the L-F formula folded
+// in; gw = (gamma - 1) w), with w folded into the speeds u +- lambda so that each component
+// takes two FMAs on top of its pressure term.
+// Primitives of the two states of a Gauss point (face frame: NI normal, TI tangential
+// momentum): 1/rho, u_n, u_t and p' = p / (gamma - 1) of each side, from one reciprocal.
+struct LfPrims {
+  double irL, irR, unL, unR, utL, utR, pL, pR;
+};
+
 template <int C, int NI, int TI>
-__device__ __forceinline__ bool lf_point(const double* qa, const double* qb, const double* ca,
-                                         const double* cb, int cs, double gm1, double gg1, double* F2,
-                                         double& sigma) {
+__device__ __forceinline__ LfPrims lf_primitives(const double* a, const double* b) {
+  LfPrims s;
+  const double irr = rcp_pos(a[0] * b[0]);
+  s.irL = b[0] * irr;
+  s.irR = a[0] * irr;
+  s.unL = a[NI] * s.irL;
+  s.unR = b[NI] * s.irR;
+  double kL = a[NI] * s.unL, kR = b[NI] * s.unR;  // |m|^2 / rho
+  s.utL = s.utR = 0.0;
+  if (C == 4) {
+    s.utL = a[TI] * s.irL;
+    s.utR = b[TI] * s.irR;
+    kL = fma(a[TI], s.utL, kL);
+    kR = fma(b[TI], s.utR, kR);
+  }
+  s.pL = fma(-0.5, kL, a[C - 1]);
+  s.pR = fma(-0.5, kR, b[C - 1]);
+  return s;
+}
+
+// Both states physical: rho > 0 and p > 0, all finite (on the bit patterns).
+__device__ __forceinline__ bool lf_physical(double rhoL, double rhoR, const LfPrims& s) {
+  return pos_finite(rhoL) && pos_finite(rhoR) && pos_finite(s.pL) && pos_finite(s.pR);
+}
+
+template <int C, int NI, int TI>
+__device__ __forceinline__ bool lf_point_acc(const double* qa, const double* qb, const double* ca,
+                                             const double* cb, int cs, double gm1, double gg1, double w,
+                                             double gw, double* Fs, double& sigma) {
   double a[C], b[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     a[c] = qa[c];
     b[c] = qb[c];
   }
-  double irL, irR, unL, unR, utL = 0.0, utR = 0.0, pL, pR;
-  auto primitives = [&]() {
-    const double irr = rcp_pos(a[0] * b[0]);
-    irL = b[0] * irr;
-    irR = a[0] * irr;
-    unL = a[NI] * irL;
-    unR = b[NI] * irR;
-    double kL = a[NI] * unL, kR = b[NI] * unR;  // |m|^2 / rho
-    if (C == 4) {
-      utL = a[TI] * irL;
-      utR = b[TI] * irR;
-      kL = fma(a[TI], utL, kL);
-      kR = fma(b[TI], utR, kR);
-    }
-    pL = fma(-0.5, kL, a[C - 1]);  // p / (gamma - 1)
-    pR = fma(-0.5, kR, b[C - 1]);
-  };
-  primitives();
-  const bool ok = pos_finite(a[0]) && pos_finite(b[0]) && pos_finite(pL) && pos_finite(pR);
+  LfPrims s = lf_primitives<C, NI, TI>(a, b);
+  const bool ok = lf_physical(a[0], b[0], s);
   if (!ok) {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       a[c] = ca[c * cs];
       b[c] = cb[c * cs];
     }
-    primitives();
+    s = lf_primitives<C, NI, TI>(a, b);
   }
+  const double irL = s.irL, irR = s.irR, unL = s.unL, unR = s.unR, utL = s.utL, utR = s.utR;
+  const double pL = s.pL, pR = s.pR;
   const double c2L = (gg1 * pL) * irL, c2R = (gg1 * pR) * irR;
   const double icL = rsqrt_pos(c2L), icR = rsqrt_pos(c2R);
   // lambda = max(|u_n| + c) with c = c^2 / c
   const double lam = max_nonneg(fma(c2L, icL, fabs(unL)), fma(c2R, icR, fabs(unR)));
-  const double alL = unL + lam, alR = unR - lam;
-  const double sp = pL + pR;
-  F2[0] = fma(a[0], alL, b[0] * alR);
-  F2[NI] = fma(a[NI], alL, fma(b[NI], alR, gm1 * sp));
-  if (C == 4) F2[TI] = fma(a[TI], alL, b[TI] * alR);
-  F2[C - 1] = fma(a[C - 1], alL, fma(b[C - 1], alR, gm1 * fma(unL, pL, unR * pR)));
+  const double alL = w * (unL + lam), alR = w * (unR - lam);
+  Fs[0] = fma(a[0], alL, fma(b[0], alR, Fs[0]));
+  Fs[NI] = fma(a[NI], alL, fma(b[NI], alR, fma(gw, pL + pR, Fs[NI])));
+  if (C == 4) Fs[TI] = fma(a[TI], alL, fma(b[TI], alR, Fs[TI]));
+  Fs[C - 1] = fma(a[C - 1], alL, fma(b[C - 1], alR, fma(gw, fma(unL, pL, unR * pR), Fs[C - 1])));
   if (ok) {
     // sigma = |dp| (1/p_l + 1/p_r) + (dMa_n)^2 + (dMa_t)^2, Ma = u / c
     const double dmn = fma(unL, icL, -unR * icR);
@@ -232,6 +250,17 @@ __device__ __forceinline__ bool lf_point(const double* qa, const double* qb, con
     sigma = kSigmaBig;
   }
   return !ok;
+}
+
+// The flux of one point as 2F = F_l + F_r - lambda (q_r - q_l), and sigma (lf_point_acc with
+// weight 1).
+template <int C, int NI, int TI>
+__device__ __forceinline__ bool lf_point(const double* qa, const double* qb, const double* ca,
+                                         const double* cb, int cs, double gm1, double gg1, double* F2,
+                                         double& sigma) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) F2[c] = 0.0;
+  return lf_point_acc<C, NI, TI>(qa, qb, ca, cb, cs, gm1, gg1, 1.0, gm1, F2, sigma);
 }
 
 }  // namespace

@@ -117,6 +117,7 @@ struct GridInfo {
   double inflow_cons[4];
   double gamma;
   double gm1, gg1;    // gamma - 1 and gamma (gamma - 1), for the flux kernels
+  double gm1_hgw[4] = {0.0, 0.0, 0.0, 0.0};  // (gamma - 1) x half Gauss weight of each point
   double thres;
   // BC_WALL_AFTER (y-lo): columns i < wall_i0 (centre x below wall_x) have fixed ghosts
   int wall_i0 = 0;
@@ -173,6 +174,12 @@ struct SpeedArgs {
   DevState* st;
   double inv_dx, inv_dy;
 };
+
+// Sets g.gm1_hgw from the tables of the problem's order (call after g.gm1 and the tables
+// are known).
+inline void set_flux_weights(GridInfo& g, const Tables& t) {
+  for (int q = 0; q < 4; ++q) g.gm1_hgw[q] = g.gm1 * t.hgw[q];
+}
 
 // A validated problem and what the kernels derive from it; shared by ase_df_init and
 // ase_df_residual_noalloc, so that both accept the same problems and describe them to the

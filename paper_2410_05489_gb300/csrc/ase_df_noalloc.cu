@@ -132,6 +132,8 @@ extern "C" ase_df_status ase_df_residual_noalloc(const ase_df_params* pin, const
     tab = &g_tables[di][oi];
   }
 
+  GridInfo g = ps.g;
+  set_flux_weights(g, *tab);
   DevState* st = reinterpret_cast<DevState*>(base);
   double* Fx = base + kStatusDoubles;
   double* Fy = Fx + nFx;
@@ -147,10 +149,10 @@ extern "C" ase_df_status ase_df_residual_noalloc(const ase_df_params* pin, const
     a.s_out = (dir == 0) ? sx_out : sy_out;
     a.st = st;
     switch (p.order) {
-      case 3: e = launch_sweep_r3(p.ndim, dir, ps.g, a, *tab, s); break;
-      case 5: e = launch_sweep_r5(p.ndim, dir, ps.g, a, *tab, s); break;
-      case 7: e = launch_sweep_r7(p.ndim, dir, ps.g, a, *tab, s); break;
-      default: e = launch_sweep_r9(p.ndim, dir, ps.g, a, *tab, s); break;
+      case 3: e = launch_sweep_r3(p.ndim, dir, g, a, *tab, s); break;
+      case 5: e = launch_sweep_r5(p.ndim, dir, g, a, *tab, s); break;
+      case 7: e = launch_sweep_r7(p.ndim, dir, g, a, *tab, s); break;
+      default: e = launch_sweep_r9(p.ndim, dir, g, a, *tab, s); break;
     }
     if (e != cudaSuccess) return nfail(ASE_DF_E_CUDA, "sweep: %s", cudaGetErrorString(e));
   }
@@ -165,7 +167,7 @@ extern "C" ase_df_status ase_df_residual_noalloc(const ase_df_params* pin, const
   c.inv_dx = ps.inv_dx;
   c.inv_dy = ps.inv_dy;
   c.stage = 0;
-  e = launch_combine(p.ndim, ps.g, c, s);
+  e = launch_combine(p.ndim, g, c, s);
   if (e != cudaSuccess) return nfail(ASE_DF_E_CUDA, "combine: %s", cudaGetErrorString(e));
   return ASE_DF_OK;
 }

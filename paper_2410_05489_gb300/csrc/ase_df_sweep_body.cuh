@@ -359,10 +359,9 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
     unsigned int nfb = 0u;
 #pragma unroll
     for (int q = 0; q < G; ++q) {
-      double F[C], sg;
-      nfb += lf_point<C, NI, TI>(st[0][q], st[1][q], ca, cb, NB * NA, g.gm1, g.gg1, F, sg) ? 1u : 0u;
-#pragma unroll
-      for (int c = 0; c < C; ++c) Fs[c] = fma((DIM == 2) ? T.hgw[q] : 0.5, F[c], Fs[c]);
+      double sg;
+      nfb += lf_point_acc<C, NI, TI>(st[0][q], st[1][q], ca, cb, NB * NA, g.gm1, g.gg1, T.hgw[q], g.gm1_hgw[q],
+                                     Fs, sg) ? 1u : 0u;
       ssum += sg;
     }
     if (nfb) {

@@ -44,3 +44,19 @@ def test_gauss_point_flops_are_the_oracles_count_less_one_half_per_component(ndi
 def test_face_flops_of_the_roofline():
     # 2D, per face of one sweep: 2 C (2r-1) + 2 C G (2r-1) + G (70 + 2 C + 1) + 1
     assert [bench.algorithmic_flops_per_face(2, r) for r in (3, 5, 7, 9)] == [160, 375, 654, 997]
+
+
+@pytest.mark.parametrize("r", [5, 7, 9])
+def test_vjp_edges_per_operation_of_the_adjoint_model(r):
+    """The residual adjoint's flop model scales the forward's algorithmic flops by
+    1 + 2 e, e the edges per operation of the reverse-mode graph (one multiply-add per edge in
+    the reverse sweep); e is the oracle tape's on smooth 2D data."""
+    from paper_2410_05489_gb300 import problems as P
+
+    pb = P.Problem(ndim=2, nx=32, ny=32, order=r, bc=("periodic",) * 4, x1=2.0, y1=2.0)
+    W = P.smooth_random(pb, 3)
+    sx, sy = P.zero_sigma(pb)
+    O.residual_vjp(pb, W, sx, sy, np.random.default_rng(1).normal(size=W.shape))
+    edges = O.last_vjp_edges()
+    ops = sum(O.op_counts_residual(pb, W, sx, sy))
+    assert abs(bench.VJP_EDGES_PER_OP[r] - edges / ops) < 1e-3 * bench.VJP_EDGES_PER_OP[r]
