@@ -486,6 +486,9 @@ def batched_bench(A, torch, args):
     from paper_2410_05489_gb300 import batch as Bt
 
     probs = P.batched_problems()
+    cut = getattr(args, "batch_cut", 0)
+    if cut:  # the first cut/2 1D and the first cut/2 2D problems (the set lists the 256 1D ones first)
+        probs = probs[:cut // 2] + probs[256:256 + cut - cut // 2]
     bt = Bt.Batch([p for p, _ in probs], [w for _, w in probs])
     tune = Bt.autotune(bt, steps=1)
     bt.run(args.warmup)
@@ -961,11 +964,25 @@ def main():
                     help="time only the gas-kinetic path on Configuration 3 (--n, --order, --steps)")
     ap.add_argument("--suite", action="store_true",
                     help="measure every workload configuration (GPU and CPU oracle) instead of the headline line")
+    ap.add_argument("--only", choices=("batched", "adjoint"),
+                    help="time only the batched or only the adjoint workload (one JSON line; for profiling)")
+    ap.add_argument("--batch-cut", type=int, default=0,
+                    help="with --only batched: the first N/2 1D and the first N/2 2D problems of the batched set")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()
-    if args.gks:
+    if args.only:
+        if rank == 0:
+            import torch
+
+            from paper_2410_05489_gb300 import ase_df as A
+            from paper_2410_05489_gb300 import build
+
+            build.build()
+            out = batched_bench(A, torch, args) if args.only == "batched" else adjoint_bench(A, torch, args)
+            print(json.dumps(out), flush=True)
+    elif args.gks:
         if rank == 0:
             gks_bench(args)
     elif args.suite:

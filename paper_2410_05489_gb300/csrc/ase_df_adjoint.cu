@@ -59,6 +59,20 @@ __device__ __forceinline__ double dabs(double x, double scale) {
   return (x < 0.0) ? -1.0 : 1.0;
 }
 
+// Scratch layouts of one direction: face f (0..n) of line b (0..m-1), and reconstructing
+// cell a (-1..n) of line l (-KT..m-1+KT).  The index runs fastest along the direction in
+// which the state arrays are contiguous (along the sweep for x-faces, along the lines for
+// y-faces), so that the threads of a warp, which the kernels also order that way, touch
+// consecutive addresses.
+template <int DIR>
+__device__ __forceinline__ size_t adj_face(int f, int b, int n, int m) {
+  return (DIR == 0) ? (size_t)b * (n + 1) + f : (size_t)f * m + b;
+}
+template <int DIR>
+__device__ __forceinline__ size_t adj_item(int a, int l, int n, int m, int KT) {
+  return (DIR == 0) ? (size_t)(l + KT) * (n + 2) + (a + 1) : (size_t)(a + 1) * (m + 2 * KT) + (l + KT);
+}
+
 // ---------------------------------------------------------------------------------
 // reconstruction VJPs.  Stencil values v[t*vs] (t = -K..K); vbc points at the adjoint
 // of W_0 in a unit-stride array; ab[0..2] accumulate the adjoints of alpha of S3_{-1},
@@ -231,150 +245,107 @@ __device__ __forceinline__ void sigma_vjp(const Branch& br, const double* ab, do
 }
 
 // ---------------------------------------------------------------------------------
-// Lax-Friedrichs point VJP (the derivative of lf_point)
+// Lax-Friedrichs point VJP (the derivative of lf_point_acc)
 // ---------------------------------------------------------------------------------
-// Primitives of one side with 1/rho and 1/c: FP64 division and square root take 6-9 FMA
-// issue slots on this part, so they come from the seeded reciprocal and reciprocal square
-// root of the forward flux (rcp_pos, rsqrt_pos) and the VJP multiplies by them.
-struct SidePrim {
-  double rho, u, w, p, c, E, ir, ic;  // ir = 1 / rho, ic = 1 / c
-};
-
+// The forward point, in the primitives of lf_primitives (p' = p / (gamma - 1)):
+//   2F_c  = a_c (u_L + lambda) + b_c (u_R - lambda) + P_c,
+//           P = (0, (gamma-1)(p'_L + p'_R), 0, (gamma-1)(u_L p'_L + u_R p'_R)) (face frame)
+//   lambda = max(|u_L| + c_L, |u_R| + c_R),  c^2 = gamma (gamma-1) p' / rho,  ic = 1 / c
+//   sigma = (u_L ic_L - u_R ic_R)^2 + (w_L ic_L - w_R ic_R)^2
+//           + gamma (gamma-1) |p'_L - p'_R| (ic_L^2 / rho_L + ic_R^2 / rho_R)
+// and p' = E - (m_n u + m_t w) / 2, u = m_n / rho, w = m_t / rho.  Given F2b (adjoint of 2F)
+// and sb (adjoint of sigma, used only on a physical point: a first-order point has the
+// constant sigma 1e30), sets ab / bb to the adjoints of the states a / b.  |x| and max take
+// the symmetric subgradient near their kinks (reading G23, kKink).
+// s = lf_primitives(a, b).
 template <int C, int NI, int TI>
-__device__ __forceinline__ SidePrim side_prim(const double* q, double gamma) {
-  SidePrim s;
-  s.rho = q[0];
-  const double ir = rcp_pos(q[0]);
-  s.ir = ir;
-  s.u = q[NI] * ir;
-  s.w = (C == 4) ? q[TI] * ir : 0.0;
-  s.E = q[C - 1];
-  s.p = (gamma - 1.0) * (s.E - 0.5 * q[0] * (s.u * s.u + s.w * s.w));
-  const double c2 = gamma * s.p * ir;
-  s.ic = rsqrt_pos(c2);
-  s.c = c2 * s.ic;
-  return s;
-}
-
-// Adjoints of the primitives (u, w, p, c) -> adjoint of the conservative state (+=),
-// with p = (gamma-1)(E - |m|^2 / (2 rho)), u = m_n / rho, w = m_t / rho,
-// c = sqrt(gamma p / rho).
-template <int C, int NI, int TI>
-__device__ __forceinline__ void side_back(const SidePrim& s, double gamma, double ub, double wb, double pb,
-                                          double cb, double* qb) {
-  const double ir = s.ir;
-  pb += cb * gamma * ir * (0.5 * s.ic);
-  double rb = -cb * s.c * 0.5 * ir;
-  const double g1 = gamma - 1.0;
-  qb[C - 1] += g1 * pb;
-  qb[NI] -= g1 * pb * s.u;
-  if (C == 4) qb[TI] -= g1 * pb * s.w;
-  rb += g1 * pb * 0.5 * (s.u * s.u + s.w * s.w);
-  qb[NI] += ub * ir;
-  rb -= ub * s.u * ir;
-  if (C == 4) {
-    qb[TI] += wb * ir;
-    rb -= wb * s.w * ir;
-  }
-  qb[0] += rb;
-}
-
-// Given F2b (adjoint of 2F, the value lf_point returns) and sb (adjoint of sigma),
-// accumulates the adjoints of the two reconstructed states, or, where the point took
-// the first-order states, of the two cell averages.
-template <int C, int NI, int TI>
-__device__ void lf_point_vjp(const double* qa, const double* qb_, const double* ca, const double* cb, double gamma,
-                             const double* F2b, double sb, double* qab, double* qbb, double* cab, double* cbb) {
-  double mmL = qa[NI] * qa[NI], mmR = qb_[NI] * qb_[NI];
-  if (C == 4) {
-    mmL = fma(qa[TI], qa[TI], mmL);
-    mmR = fma(qb_[TI], qb_[TI], mmR);
-  }
-  const double prL = (gamma - 1.0) * fma(qa[C - 1], qa[0], -0.5 * mmL);
-  const double prR = (gamma - 1.0) * fma(qb_[C - 1], qb_[0], -0.5 * mmR);
-  const bool ok = (qa[0] > 0.0) && (qb_[0] > 0.0) && (prL > 0.0) && (prR > 0.0) && isfinite(prL) &&
-                  isfinite(prR);
-  double a[C], b[C];
+__device__ __forceinline__ void lf_point_vjp(const double* a, const double* b, const LfPrims& s, double gm1,
+                                             double gg1, const double* F2b, double sb, bool physical, double* ab,
+                                             double* bb) {
+  const double c2L = (gg1 * s.pL) * s.irL, c2R = (gg1 * s.pR) * s.irR;
+  const double icL = rsqrt_pos(c2L), icR = rsqrt_pos(c2R);
+  const double cL = c2L * icL, cR = c2R * icR;
+  const double sL = fabs(s.unL) + cL, sR = fabs(s.unR) + cR;
+  const double lam = fmax(sL, sR);
+  // direct terms of 2F and the adjoints of u, p', lambda
+  double uLb = 0.0, uRb = 0.0, lamb = 0.0;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    a[c] = ok ? qa[c] : ca[c];
-    b[c] = ok ? qb_[c] : cb[c];
+    ab[c] = F2b[c] * (s.unL + lam);
+    bb[c] = F2b[c] * (s.unR - lam);
+    uLb = fma(F2b[c], a[c], uLb);
+    uRb = fma(F2b[c], b[c], uRb);
+    lamb = fma(F2b[c], a[c] - b[c], lamb);
   }
-  double ab_[C], bb_[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) ab_[c] = bb_[c] = 0.0;
-  const SidePrim L = side_prim<C, NI, TI>(a, gamma);
-  const SidePrim R = side_prim<C, NI, TI>(b, gamma);
-  const double sL = fabs(L.u) + L.c, sR = fabs(R.u) + R.c;
-  const double lam = fmax(sL, sR);
-  // share of d lam going to the left / right speed
+  uLb = fma(F2b[C - 1] * gm1, s.pL, uLb);
+  uRb = fma(F2b[C - 1] * gm1, s.pR, uRb);
+  double pLb = gm1 * fma(F2b[C - 1], s.unL, F2b[NI]);
+  double pRb = gm1 * fma(F2b[C - 1], s.unR, F2b[NI]);
+  // lambda = max(s_L, s_R), s = |u| + c
   double tL = (sL < sR) ? 0.0 : 1.0;
   if (fabs(sL - sR) <= kKink * (sL + sR)) tL = 0.5;
-  const double tR = 1.0 - tL;
-  // 2F = F(a) + F(b) - lam (b - a)
-  double lamb = 0.0;
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    lamb -= F2b[c] * (b[c] - a[c]);
-    ab_[c] += lam * F2b[c];
-    bb_[c] -= lam * F2b[c];
-  }
-  // F(q) = (m_n, m_n u + p, m_n w, u (E + p)) in the face frame
-  double uLb = F2b[NI] * a[NI] + F2b[C - 1] * (L.E + L.p);
-  double uRb = F2b[NI] * b[NI] + F2b[C - 1] * (R.E + R.p);
-  double pLb = F2b[NI] + F2b[C - 1] * L.u;
-  double pRb = F2b[NI] + F2b[C - 1] * R.u;
-  double wLb = 0.0, wRb = 0.0, cLb = 0.0, cRb = 0.0;
-  ab_[NI] += F2b[0] + F2b[NI] * L.u;
-  bb_[NI] += F2b[0] + F2b[NI] * R.u;
-  if (C == 4) {
-    ab_[NI] += F2b[TI] * L.w;
-    bb_[NI] += F2b[TI] * R.w;
-    wLb += F2b[TI] * a[NI];
-    wRb += F2b[TI] * b[NI];
-  }
-  ab_[C - 1] += F2b[C - 1] * L.u;
-  bb_[C - 1] += F2b[C - 1] * R.u;
-  // lam = max(|u_L| + c_L, |u_R| + c_R), piecewise
-  uLb += tL * lamb * dabs(L.u, L.c);
-  cLb += tL * lamb;
-  uRb += tR * lamb * dabs(R.u, R.c);
-  cRb += tR * lamb;
-  // sigma = |pL - pR| (1/pL + 1/pR) + (uL/cL - uR/cR)^2 + (wL/cL - wR/cR)^2; constant
-  // (1e30) at a first-order point
-  if (ok && sb != 0.0) {
-    const double dp = L.p - R.p;
-    const double sg = dabs(dp, L.p + R.p);
-    const double adp = fabs(dp);
-    const double ipL = rcp_pos(L.p), ipR = rcp_pos(R.p);
-    const double h = ipL + ipR;
-    pLb += sb * (sg * h - adp * (ipL * ipL));
-    pRb += sb * (-sg * h - adp * (ipR * ipR));
-    const double dmn = L.u * L.ic - R.u * R.ic;
-    uLb += sb * 2.0 * dmn * L.ic;
-    uRb -= sb * 2.0 * dmn * R.ic;
-    cLb -= sb * 2.0 * dmn * L.u * (L.ic * L.ic);
-    cRb += sb * 2.0 * dmn * R.u * (R.ic * R.ic);
+  const double sLb = tL * lamb, sRb = (1.0 - tL) * lamb;
+  uLb = fma(sLb, dabs(s.unL, cL), uLb);
+  uRb = fma(sRb, dabs(s.unR, cR), uRb);
+  double cLb = sLb, cRb = sRb, icLb = 0.0, icRb = 0.0, irLb = 0.0, irRb = 0.0, wLb = 0.0, wRb = 0.0;
+  if (physical && sb != 0.0) {
+    const double dmn = fma(s.unL, icL, -s.unR * icR);
+    const double gn = 2.0 * sb * dmn;
+    uLb = fma(gn, icL, uLb);
+    uRb = fma(-gn, icR, uRb);
+    icLb = fma(gn, s.unL, icLb);
+    icRb = fma(-gn, s.unR, icRb);
     if (C == 4) {
-      const double dmt = L.w * L.ic - R.w * R.ic;
-      wLb += sb * 2.0 * dmt * L.ic;
-      wRb -= sb * 2.0 * dmt * R.ic;
-      cLb -= sb * 2.0 * dmt * L.w * (L.ic * L.ic);
-      cRb += sb * 2.0 * dmt * R.w * (R.ic * R.ic);
+      const double dmt = fma(s.utL, icL, -s.utR * icR);
+      const double gt = 2.0 * sb * dmt;
+      wLb = gt * icL;
+      wRb = -gt * icR;
+      icLb = fma(gt, s.utL, icLb);
+      icRb = fma(-gt, s.utR, icRb);
     }
+    const double dp = s.pL - s.pR;
+    const double S = fma(s.irL * icL, icL, s.irR * icR * icR);
+    const double gp = sb * gg1 * dabs(dp, s.pL + s.pR) * S;
+    pLb += gp;
+    pRb -= gp;
+    const double Sb = sb * gg1 * fabs(dp);
+    irLb = Sb * icL * icL;
+    irRb = Sb * icR * icR;
+    icLb = fma(2.0 * Sb * s.irL, icL, icLb);
+    icRb = fma(2.0 * Sb * s.irR, icR, icRb);
   }
-  side_back<C, NI, TI>(L, gamma, uLb, wLb, pLb, cLb, ab_);
-  side_back<C, NI, TI>(R, gamma, uRb, wRb, pRb, cRb, bb_);
-#pragma unroll
-  for (int c = 0; c < C; ++c) {
-    if (ok) {
-      qab[c] += ab_[c];
-      qbb[c] += bb_[c];
-    } else {
-      cab[c] += ab_[c];
-      cbb[c] += bb_[c];
-    }
+  // c = sqrt(c^2), ic = 1 / sqrt(c^2): dc/dc^2 = ic / 2, d ic / dc^2 = -ic^3 / 2;
+  // c^2 = gamma (gamma-1) p' / rho
+  const double c2Lb = 0.5 * icL * fma(-icLb, icL * icL, cLb);
+  const double c2Rb = 0.5 * icR * fma(-icRb, icR * icR, cRb);
+  pLb = fma(c2Lb * gg1, s.irL, pLb);
+  pRb = fma(c2Rb * gg1, s.irR, pRb);
+  irLb = fma(c2Lb * gg1, s.pL, irLb);
+  irRb = fma(c2Rb * gg1, s.pR, irRb);
+  // p' = E - (m_n u + m_t w) / 2
+  ab[C - 1] += pLb;
+  bb[C - 1] += pRb;
+  ab[NI] = fma(-0.5 * pLb, s.unL, ab[NI]);
+  bb[NI] = fma(-0.5 * pRb, s.unR, bb[NI]);
+  uLb = fma(-0.5 * pLb, a[NI], uLb);
+  uRb = fma(-0.5 * pRb, b[NI], uRb);
+  if (C == 4) {
+    ab[TI] = fma(-0.5 * pLb, s.utL, ab[TI]);
+    bb[TI] = fma(-0.5 * pRb, s.utR, bb[TI]);
+    wLb = fma(-0.5 * pLb, a[TI], wLb);
+    wRb = fma(-0.5 * pRb, b[TI], wRb);
+    ab[TI] = fma(wLb, s.irL, ab[TI]);
+    bb[TI] = fma(wRb, s.irR, bb[TI]);
+    irLb = fma(wLb, a[TI], irLb);
+    irRb = fma(wRb, b[TI], irRb);
   }
+  // u = m_n / rho, 1/rho
+  ab[NI] = fma(uLb, s.irL, ab[NI]);
+  bb[NI] = fma(uRb, s.irR, bb[NI]);
+  irLb = fma(uLb, a[NI], irLb);
+  irRb = fma(uRb, b[NI], irRb);
+  ab[0] = fma(-irLb * s.irL, s.irL, ab[0]);
+  bb[0] = fma(-irRb * s.irR, s.irR, bb[0]);
 }
 
 // ---------------------------------------------------------------------------------
@@ -422,17 +393,33 @@ __device__ __forceinline__ int face_preimages(int e, int n, int bl, int bh, int 
 // ---------------------------------------------------------------------------------
 // K1: face kernel
 // ---------------------------------------------------------------------------------
-// 16 x 16 faces per CTA in 2D: the face adjoint needs ~255 registers (one CTA per SM), and
-// the smaller tile gives more CTAs per grid than the forward sweep's 8 x 64.
+// 2D: 8 faces x 16 lines per CTA of 128 threads, one face per thread, three CTAs per SM;
+// 1D: 256 faces per CTA of 256 threads.  Phase A (per face) recomputes the two states at
+// each Gauss point and writes their adjoints to shared memory; phase B (per face and side)
+// takes them back through the tangential reconstruction.
 template <int R, int DIM>
-using AdjTile = Tile<R, DIM, (DIM == 2) ? 16 : 1, (DIM == 2) ? 16 : 256>;
+struct AdjShape {
+  static constexpr int TN = (DIM == 2) ? 8 : 256;
+  static constexpr int TT = (DIM == 2) ? 16 : 1;
+  static constexpr int NT = TN * TT;
+  static constexpr int MINB = (DIM == 2) ? 3 : 1;
+};
+
+template <int R, int DIM>
+using AdjTile = Tile<R, DIM, AdjShape<R, DIM>::TT, AdjShape<R, DIM>::TN>;
+
+template <int R, int DIM>
+constexpr size_t adj_smem_doubles() {
+  using TL = AdjTile<R, DIM>;
+  return TL::smem_doubles + (size_t)AdjShape<R, DIM>::NT * 2 * TL::G * TL::C;
+}
 
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(AdjTile<R, DIM>::NT, 1)
+__global__ void __launch_bounds__(AdjShape<R, DIM>::NT, AdjShape<R, DIM>::MINB)
 adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const __grid_constant__ Tables T) {
   using TL = AdjTile<R, DIM>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
-  constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
+  constexpr int TN = TL::TN, TT = TL::TT, NT = AdjShape<R, DIM>::NT;
   constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
   constexpr int NI = (DIR == 0) ? 1 : 2;
   constexpr int TI = (DIR == 0) ? 2 : 1;
@@ -444,6 +431,9 @@ adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const 
   double* sQM = sQP + C * NB * NQ;
   double* sSn = sQM + C * NB * NQ;
   double* sSt = sSn + NB * NSN;
+  // adjoints of the Gauss-point states, [side][G][C][face of the tile] (conflict-free: the
+  // threads of a warp take consecutive faces)
+  double* sStb = smem + TL::smem_doubles;
 
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int mlin = (DIR == 0) ? g.ny : g.nx;
@@ -461,15 +451,20 @@ adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const 
     const int i = (DIR == 0) ? a : b, j = (DIR == 0) ? b : a;
     sW[(c * NB + bb) * NA + ai] = fetch_w(g, args.W, c, i, j, 0.0);
   }
+  // sigma staging: consecutive threads take consecutive entries of the global arrays
   for (int idx = tid; idx < NB * NSN; idx += NT) {
-    const int fa = idx % NSN, bb = idx / NSN;
+    int fa, bb;
+    if (DIR == 0) { fa = idx % NSN; bb = idx / NSN; }
+    else { bb = idx % NB; fa = idx / NB; }
     const int f = face_map(a0 - K + fa, n, bcn_lo, bcn_hi);
     const int b = wrap_or_clamp(b0 - KT + bb, mlin, bct_lo, bct_hi);
     sSn[bb * NSN + fa] = (DIR == 0) ? args.s_norm[(size_t)b * (g.nx + 1) + f] : args.s_norm[(size_t)f * g.nx + b];
   }
   if (DIM == 2) {
     for (int idx = tid; idx < NQ * (NST - 1); idx += NT) {
-      const int qa = idx % NQ, fb = idx / NQ;
+      int qa, fb;
+      if (DIR == 0) { qa = idx % NQ; fb = idx / NQ; }
+      else { fb = idx % (NST - 1); qa = idx / (NST - 1); }
       const int a = wrap_or_clamp(a0 - 1 + qa, n, bcn_lo, bcn_hi);
       const int f = face_map(b0 - K + 1 + fb, mlin, bct_lo, bct_hi);
       sSt[qa * NST + fb] = (DIR == 0) ? args.s_tan[(size_t)f * g.nx + a] : args.s_tan[(size_t)a * (g.nx + 1) + f];
@@ -490,106 +485,133 @@ adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const 
   }
   __syncthreads();
 
-  // ---- per face: recompute the Gauss-point states, back-propagate ----
   const size_t nfaces = (size_t)(n + 1) * mlin;
   const double fscale = aa.lscale * aa.inv_h;
-  for (int it = tid; it < TN * TT; it += NT) {
-    int fa, tb;
+  auto face_of = [&](int it, int& fa, int& tb) {
     if (DIR == 0) { fa = it % TN; tb = it / TN; }
     else { tb = it % TT; fa = it / TT; }
+  };
+
+  // ---- phase A (per face): the Gauss-point flux VJPs ----
+  {
+    const int it = tid;  // NT = TN * TT: one face per thread
+    int fa, tb;
+    face_of(it, fa, tb);
     const int f = a0 + fa, b = b0 + tb;
-    if (f > n || b >= mlin) continue;
-    const size_t face = (size_t)b * (n + 1) + f;
-    // F_f enters L of cell f with +1/h and L of cell f-1 with -1/h
-    double Fb[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      double lb = 0.0;
-      if (aa.Lbar) {
-        if (f < n)
-          lb += (DIR == 0) ? aa.Lbar[((size_t)c * g.ny + b) * g.nx + f] : aa.Lbar[((size_t)c * g.ny + f) * g.nx + b];
-        if (f >= 1)
-          lb -= (DIR == 0) ? aa.Lbar[((size_t)c * g.ny + b) * g.nx + f - 1]
-                           : aa.Lbar[((size_t)c * g.ny + f - 1) * g.nx + b];
-      }
-      Fb[c] = lb * fscale;
-    }
-    double sbar = 0.0;
-    if (aa.sbar_out)
-      sbar = ((DIR == 0) ? aa.sbar_out[(size_t)b * (g.nx + 1) + f] : aa.sbar_out[(size_t)f * g.nx + b]) * (1.0 / G);
-    double st[2][G][C];
-    Branch bt[2];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int qa = fa + side;
-      const double* Q = side == 0 ? sQP : sQM;
-      if (DIM == 2) {
-        bt[side] = select_branch<R>(sSt + qa * NST + tb, g.thres);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          double out[G];
-          recon_eval<R, G>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt[side], T, 2, out);
-#pragma unroll
-          for (int q = 0; q < G; ++q) st[side][q][c] = out[q];
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < C; ++c) st[side][0][c] = Q[c * NQ + qa];
-      }
-    }
-    double ca[C], cb[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      ca[c] = sW[(c * NB + tb + KT) * NA + fa + K];
-      cb[c] = sW[(c * NB + tb + KT) * NA + fa + K + 1];
-    }
-    double stb[2][G][C], cab[C], cbb[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      cab[c] = cbb[c] = 0.0;
-#pragma unroll
-      for (int q = 0; q < G; ++q) stb[0][q][c] = stb[1][q][c] = 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < G; ++q) {
-      double F2b[C];
-      const double hw = (DIM == 2) ? T.hgw[q] : 0.5;
-#pragma unroll
-      for (int c = 0; c < C; ++c) F2b[c] = hw * Fb[c];
-      lf_point_vjp<C, NI, TI>(st[0][q], st[1][q], ca, cb, g.gamma, F2b, sbar, stb[0][q], stb[1][q], cab, cbb);
-    }
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int qa = fa + side;
-      const double* Q = side == 0 ? sQP : sQM;
-      double ab[4] = {0.0, 0.0, 0.0, 0.0};
+    if (f <= n && b < mlin) {
+      const size_t face = adj_face<DIR>(f, b, n, mlin);
+      // F_f enters L of cell f with +1/h and L of cell f-1 with -1/h
+      double Fb[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        double vb[NTAP];
-#pragma unroll
-        for (int t = 0; t < NTAP; ++t) vb[t] = 0.0;
-        if (DIM == 2) {
-          double pb[G];
-#pragma unroll
-          for (int q = 0; q < G; ++q) pb[q] = stb[side][q][c];
-          recon_vjp<R, G>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt[side], T, 2, pb, vb + KT, ab);
-        } else {
-          vb[0] = stb[side][0][c];
+        double lb = 0.0;
+        if (aa.Lbar) {
+          if (f < n)
+            lb += (DIR == 0) ? aa.Lbar[((size_t)c * g.ny + b) * g.nx + f] : aa.Lbar[((size_t)c * g.ny + f) * g.nx + b];
+          if (f >= 1)
+            lb -= (DIR == 0) ? aa.Lbar[((size_t)c * g.ny + b) * g.nx + f - 1]
+                             : aa.Lbar[((size_t)c * g.ny + f - 1) * g.nx + b];
         }
-#pragma unroll
-        for (int t = 0; t < NTAP; ++t) aa.Tbar[((size_t)((side * NTAP + t) * C + c)) * nfaces + face] = vb[t];
+        Fb[c] = lb * fscale;
       }
-      if (DIM == 2) {
-        double sb[4];
-        sigma_vjp<R>(bt[side], ab, g.thres, sb);
+      double sbar = 0.0;
+      if (aa.sbar_out)
+        sbar = ((DIR == 0) ? aa.sbar_out[(size_t)b * (g.nx + 1) + f] : aa.sbar_out[(size_t)f * g.nx + b]) * (1.0 / G);
+      // adjoints of the two cell averages (first-order points), accumulated in place
 #pragma unroll
-        for (int q = 0; q < 4; ++q) aa.Stb[(size_t)(side * 4 + q) * nfaces + face] = sb[q];
+      for (int c = 0; c < 2 * C; ++c) aa.Cbar[(size_t)c * nfaces + face] = 0.0;
+#pragma unroll 1
+      for (int q = 0; q < G; ++q) {
+        double st[2][C];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const int qa = fa + side;
+          const double* Q = side == 0 ? sQP : sQM;
+          if (DIM == 2) {
+            const Branch bt = select_branch<R>(sSt + qa * NST + tb, g.thres);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+              double out[1];
+              recon_eval<R, 1>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt, T, 2 + q, out);
+              st[side][c] = out[0];
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) st[side][c] = Q[c * NQ + qa];
+          }
+        }
+        double F2b[C];
+        const double hw = T.hgw[q];
+#pragma unroll
+        for (int c = 0; c < C; ++c) F2b[c] = hw * Fb[c];
+        const LfPrims pr = lf_primitives<C, NI, TI>(st[0], st[1]);
+        double* out0 = sStb + (size_t)(q * C) * NT + it;        // side 0, point q, component 0
+        double* out1 = sStb + (size_t)((G + q) * C) * NT + it;  // side 1
+        double ab[C], bb[C];
+        if (lf_physical(st[0][0], st[1][0], pr)) {
+          lf_point_vjp<C, NI, TI>(st[0], st[1], pr, g.gm1, g.gg1, F2b, sbar, true, ab, bb);
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            out0[c * NT] = ab[c];
+            out1[c * NT] = bb[c];
+          }
+        } else {
+          // the point took the cell averages either side of the face
+          double ca[C], cb[C];
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            ca[c] = sW[(c * NB + tb + KT) * NA + fa + K];
+            cb[c] = sW[(c * NB + tb + KT) * NA + fa + K + 1];
+            out0[c * NT] = out1[c * NT] = 0.0;
+          }
+          lf_point_vjp<C, NI, TI>(ca, cb, lf_primitives<C, NI, TI>(ca, cb), g.gm1, g.gg1, F2b, sbar, false, ab,
+                                  bb);
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            aa.Cbar[(size_t)c * nfaces + face] += ab[c];
+            aa.Cbar[(size_t)(C + c) * nfaces + face] += bb[c];
+          }
+        }
       }
     }
+  }
+  __syncthreads();
+
+  // ---- phase B (per face and side): the tangential reconstruction VJP ----
+  for (int item = tid; item < 2 * NT; item += NT) {
+    const int side = item / NT, it = item - side * NT;  // a warp: consecutive faces of one side
+    int fa, tb;
+    face_of(it, fa, tb);
+    const int f = a0 + fa, b = b0 + tb;
+    if (f > n || b >= mlin) continue;
+    const size_t face = adj_face<DIR>(f, b, n, mlin);
+    const int qa = fa + side;
+    const double* Q = side == 0 ? sQP : sQM;
+    const double* pin = sStb + (size_t)(side * G * C) * NT + it;  // [G][C] at stride NT
+    Branch bt;
+    if (DIM == 2) bt = select_branch<R>(sSt + qa * NST + tb, g.thres);
+    double ab[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      aa.Cbar[(size_t)c * nfaces + face] = cab[c];
-      aa.Cbar[(size_t)(C + c) * nfaces + face] = cbb[c];
+      double vb[NTAP];
+#pragma unroll
+      for (int t = 0; t < NTAP; ++t) vb[t] = 0.0;
+      if (DIM == 2) {
+        double pb[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) pb[q] = pin[(size_t)(q * C + c) * NT];
+        recon_vjp<R, G>(Q + (c * NB + tb + K) * NQ + qa, NQ, bt, T, 2, pb, vb + KT, ab);
+      } else {
+        vb[0] = pin[(size_t)c * NT];
+      }
+#pragma unroll
+      for (int t = 0; t < NTAP; ++t) aa.Tbar[((size_t)((side * NTAP + t) * C + c)) * nfaces + face] = vb[t];
+    }
+    if (DIM == 2) {
+      double sb[4];
+      sigma_vjp<R>(bt, ab, g.thres, sb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) aa.Stb[(size_t)(side * 4 + q) * nfaces + face] = sb[q];
     }
   }
 }
@@ -597,8 +619,9 @@ adj_face_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa, const 
 // ---------------------------------------------------------------------------------
 // K2: normal VJP per reconstructing cell (a in [-1, n], line l in [-KT, m+KT))
 // ---------------------------------------------------------------------------------
+// 128 threads and three CTAs per SM: the WENO branch's VJP needs ~170 registers.
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(256) adj_normal_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa,
+__global__ void __launch_bounds__(128, 3) adj_normal_kernel(const GridInfo g, const SweepArgs args, const AdjArgs aa,
                                                          const __grid_constant__ Tables T) {
   constexpr int K = (R - 1) / 2, C = (DIM == 1) ? 3 : 4, KT = (DIM == 2) ? K : 0;
   constexpr int NTAP = 2 * KT + 1, NS = 2 * K + 1;
@@ -609,41 +632,39 @@ __global__ void __launch_bounds__(256) adj_normal_kernel(const GridInfo g, const
   const size_t nfaces = (size_t)(n + 1) * mlin;
   const int na = n + 2, nl = mlin + 2 * KT;
   const size_t nitems = (size_t)na * nl;
-  for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += (size_t)gridDim.x * blockDim.x) {
-    const int a = (int)(it % na) - 1;
-    const int l = (int)(it / na) - KT;
+  // one thread per (component, reconstructing cell); consecutive threads take consecutive
+  // items of one component (the item index is adj_item<DIR>(a, l))
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < C * nitems;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / nitems);
+    const size_t it = idx - (size_t)c * nitems;
+    const int a = (DIR == 0) ? (int)(it % na) - 1 : (int)(it / nl) - 1;
+    const int l = (DIR == 0) ? (int)(it / na) - KT : (int)(it % nl) - KT;
     // adjoints of the plus (xi = 0) and minus (xi = -1) values of cell (a, l): the
     // plus value is the left state of face a+1, the minus value the right state of face
     // a, each read by the tangential stencils of the face lines b = l - t
-    double QPb[C], QMb[C];
+    double QPb = 0.0, QMb = 0.0;
     bool any = false;
-#pragma unroll
-    for (int c = 0; c < C; ++c) QPb[c] = QMb[c] = 0.0;
 #pragma unroll
     for (int t = -KT; t <= KT; ++t) {
       const int b = l - t;
       if (b < 0 || b >= mlin) continue;
       if (a + 1 <= n) {
-        const size_t face = (size_t)b * (n + 1) + (a + 1);
-#pragma unroll
-        for (int c = 0; c < C; ++c) QPb[c] += aa.Tbar[((size_t)((0 * NTAP + t + KT) * C + c)) * nfaces + face];
+        QPb += aa.Tbar[((size_t)((0 * NTAP + t + KT) * C + c)) * nfaces + adj_face<DIR>(a + 1, b, n, mlin)];
         any = true;
       }
       if (a >= 0) {
-        const size_t face = (size_t)b * (n + 1) + a;
-#pragma unroll
-        for (int c = 0; c < C; ++c) QMb[c] += aa.Tbar[((size_t)((1 * NTAP + t + KT) * C + c)) * nfaces + face];
+        QMb += aa.Tbar[((size_t)((1 * NTAP + t + KT) * C + c)) * nfaces + adj_face<DIR>(a, b, n, mlin)];
         any = true;
       }
     }
-    double* out = aa.Nbar + it;  // [m][c][item]
+    double* out = aa.Nbar + (size_t)c * nitems + it;  // [m][c][item]
+    double* sout = aa.Snb + (size_t)c * nitems + it;  // [q][c][item]: this component's share
     if (!any) {
 #pragma unroll
-      for (int m = 0; m < NS; ++m)
+      for (int m = 0; m < NS; ++m) out[(size_t)m * C * nitems] = 0.0;
 #pragma unroll
-        for (int c = 0; c < C; ++c) out[((size_t)(m * C + c)) * nitems] = 0.0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) aa.Snb[(size_t)q * nitems + it] = 0.0;
+      for (int q = 0; q < 4; ++q) sout[(size_t)q * C * nitems] = 0.0;
       continue;
     }
     // branch of cell (a, l) from the normal faces of its (mapped) line
@@ -656,24 +677,22 @@ __global__ void __launch_bounds__(256) adj_normal_kernel(const GridInfo g, const
     }
     const Branch br = select_branch<R>(s, g.thres);
     double ab[4] = {0.0, 0.0, 0.0, 0.0};
+    double v[NS], vb[NS];
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      double v[NS], vb[NS];
-#pragma unroll
-      for (int m = 0; m < NS; ++m) {
-        const int x = a - K + m;
-        v[m] = (DIR == 0) ? fetch_w(g, args.W, c, x, l, 0.0) : fetch_w(g, args.W, c, l, x, 0.0);
-        vb[m] = 0.0;
-      }
-      const double pb[2] = {QPb[c], QMb[c]};
-      recon_vjp<R, 2>(v + K, 1, br, T, 0, pb, vb + K, ab);
-#pragma unroll
-      for (int m = 0; m < NS; ++m) out[((size_t)(m * C + c)) * nitems] = vb[m];
+    for (int m = 0; m < NS; ++m) {
+      const int x = a - K + m;
+      v[m] = (DIR == 0) ? fetch_w(g, args.W, c, x, l, 0.0) : fetch_w(g, args.W, c, l, x, 0.0);
+      vb[m] = 0.0;
     }
+    const double pb[2] = {QPb, QMb};
+    recon_vjp<R, 2>(v + K, 1, br, T, 0, pb, vb + K, ab);
+#pragma unroll
+    for (int m = 0; m < NS; ++m) out[(size_t)m * C * nitems] = vb[m];
+    // the sigma_in adjoints are linear in ab: each component writes its share, the gather sums
     double sb[4];
     sigma_vjp<R>(br, ab, g.thres, sb);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) aa.Snb[(size_t)q * nitems + it] = sb[q];
+    for (int q = 0; q < 4; ++q) sout[(size_t)q * C * nitems] = sb[q];
   }
 }
 
@@ -689,11 +708,13 @@ __global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, con
   const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
   const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
   const size_t nfaces = (size_t)(n + 1) * mlin;
-  const int na = n + 2;
-  const size_t nitems = (size_t)na * (mlin + 2 * KT);
+  const size_t nitems = (size_t)(n + 2) * (mlin + 2 * KT);
   const size_t ncell = (size_t)g.nx * g.ny;
-  for (size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x; cell < ncell;
-       cell += (size_t)gridDim.x * blockDim.x) {
+  // one thread per (component, cell): consecutive threads take consecutive cells
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < C * ncell;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / ncell);
+    const size_t cell = idx - (size_t)c * ncell;
     const int ci = (int)(cell % g.nx), cj = (int)(cell / g.nx);
     const int i = (DIR == 0) ? ci : cj;  // along the sweep
     const int j = (DIR == 0) ? cj : ci;  // line
@@ -702,9 +723,7 @@ __global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, con
     int nls = 1;
     ls[0] = j;
     if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
-    double acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.0;
+    double acc = 0.0;
     for (int il = 0; il < nls; ++il) {
       const int l = ls[il];
       for (int ix = 0; ix < nxs; ++ix) {
@@ -716,27 +735,16 @@ __global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, con
         for (int m = 0; m < NS; ++m) {
           const int a = x - (m - K);
           if (a < -1 || a > n) continue;
-          const size_t item = (size_t)(l + KT) * na + (a + 1);
-#pragma unroll
-          for (int c = 0; c < C; ++c) acc[c] += aa.Nbar[((size_t)(m * C + c)) * nitems + item];
+          acc += aa.Nbar[((size_t)(m * C + c)) * nitems + adj_item<DIR>(a, l, n, mlin, KT)];
         }
         // first-order states: face x+1 has this cell on its left, face x on its right
         if (l >= 0 && l < mlin) {
-          if (x + 1 >= 0 && x + 1 <= n) {
-            const size_t face = (size_t)l * (n + 1) + (x + 1);
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] += aa.Cbar[(size_t)c * nfaces + face];
-          }
-          if (x >= 0 && x <= n) {
-            const size_t face = (size_t)l * (n + 1) + x;
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] += aa.Cbar[(size_t)(C + c) * nfaces + face];
-          }
+          if (x + 1 >= 0 && x + 1 <= n) acc += aa.Cbar[(size_t)c * nfaces + adj_face<DIR>(x + 1, l, n, mlin)];
+          if (x >= 0 && x <= n) acc += aa.Cbar[(size_t)(C + c) * nfaces + adj_face<DIR>(x, l, n, mlin)];
         }
       }
     }
-#pragma unroll
-    for (int c = 0; c < C; ++c) aa.Wbar[(size_t)c * ncell + cell] += acc[c];
+    aa.Wbar[(size_t)c * ncell + cell] += acc;
   }
 }
 
@@ -746,7 +754,7 @@ __global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, con
 // ---------------------------------------------------------------------------------
 template <int R, int DIM, int DIR>
 __global__ void __launch_bounds__(256) adj_gather_sn_kernel(const GridInfo g, const AdjArgs aa) {
-  constexpr int K = (R - 1) / 2, KT = (DIM == 2) ? K : 0;
+  constexpr int K = (R - 1) / 2, KT = (DIM == 2) ? K : 0, C = (DIM == 1) ? 3 : 4;
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int mlin = (DIR == 0) ? g.ny : g.nx;
   const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
@@ -765,14 +773,17 @@ __global__ void __launch_bounds__(256) adj_gather_sn_kernel(const GridInfo g, co
     ls[0] = j;
     if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
     double acc = 0.0;
+#pragma unroll 1
     for (int il = 0; il < nls; ++il) {
-      const size_t row = (size_t)(ls[il] + KT) * na;
+#pragma unroll 1
       for (int k = 0; k < nfs; ++k) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int a = fs[k] + 1 - q;  // the cell whose stencil face q (face a-1+q) is f
           if (a < -1 || a > n) continue;
-          acc += aa.Snb[(size_t)q * nitems + row + (a + 1)];
+          const size_t item = adj_item<DIR>(a, ls[il], n, mlin, KT);
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc += aa.Snb[(size_t)(q * C + c) * nitems + item];
         }
       }
     }
@@ -809,7 +820,7 @@ __global__ void __launch_bounds__(256) adj_gather_st_kernel(const GridInfo g, co
           for (int q = 0; q < 4; ++q) {
             const int b = tfs[k] + 1 - q;
             if (b < 0 || b >= mlin) continue;
-            acc += aa.Stb[(size_t)(side * 4 + q) * nfaces + (size_t)b * (n + 1) + f];
+            acc += aa.Stb[(size_t)(side * 4 + q) * nfaces + adj_face<DIR>(f, b, n, mlin)];
           }
         }
       }
@@ -818,7 +829,9 @@ __global__ void __launch_bounds__(256) adj_gather_st_kernel(const GridInfo g, co
   }
 }
 
-inline int grid_for(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 16)); }
+inline int grid_for(size_t n, int threads = 256) {
+  return (int)std::max<size_t>(1, std::min<size_t>((n + threads - 1) / threads, 152 * 16));
+}
 
 // Phase 1 (K1, K2) writes only this direction's scratch; phase 2 (K3 - K5) adds into the
 // outputs shared with the other direction.  Phase 1 of the two directions may run
@@ -831,20 +844,20 @@ cudaError_t adj_launch(int phase, const GridInfo& g, const SweepArgs& a, const A
   const int m = (DIR == 0) ? g.ny : g.nx;
   cudaError_t e = cudaSuccess;
   if (phase & 1) {
-    const size_t smem = TL::smem_doubles * sizeof(double);
+    const size_t smem = adj_smem_doubles<R, DIM>() * sizeof(double);
     auto k1 = adj_face_kernel<R, DIM, DIR>;
     static std::atomic<unsigned long long> attr_done{0ull};
     e = ensure_smem_limit(k1, smem, attr_done);
     if (e != cudaSuccess) return e;
     dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
-    k1<<<grid, TL::NT, smem, s>>>(g, a, aa, t);
+    k1<<<grid, AdjShape<R, DIM>::NT, smem, s>>>(g, a, aa, t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t nitems = (size_t)(n + 2) * (m + 2 * TL::KT);
-    adj_normal_kernel<R, DIM, DIR><<<grid_for(nitems), 256, 0, s>>>(g, a, aa, t);
+    adj_normal_kernel<R, DIM, DIR><<<grid_for((size_t)TL::C * nitems, 128), 128, 0, s>>>(g, a, aa, t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (!(phase & 2)) return cudaSuccess;
-  adj_gather_w_kernel<R, DIM, DIR><<<grid_for((size_t)g.nx * g.ny), 256, 0, s>>>(g, aa);
+  adj_gather_w_kernel<R, DIM, DIR><<<grid_for((size_t)TL::C * g.nx * g.ny), 256, 0, s>>>(g, aa);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (aa.sbar_norm) {
     adj_gather_sn_kernel<R, DIM, DIR><<<grid_for((size_t)(n + 1) * m), 256, 0, s>>>(g, aa);

@@ -19,7 +19,7 @@ struct AdjArgs {
   double* Cbar;            // [2][C][(n+1) m]: adjoint of the two cell averages of a first-order face
   double* Stb;             // [2][4][(n+1) m]: sigma_in adjoints of the tangential branches (2D)
   double* Nbar;            // [2K+1][C][(n+2)(m+2KT)]: adjoint of each stencil cell of a normal reconstruction
-  double* Snb;             // [4][(n+2)(m+2KT)]: sigma_in adjoints of the normal branches
+  double* Snb;             // [4][C][(n+2)(m+2KT)]: sigma_in adjoints of the normal branches, per component
   // outputs (accumulated)
   double* Wbar;            // += [C][ny][nx]
   double* sbar_norm;       // += sigma_in adjoint of the faces normal to the sweep (NULL: not wanted)
@@ -32,7 +32,7 @@ struct AdjArgs {
 inline size_t adj_scratch_doubles(int dim, int order, long long n, long long m) {
   const long long K = (order - 1) / 2, KT = (dim == 2) ? K : 0, C = (dim == 1) ? 3 : 4;
   const long long nf = (n + 1) * m, ni = (n + 2) * (m + 2 * KT);
-  return (size_t)(2 * (2 * KT + 1) * C * nf + 2 * C * nf + (dim == 2 ? 8 * nf : 0) + (2 * K + 1) * C * ni + 4 * ni);
+  return (size_t)(2 * (2 * KT + 1) * C * nf + 2 * C * nf + (dim == 2 ? 8 * nf : 0) + (2 * K + 1) * C * ni + 4 * C * ni);
 }
 
 // phase: 1 = the face and normal kernels (this direction's scratch only), 2 = the gathers

@@ -95,22 +95,28 @@ batch_sweep_kernel(const BatchProblem* __restrict__ probs, const int4* __restric
                    DevState* states) {
   extern __shared__ double smem[];
   __shared__ Tables sT;
-  __shared__ int s_item;
+  __shared__ int s_item[2];  // the current work item and the next one (fetched during the tile)
   __shared__ int s_variant;
-  if (threadIdx.x == 0) s_variant = -1;
+  if (threadIdx.x == 0) {
+    s_variant = -1;
+    s_item[0] = (int)atomicAdd(counter, 1u);
+  }
+  int k = 0;
   while (true) {
-    __syncthreads();  // the previous tile is done with smem and s_item
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    // the previous tile is done with smem, and s_item[k] holds this tile's item (written by
+    // thread 0 before this barrier, after every thread had read the slot's previous value)
     __syncthreads();
-    const int it = s_item;
+    const int it = s_item[k];
     if (it >= nitems) break;
+    if (threadIdx.x == 0) s_item[k ^ 1] = (int)atomicAdd(counter, 1u);  // read after the next barrier
+    k ^= 1;
     const int4 w = items[it];  // problem, a0, b0, lines of a 2D tile
     const BatchProblem& pb = probs[w.x];
     const int variant = pb.variant;
     if (variant != s_variant) {  // stage this order's tables in shared memory
       const double* src = reinterpret_cast<const double*>(tabs + variant);
       double* dst = reinterpret_cast<double*>(&sT);
-      for (int k = threadIdx.x; k < (int)(sizeof(Tables) / sizeof(double)); k += kNT) dst[k] = src[k];
+      for (int e = threadIdx.x; e < (int)(sizeof(Tables) / sizeof(double)); e += kNT) dst[e] = src[e];
       __syncthreads();
       if (threadIdx.x == 0) s_variant = variant;
       __syncthreads();

@@ -204,8 +204,9 @@ __device__ __forceinline__ void tang_eval(const double* v, int vs, const Branch&
 
 // Tile of the face kernels: TN faces along the sweep on TT lines.  The Lax-Friedrichs sweep
 // uses 8 x 64 in 2D (measured on GB300 against 16 x 32, 16 x 16, 32 x 16 and 8 x 32: 1.4 %
-// faster than 16 x 32 at order 9, from the smaller share of halo lines); 256 faces in 1D.
-template <int R, int DIM, int TT_ = (DIM == 2) ? 64 : 1, int TN_ = (DIM == 2) ? 8 : 256>
+// faster than 16 x 32 at order 9, from the smaller share of halo lines); 255 faces in 1D (256
+// reconstructing cells: phase 1 gives every one of the 256 threads one cell).
+template <int R, int DIM, int TT_ = (DIM == 2) ? 64 : 1, int TN_ = (DIM == 2) ? 8 : 255>
 struct Tile {
   static constexpr int K = (R - 1) / 2;
   static constexpr int C = (DIM == 1) ? 3 : 4;
