@@ -709,21 +709,18 @@ def _cores():
         return os.cpu_count() or 1
 
 
-def _oracle_rows_parallel(O, pb, W, sx, sy, threads):
-    """One residual evaluation by the oracle with the rows split over `threads` host
-    threads (each runs the serial code on its rows; the C calls release the GIL)."""
-    from concurrent.futures import ThreadPoolExecutor
-
-    blocks = [b for b in np.array_split(np.arange(pb.nyc), threads) if len(b)]
-    with ThreadPoolExecutor(len(blocks)) as ex:
-        list(ex.map(lambda b: O.residual_rows(pb, W, sx, sy, int(b[0]), int(b[-1])), blocks))
+def _oracle_all_cores(O, pb, W, sx, sy, threads):
+    """One residual evaluation by the oracle with its face loops on `threads` host threads
+    (oracle.threads: the serial results bit for bit)."""
+    with O.threads(threads):
+        O.residual(pb, W, sx, sy)
 
 
 def _cpu_rates(O, pb, W, sx, sy, cores):
     t0 = time.perf_counter()
     O.residual(pb, W, sx, sy)
     t1 = time.perf_counter()
-    _oracle_rows_parallel(O, pb, W, sx, sy, cores)
+    _oracle_all_cores(O, pb, W, sx, sy, cores)
     t2 = time.perf_counter()
     return ({"value": round(pb.ncells / (t1 - t0) / 1e6, 4), "cores": 1},
             {"value": round(pb.ncells / (t2 - t1) / 1e6, 4), "cores": cores})
@@ -799,7 +796,7 @@ def suite_bench(args):
     O.residual_rows(pb, W0, sx, sy, lo, hi)
     band = time.perf_counter() - t0
     t0 = time.perf_counter()
-    _oracle_rows_parallel(O, pb, W0, sx, sy, cores)
+    _oracle_all_cores(O, pb, W0, sx, sy, cores)
     full = time.perf_counter() - t0
     rows.append({"config": "jet 2D 1600x800, r=9, %d CFL steps after %d warm-up steps from t=0" % (args.steps, args.warmup),
                  "gpu": {"value": round(value, 3), "ms_per_step": round(ms / args.steps, 4), "flags": flags},
