@@ -393,7 +393,9 @@ __device__ __forceinline__ int face_preimages(int e, int n, int bl, int bh, int 
 // ---------------------------------------------------------------------------------
 // K1: face kernel
 // ---------------------------------------------------------------------------------
-// 2D: 8 faces x 16 lines per CTA of 128 threads, one face per thread, three CTAs per SM;
+// 2D: 8 faces x 16 lines per CTA of 128 threads, one face per thread; four CTAs per SM up to
+// order 7 (128 registers, a few hundred bytes of spills: measured 9 % faster than three CTAs
+// at 168 registers), three at order 9 (its 64 KB of shared memory per CTA allows no more);
 // 1D: 256 faces per CTA of 256 threads.  Phase A (per face) recomputes the two states at
 // each Gauss point and writes their adjoints to shared memory; phase B (per face and side)
 // takes them back through the tangential reconstruction.
@@ -402,7 +404,7 @@ struct AdjShape {
   static constexpr int TN = (DIM == 2) ? 8 : 256;
   static constexpr int TT = (DIM == 2) ? 16 : 1;
   static constexpr int NT = TN * TT;
-  static constexpr int MINB = (DIM == 2) ? 3 : 1;
+  static constexpr int MINB = (DIM == 2) ? (R <= 7 ? 4 : 3) : 1;
 };
 
 template <int R, int DIM>
