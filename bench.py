@@ -109,6 +109,52 @@ def algorithmic_flops_per_face(ndim: int, r: int) -> float:
     return normal + tang + G * (phi + 2 * C + 1) + 1
 
 
+# The gas-kinetic Gauss point (Sec. 2.2, Appendix A): FP64 operations of one closed-form
+# evaluation of F and F_t (three Maxwellians and their moments, half-line moments of two,
+# seven slope solves, the compatibility condition, the time integrals), exp and erfc counted
+# as one operation each; and sigma of one Gauss point (Sec. 3.1).  tests/test_flop_model.py
+# counts both from an evaluation that reproduces the oracle's values.
+GKS_POINT_FLOPS = {2: 1365, 1: 598}
+SIGMA_POINT_FLOPS = {2: 43, 1: 32}
+
+
+def gks_flops_per_face(ndim: int, r: int) -> float:
+    """FP64 operations of one face of one gas-kinetic sweep on the all-smooth branch: the
+    normal reconstruction of the face's cell, value and derivative at both of its faces
+    (4 C (2r-1), + 2 C to scale the derivatives by 1/h); in 2D per side, component and Gauss
+    point the tangential value, tangential derivative and the tangential reconstruction of
+    the normal derivative (3 (2r-1), + 1 to scale the tangential derivative); per Gauss point
+    the gas-kinetic flux, sigma and the Gauss sums of F, F_t and sigma (4 C + 1); + 1 for the
+    face sigma."""
+    C = 4 if ndim == 2 else 3
+    G = ((r - 1) // 2 if r > 3 else 1) if ndim == 2 else 1
+    normal = 4 * C * (2 * r - 1) + 2 * C
+    tang = 2 * C * G * (3 * (2 * r - 1) + 1) if ndim == 2 else 0
+    return normal + tang + G * (GKS_POINT_FLOPS[ndim] + SIGMA_POINT_FLOPS[ndim] + 4 * C + 1) + 1
+
+
+def gks_sweep_roofline(A, torch, s, pb, steps: int, peak_tflops: float, clk_mhz: float) -> dict:
+    """Roofline of the gas-kinetic face sweep from its launch times: `steps` more S2O4 steps
+    of solver s with a CUDA event pair around every launch (x and y sweeps in series)."""
+    A.ase_df_profile_enable(s.ctx, True)
+    for _ in range(steps):
+        s.gks_step()
+    torch.cuda.synchronize()
+    ms, n = A.ase_df_profile_read(s.ctx)
+    A.ase_df_profile_enable(s.ctx, False)
+    sweep_ms, sweep_n = ms[0] + ms[1], n[0] + n[1]
+    faces = 0.5 * ((pb.nx + 1) * pb.ny + (pb.ny + 1) * pb.nx) if pb.ndim == 2 else pb.nx + 1
+    flops = gks_flops_per_face(pb.ndim, pb.order) * faces
+    achieved = flops / (sweep_ms / sweep_n * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "gks_sweep_kernel<%d>, x and y launches" % pb.order,
+            "achieved": round(achieved, 4), "peak": round(peak_tflops, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tflops, 4), "flops_per_launch": flops,
+            "flops_per_face": gks_flops_per_face(pb.ndim, pb.order),
+            "launch_ms": round(sweep_ms / sweep_n, 4),
+            "launch_ms_source": "CUDA event pair around every launch, %d further steps" % steps,
+            "peak_source": "2 FP64 FMA/cycle/SM x SMs x %.0f MHz x 2 flops" % clk_mhz}
+
+
 # Edges per operation of the oracle's reverse-mode graph of one 2D residual (smooth data,
 # 32^2 periodic; tests/test_flop_model.py): the reverse sweep does one multiply-add per edge
 # (the cost model of reverse mode), so the residual adjoint's algorithmic flops are taken as
@@ -865,8 +911,9 @@ def suite_bench(args):
             e1.synchronize()
             gms = e0.elapsed_time(e1)
             flags = s.status()[0]
+            roof = gks_sweep_roofline(A, torch, s, pb, 20, fp64_peak_tflops(torch), 2070.0)
             s.close()
-            per_n.append({"n": nn, "ms_20_steps": round(gms, 3),
+            per_n.append({"n": nn, "ms_20_steps": round(gms, 3), "sweep_frac": roof["frac"],
                           "value": round(pb.ncells * 2 * 20 / (gms * 1e-3) / 1e6, 3), "flags": flags,
                           "paper_cpu_s_20_steps": table4[r][k],
                           "paper_cpu_over_gpu": round(table4[r][k] / (gms * 1e-3), 1)})
@@ -930,19 +977,25 @@ def gks_bench(args):
         s.gks_step()
     s.set_state(W0)
     torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         s.gks_step()
     e1.record()
     e1.synchronize()
+    clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     flags = s.status()[0]
+    clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    roof = gks_sweep_roofline(A, torch, s, pb, args.steps, fp64_peak_tflops(torch, clk), clk)
     s.close()
     print(json.dumps({"workload": "GKS + S2O4, Configuration 3, %d^2, order %d" % (args.n, args.order),
                       "steps": args.steps, "ms_per_step": round(ms / args.steps, 4),
                       "value": round(pb.ncells * 2 * args.steps / (ms * 1e-3) / 1e6, 3),
-                      "unit": "Mcell-updates/s per stage", "flags": flags}), flush=True)
+                      "unit": "Mcell-updates/s per stage", "flags": flags, "roofline": roof,
+                      "clocks": clocks}), flush=True)
 
 
 def main():

@@ -701,8 +701,10 @@ __global__ void __launch_bounds__(128, 3) adj_normal_kernel(const GridInfo g, co
 // ---------------------------------------------------------------------------------
 // K3: gather into Wbar (per interior cell)
 // ---------------------------------------------------------------------------------
+// This direction's adjoint of W component c of one interior cell: the Nbar and Cbar
+// entries of every stencil position that the boundary maps onto it (a fixed order).
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, const AdjArgs aa) {
+__device__ __forceinline__ double gather_w_sum(const GridInfo& g, const AdjArgs& aa, int c, size_t cell) {
   constexpr int K = (R - 1) / 2, C = (DIM == 1) ? 3 : 4, KT = (DIM == 2) ? K : 0;
   constexpr int NS = 2 * K + 1;
   const int n = (DIR == 0) ? g.nx : g.ny;
@@ -711,42 +713,47 @@ __global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, con
   const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
   const size_t nfaces = (size_t)(n + 1) * mlin;
   const size_t nitems = (size_t)(n + 2) * (mlin + 2 * KT);
+  const int ci = (int)(cell % g.nx), cj = (int)(cell / g.nx);
+  const int i = (DIR == 0) ? ci : cj;  // along the sweep
+  const int j = (DIR == 0) ? cj : ci;  // line
+  int xs[16], ls[16];
+  const int nxs = cell_preimages(i, n, bcn_lo, bcn_hi, -K - 1, n + K, xs);
+  int nls = 1;
+  ls[0] = j;
+  if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
+  double acc = 0.0;
+  for (int il = 0; il < nls; ++il) {
+    const int l = ls[il];
+    for (int ix = 0; ix < nxs; ++ix) {
+      const int x = xs[ix];
+      // inflow ghost cells hold the constant inflow state
+      const int gi = (DIR == 0) ? x : l, gj = (DIR == 0) ? l : x;
+      if (gi < 0 && g.bc[0] == BC_INFLOW_BAND && gj >= g.band_j0 && gj <= g.band_j1) continue;
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        const int a = x - (m - K);
+        if (a < -1 || a > n) continue;
+        acc += aa.Nbar[((size_t)(m * C + c)) * nitems + adj_item<DIR>(a, l, n, mlin, KT)];
+      }
+      // first-order states: face x+1 has this cell on its left, face x on its right
+      if (l >= 0 && l < mlin) {
+        if (x + 1 >= 0 && x + 1 <= n) acc += aa.Cbar[(size_t)c * nfaces + adj_face<DIR>(x + 1, l, n, mlin)];
+        if (x >= 0 && x <= n) acc += aa.Cbar[(size_t)(C + c) * nfaces + adj_face<DIR>(x, l, n, mlin)];
+      }
+    }
+  }
+  return acc;
+}
+
+template <int R, int DIM, int DIR>
+__global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, const AdjArgs aa) {
+  constexpr int C = (DIM == 1) ? 3 : 4;
   const size_t ncell = (size_t)g.nx * g.ny;
   // one thread per (component, cell): consecutive threads take consecutive cells
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < C * ncell;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(idx / ncell);
-    const size_t cell = idx - (size_t)c * ncell;
-    const int ci = (int)(cell % g.nx), cj = (int)(cell / g.nx);
-    const int i = (DIR == 0) ? ci : cj;  // along the sweep
-    const int j = (DIR == 0) ? cj : ci;  // line
-    int xs[16], ls[16];
-    const int nxs = cell_preimages(i, n, bcn_lo, bcn_hi, -K - 1, n + K, xs);
-    int nls = 1;
-    ls[0] = j;
-    if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
-    double acc = 0.0;
-    for (int il = 0; il < nls; ++il) {
-      const int l = ls[il];
-      for (int ix = 0; ix < nxs; ++ix) {
-        const int x = xs[ix];
-        // inflow ghost cells hold the constant inflow state
-        const int gi = (DIR == 0) ? x : l, gj = (DIR == 0) ? l : x;
-        if (gi < 0 && g.bc[0] == BC_INFLOW_BAND && gj >= g.band_j0 && gj <= g.band_j1) continue;
-#pragma unroll
-        for (int m = 0; m < NS; ++m) {
-          const int a = x - (m - K);
-          if (a < -1 || a > n) continue;
-          acc += aa.Nbar[((size_t)(m * C + c)) * nitems + adj_item<DIR>(a, l, n, mlin, KT)];
-        }
-        // first-order states: face x+1 has this cell on its left, face x on its right
-        if (l >= 0 && l < mlin) {
-          if (x + 1 >= 0 && x + 1 <= n) acc += aa.Cbar[(size_t)c * nfaces + adj_face<DIR>(x + 1, l, n, mlin)];
-          if (x >= 0 && x <= n) acc += aa.Cbar[(size_t)(C + c) * nfaces + adj_face<DIR>(x, l, n, mlin)];
-        }
-      }
-    }
-    aa.Wbar[(size_t)c * ncell + cell] += acc;
+    aa.Wbar[idx] += gather_w_sum<R, DIM, DIR>(g, aa, c, idx - (size_t)c * ncell);
   }
 }
 
@@ -754,80 +761,132 @@ __global__ void __launch_bounds__(256) adj_gather_w_kernel(const GridInfo g, con
 // K4: gather of the normal-face sigma_in adjoints (per entry of this direction's
 // normal sigma array)
 // ---------------------------------------------------------------------------------
+// Entry idx of the normal sigma array: sx[j][e] (x-sweep) or sy[e][j] (y-sweep), row-major.
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(256) adj_gather_sn_kernel(const GridInfo g, const AdjArgs aa) {
+__device__ __forceinline__ double gather_sn_sum(const GridInfo& g, const AdjArgs& aa, size_t idx) {
   constexpr int K = (R - 1) / 2, KT = (DIM == 2) ? K : 0, C = (DIM == 1) ? 3 : 4;
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int mlin = (DIR == 0) ? g.ny : g.nx;
   const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
   const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
-  const int na = n + 2;
-  const size_t nitems = (size_t)na * (mlin + 2 * KT);
-  const size_t nent = (size_t)(n + 1) * mlin;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nent;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    int e, j;
-    if (DIR == 0) { e = (int)(idx % (g.nx + 1)); j = (int)(idx / (g.nx + 1)); }  // sx[j][e]
-    else { j = (int)(idx % g.nx); e = (int)(idx / g.nx); }                       // sy[e][j]
-    int fs[16], ls[16];
-    const int nfs = face_preimages(e, n, bcn_lo, bcn_hi, -2, n + 2, fs);
-    int nls = 1;
-    ls[0] = j;
-    if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
-    double acc = 0.0;
+  const size_t nitems = (size_t)(n + 2) * (mlin + 2 * KT);
+  int e, j;
+  if (DIR == 0) { e = (int)(idx % (g.nx + 1)); j = (int)(idx / (g.nx + 1)); }  // sx[j][e]
+  else { j = (int)(idx % g.nx); e = (int)(idx / g.nx); }                       // sy[e][j]
+  int fs[16], ls[16];
+  const int nfs = face_preimages(e, n, bcn_lo, bcn_hi, -2, n + 2, fs);
+  int nls = 1;
+  ls[0] = j;
+  if (DIM == 2) nls = cell_preimages(j, mlin, bct_lo, bct_hi, -KT, mlin + KT - 1, ls);
+  double acc = 0.0;
 #pragma unroll 1
-    for (int il = 0; il < nls; ++il) {
+  for (int il = 0; il < nls; ++il) {
 #pragma unroll 1
-      for (int k = 0; k < nfs; ++k) {
+    for (int k = 0; k < nfs; ++k) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int a = fs[k] + 1 - q;  // the cell whose stencil face q (face a-1+q) is f
-          if (a < -1 || a > n) continue;
-          const size_t item = adj_item<DIR>(a, ls[il], n, mlin, KT);
+      for (int q = 0; q < 4; ++q) {
+        const int a = fs[k] + 1 - q;  // the cell whose stencil face q (face a-1+q) is f
+        if (a < -1 || a > n) continue;
+        const size_t item = adj_item<DIR>(a, ls[il], n, mlin, KT);
 #pragma unroll
-          for (int c = 0; c < C; ++c) acc += aa.Snb[(size_t)(q * C + c) * nitems + item];
-        }
+        for (int c = 0; c < C; ++c) acc += aa.Snb[(size_t)(q * C + c) * nitems + item];
       }
     }
-    aa.sbar_norm[idx] += acc;
   }
+  return acc;
+}
+
+template <int R, int DIM, int DIR>
+__global__ void __launch_bounds__(256) adj_gather_sn_kernel(const GridInfo g, const AdjArgs aa) {
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const size_t nent = (size_t)(n + 1) * mlin;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nent;
+       idx += (size_t)gridDim.x * blockDim.x)
+    aa.sbar_norm[idx] += gather_sn_sum<R, DIM, DIR>(g, aa, idx);
 }
 
 // ---------------------------------------------------------------------------------
 // K5: gather of the tangential-face sigma_in adjoints (2D)
 // ---------------------------------------------------------------------------------
+// Entry idx of the tangential sigma array: sy[te][i] (x-sweep) or sx[i][te] (y-sweep).
 template <int R, int DIR>
-__global__ void __launch_bounds__(256) adj_gather_st_kernel(const GridInfo g, const AdjArgs aa) {
+__device__ __forceinline__ double gather_st_sum(const GridInfo& g, const AdjArgs& aa, size_t idx) {
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int mlin = (DIR == 0) ? g.ny : g.nx;
   const int bcn_lo = (DIR == 0) ? g.bc[0] : g.bc[2], bcn_hi = (DIR == 0) ? g.bc[1] : g.bc[3];
   const int bct_lo = (DIR == 0) ? g.bc[2] : g.bc[0], bct_hi = (DIR == 0) ? g.bc[3] : g.bc[1];
   const size_t nfaces = (size_t)(n + 1) * mlin;
-  const size_t nent = (size_t)(mlin + 1) * n;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nent;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    int te, i;
-    if (DIR == 0) { i = (int)(idx % g.nx); te = (int)(idx / g.nx); }            // sy[te][i]
-    else { te = (int)(idx % (g.nx + 1)); i = (int)(idx / (g.nx + 1)); }         // sx[i][te]
-    int xs[16], tfs[16];
-    const int nxs = cell_preimages(i, n, bcn_lo, bcn_hi, -1, n, xs);
-    const int ntf = face_preimages(te, mlin, bct_lo, bct_hi, -1, mlin + 1, tfs);
-    double acc = 0.0;
-    for (int side = 0; side < 2; ++side) {
-      for (int ix = 0; ix < nxs; ++ix) {
-        const int f = xs[ix] + 1 - side;  // the face whose side-`side` column is x
-        if (f < 0 || f > n) continue;
-        for (int k = 0; k < ntf; ++k) {
+  int te, i;
+  if (DIR == 0) { i = (int)(idx % g.nx); te = (int)(idx / g.nx); }            // sy[te][i]
+  else { te = (int)(idx % (g.nx + 1)); i = (int)(idx / (g.nx + 1)); }         // sx[i][te]
+  int xs[16], tfs[16];
+  const int nxs = cell_preimages(i, n, bcn_lo, bcn_hi, -1, n, xs);
+  const int ntf = face_preimages(te, mlin, bct_lo, bct_hi, -1, mlin + 1, tfs);
+  double acc = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    for (int ix = 0; ix < nxs; ++ix) {
+      const int f = xs[ix] + 1 - side;  // the face whose side-`side` column is x
+      if (f < 0 || f > n) continue;
+      for (int k = 0; k < ntf; ++k) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int b = tfs[k] + 1 - q;
-            if (b < 0 || b >= mlin) continue;
-            acc += aa.Stb[(size_t)(side * 4 + q) * nfaces + adj_face<DIR>(f, b, n, mlin)];
-          }
+        for (int q = 0; q < 4; ++q) {
+          const int b = tfs[k] + 1 - q;
+          if (b < 0 || b >= mlin) continue;
+          acc += aa.Stb[(size_t)(side * 4 + q) * nfaces + adj_face<DIR>(f, b, n, mlin)];
         }
       }
     }
-    aa.sbar_tan[idx] += acc;
+  }
+  return acc;
+}
+
+template <int R, int DIR>
+__global__ void __launch_bounds__(256) adj_gather_st_kernel(const GridInfo g, const AdjArgs aa) {
+  const int n = (DIR == 0) ? g.nx : g.ny;
+  const int mlin = (DIR == 0) ? g.ny : g.nx;
+  const size_t nent = (size_t)(mlin + 1) * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nent;
+       idx += (size_t)gridDim.x * blockDim.x)
+    aa.sbar_tan[idx] += gather_st_sum<R, DIR>(g, aa, idx);
+}
+
+// ---------------------------------------------------------------------------------
+// K3-K5 of both directions in one launch (2D)
+// ---------------------------------------------------------------------------------
+// The three outputs are disjoint: Wbar, sigma_x's adjoint (the x-direction's normal faces and
+// the y-direction's tangential ones) and sigma_y's.  Each element is one thread's, and it adds
+// the x-direction's sum before the y-direction's, the order of the per-direction launches,
+// so the results are theirs bit for bit.
+template <int R>
+__global__ void __launch_bounds__(256) adj_gather_both_kernel(const GridInfo g, const AdjArgs ax, const AdjArgs ay) {
+  constexpr int C = 4;
+  const size_t ncell = (size_t)g.nx * g.ny;
+  const size_t nw = C * ncell;
+  const size_t nsx = ax.sbar_norm ? (size_t)(g.nx + 1) * g.ny : 0;
+  const size_t nsy = ay.sbar_norm ? (size_t)(g.ny + 1) * g.nx : 0;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nw + nsx + nsy;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    if (idx < nw) {
+      const int c = (int)(idx / ncell);
+      const size_t cell = idx - (size_t)c * ncell;
+      double w = ax.Wbar[idx];
+      w += gather_w_sum<R, 2, 0>(g, ax, c, cell);
+      w += gather_w_sum<R, 2, 1>(g, ay, c, cell);
+      ax.Wbar[idx] = w;
+    } else if (idx < nw + nsx) {
+      const size_t k = idx - nw;
+      double s = ax.sbar_norm[k];
+      s += gather_sn_sum<R, 2, 0>(g, ax, k);
+      s += gather_st_sum<R, 1>(g, ay, k);
+      ax.sbar_norm[k] = s;
+    } else {
+      const size_t k = idx - nw - nsx;
+      double s = ay.sbar_norm[k];
+      s += gather_st_sum<R, 0>(g, ax, k);
+      s += gather_sn_sum<R, 2, 1>(g, ay, k);
+      ay.sbar_norm[k] = s;
+    }
   }
 }
 
@@ -872,6 +931,14 @@ cudaError_t adj_launch(int phase, const GridInfo& g, const SweepArgs& a, const A
   return cudaSuccess;
 }
 
+template <int R>
+cudaError_t adj_gather_both_launch(const GridInfo& g, const AdjArgs& ax, const AdjArgs& ay, cudaStream_t s) {
+  const size_t n = (size_t)4 * g.nx * g.ny + (ax.sbar_norm ? (size_t)(g.nx + 1) * g.ny : 0) +
+                   (ay.sbar_norm ? (size_t)(g.ny + 1) * g.nx : 0);
+  adj_gather_both_kernel<R><<<grid_for(n), 256, 0, s>>>(g, ax, ay);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 #define ASE_DF_CAT2(a, b) a##b
@@ -884,6 +951,11 @@ cudaError_t ASE_DF_CAT(launch_adjoint_r, ASE_DF_ORDER)(int dim, int dir, int pha
   if (dim == 1) return adj_launch<R, 1, 0>(phase, g, a, aa, t, s);
   if (dir == 0) return adj_launch<R, 2, 0>(phase, g, a, aa, t, s);
   return adj_launch<R, 2, 1>(phase, g, a, aa, t, s);
+}
+
+cudaError_t ASE_DF_CAT(launch_adjoint_gathers_2d_r, ASE_DF_ORDER)(const GridInfo& g, const AdjArgs& ax,
+                                                                   const AdjArgs& ay, cudaStream_t s) {
+  return adj_gather_both_launch<ASE_DF_ORDER>(g, ax, ay, s);
 }
 
 }  // namespace asedf

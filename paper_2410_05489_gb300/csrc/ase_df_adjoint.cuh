@@ -46,6 +46,14 @@ cudaError_t launch_adjoint_r7(int dim, int dir, int phase, const GridInfo& g, co
 cudaError_t launch_adjoint_r9(int dim, int dir, int phase, const GridInfo& g, const SweepArgs& a,
                               const AdjArgs& aa, const Tables& t, cudaStream_t s);
 
+// 2D: the gathers (phase 2) of both directions in one launch, ax / ay the x- and
+// y-direction's arguments (the same outputs; ax.sbar_norm == ay.sbar_tan and
+// ay.sbar_norm == ax.sbar_tan).  The results equal phase 2 of x, then of y, bit for bit.
+cudaError_t launch_adjoint_gathers_2d_r3(const GridInfo& g, const AdjArgs& ax, const AdjArgs& ay, cudaStream_t s);
+cudaError_t launch_adjoint_gathers_2d_r5(const GridInfo& g, const AdjArgs& ax, const AdjArgs& ay, cudaStream_t s);
+cudaError_t launch_adjoint_gathers_2d_r7(const GridInfo& g, const AdjArgs& ax, const AdjArgs& ay, cudaStream_t s);
+cudaError_t launch_adjoint_gathers_2d_r9(const GridInfo& g, const AdjArgs& ax, const AdjArgs& ay, cudaStream_t s);
+
 // out = a x + b y (y may be NULL, then out = a x); out may alias x or y.
 cudaError_t launch_axpby(double* out, double a, const double* x, double b, const double* y, size_t n,
                          cudaStream_t s);

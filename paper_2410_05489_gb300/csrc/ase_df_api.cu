@@ -617,9 +617,9 @@ static ase_df_status ensure_adjoint(ase_df_ctx* c) {
 
 // Wbar += J_W^T (lscale Lbar) + ..., sbi += J_sigma^T ... for both directions.  In 2D the
 // face and normal kernels of the y-direction run on the side stream beside those of the
-// x-direction (each direction has its own scratch); the gathers into the shared outputs
-// then run on s, x-direction first, as in the serial order (with kernel timing on,
-// everything is serial on s).
+// x-direction (each direction has its own scratch); the gathers of both directions into
+// the shared outputs then run as one launch on s, which adds the x-direction's sums first,
+// as the serial order does (with kernel timing on, everything is serial on s).
 static cudaError_t residual_adjoint(ase_df_ctx* c, const double* W, const double* sx, const double* sy,
                                     const double* Lbar, double lscale, const double* sbo_x, const double* sbo_y,
                                     double* Wbar, double* sbi_x, double* sbi_y, cudaStream_t s) {
@@ -679,8 +679,12 @@ static cudaError_t residual_adjoint(ase_df_ctx* c, const double* W, const double
   if (ex != cudaSuccess) return ex;
   if (ey != cudaSuccess) return ey;
   if (e != cudaSuccess) return e;
-  if ((e = launch(0, 2, s)) != cudaSuccess) return e;
-  return launch(1, 2, s);
+  switch (c->p.order) {
+    case 3: return launch_adjoint_gathers_2d_r3(g, aa[0], aa[1], s);
+    case 5: return launch_adjoint_gathers_2d_r5(g, aa[0], aa[1], s);
+    case 7: return launch_adjoint_gathers_2d_r7(g, aa[0], aa[1], s);
+    default: return launch_adjoint_gathers_2d_r9(g, aa[0], aa[1], s);
+  }
 }
 
 extern "C" {

@@ -389,15 +389,18 @@ __device__ __forceinline__ bool gks_physical(const double* q, double gamma) {
 // ---------------------------------------------------------------------------------
 // the face kernel
 // ---------------------------------------------------------------------------------
-// One (face, Gauss point) per thread: the gas-kinetic flux needs ~220 registers, so one
-// 256-thread CTA runs per SM, and a tile of TN x TT faces with TN TT G ~ 256 keeps the CTAs
-// small enough that the last wave of a grid is a small part of it (400^2 at order 9: 2525
-// tiles of 4 x 16 faces, 16.6 waves, instead of 650 tiles of 16 x 16 faces, 4.3 waves).
+// One (face, Gauss point) per thread.  The gas-kinetic flux needs ~200 registers, so in 2D
+// a CTA of 128 threads with a tile of TN x TT faces, TN TT G ~ 128, runs two to an SM: while
+// one CTA waits at a barrier or reconstructs its band, the other keeps the FP64 pipe busy,
+// and the tiles are small enough that the last wave of a 100^2 grid is a small part of it.
+// 1D: 256 faces per CTA of 256 threads.
 template <int R, int DIM>
 struct GksShape {
   static constexpr int G = (DIM == 2) ? (R == 3 ? 1 : (R - 1) / 2) : 1;
+  static constexpr int NT = (DIM == 2) ? 128 : 256;
+  static constexpr int MINB = (DIM == 2) ? 2 : 1;
   static constexpr int TN = (DIM == 2) ? (G == 1 ? 8 : 4) : 256;
-  static constexpr int TT = (DIM == 2) ? 256 / (TN * G) : 1;  // r9: 16, r7: 21, r5: 32, r3: 32
+  static constexpr int TT = (DIM == 2) ? NT / (TN * G) : 1;  // r9: 8, r7: 10, r5: 16, r3: 16
 };
 
 template <int R, int DIM>
@@ -412,12 +415,12 @@ struct GksTile {
 };
 
 template <int R, int DIM, int DIR>
-__global__ void __launch_bounds__(GksTileShape<R, DIM>::NT, 1)
+__global__ void __launch_bounds__(GksShape<R, DIM>::NT, GksShape<R, DIM>::MINB)
 gks_sweep_kernel(const GridInfo g, const GksSweepArgs args, const __grid_constant__ Tables T,
                  const __grid_constant__ DTables D) {
   using TL = GksTileShape<R, DIM>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
-  constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
+  constexpr int TN = TL::TN, TT = TL::TT, NT = GksShape<R, DIM>::NT;
   constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
   constexpr int NI = (DIR == 0) ? 1 : 2;
   constexpr int TI = (DIR == 0) ? 2 : 1;
@@ -603,7 +606,7 @@ cudaError_t gks_launch(const GridInfo& g, const GksSweepArgs& a, const Tables& t
   const int n = (DIR == 0) ? g.nx : g.ny;
   const int m = (DIR == 0) ? g.ny : g.nx;
   dim3 grid((n + 1 + TL::TN - 1) / TL::TN, (m + TL::TT - 1) / TL::TT);
-  k<<<grid, TL::NT, smem, s>>>(g, a, t, d);
+  k<<<grid, GksShape<R, DIM>::NT, smem, s>>>(g, a, t, d);
   return cudaGetLastError();
 }
 
