@@ -87,6 +87,8 @@ typedef enum {
                                           combination of W^n and W^(s) without the flux update
                                           (last resort of the positivity repair; that cell is
                                           not conservative in that stage) */
+#define ASE_DF_FLAG_SYNC        0x10u  /* internal error: a grid barrier of the positivity repair
+                                          gave up waiting (the stage's repair is incomplete) */
 
 /* Problem statement (Sec. 2: 1D/2D Euler on a uniform Cartesian grid). */
 typedef struct {
@@ -220,7 +222,7 @@ const char* ase_df_last_error(const ase_df_ctx* ctx);
  * stops recording; while it records, the two sweeps of a stage run one after the
  * other on the caller's stream, so that each launch is timed alone).  ase_df_profile_read synchronises, then returns per kernel kind
  * (0: x-face sweep, 1: y-face sweep, 2: combine, 3: wave-speed reduction, 4: positivity
- * repair pass) the summed milliseconds ms[5] and the launch counts n[5]; at most 65536
+ * repair, one launch per stage) the summed milliseconds ms[5] and the launch counts n[5]; at most 65536
  * launches are recorded. */
 ase_df_status ase_df_profile_enable(ase_df_ctx* ctx, int32_t enable);
 ase_df_status ase_df_profile_read(ase_df_ctx* ctx, double* ms, int64_t* n);

@@ -26,6 +26,7 @@ FLAG_NONPHYSICAL = 0x1
 FLAG_POSITIVITY = 0x2
 FLAG_DT = 0x4
 FLAG_FROZEN = 0x8
+FLAG_SYNC = 0x10
 
 
 class AseDfError(RuntimeError):

@@ -439,16 +439,9 @@ static cudaError_t combine(ase_df_ctx* c, int stage, const double* Wn, const dou
   r.dt_fixed = dt_fixed;
   r.stage = stage;
   r.tfrac = rk_tfrac(stage);
-  for (int pass = 1; pass <= kRepairPasses && e == cudaSuccess; ++pass) {
-    r.pass = pass;
-    ProfScope prof(c, s, 4);
-    e = launch_repair(c->dim, c->g, r, s);
-  }
-  if (e == cudaSuccess) {
-    ProfScope prof(c, s, 4);
-    e = launch_freeze(c->dim, c->g, r, s);
-  }
-  return e;
+  r.pass = 1;
+  ProfScope prof(c, s, 4);
+  return launch_repair_all(c->dim, c->g, r, s);
 }
 
 static ase_df_status check_ptrs(ase_df_ctx* c, const void* W, const void* sx, const void* sy) {

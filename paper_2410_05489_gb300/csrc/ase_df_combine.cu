@@ -7,12 +7,14 @@
 //   W2 = 3/4 W^n + 1/4 W1 + 1/4 dt L(W1)
 //   W^{n+1} = 1/3 W^n + 2/3 W2 + 2/3 dt L(W2)          (Sec. 2.3, Eq. SSP-RK3).
 //
-// Positivity of a stage update (the paper's "transition to a first-order scheme for
-// preserving positivity", done a posteriori): the combine kernel marks every cell whose
-// new average is non-physical; each repair pass gives every face of a marked cell the
-// first-order Lax-Friedrichs flux of the stage's cell averages (and sigma 1e30) and
-// updates again every cell next to such a face; cells that turn non-physical in a pass
-// are marked for the next one.  Passes with nothing to do return at once.  Last resort:
+// Positivity of a stage update (the paper falls back to a first-order scheme where
+// positivity is at risk; here that is done a posteriori): the combine kernel marks every
+// cell whose new average is non-physical; each repair pass gives every face of a marked
+// cell the first-order Lax-Friedrichs flux of the stage's cell averages (and sigma 1e30)
+// and updates again every cell next to such a face; cells that turn non-physical in a
+// pass are marked for the next one.  All passes of a stage run in one cooperative launch
+// with a grid barrier between them, which returns at once when the combine marked no
+// cell and stops after a pass that marked none.  Last resort:
 // a cell still non-physical after the passes keeps the stage's combination of W^n and
 // W^(s) without the flux update (a convex combination of physical states); where
 // rounding of a near-vacuum pressure still leaves p <= 0, E is raised so that
@@ -20,6 +22,9 @@
 // stage, and ASE_DF_FLAG_FROZEN is raised.
 
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
 
 #include "ase_df_adjoint.cuh"
 #include "ase_df_combine_body.cuh"
@@ -33,16 +38,56 @@ __global__ void __launch_bounds__(256) combine_kernel(const GridInfo g, const Co
   combine_range<DIM>(g, a, first, (size_t)g.nx * g.ny, stride, first == 0);
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(256) repair_kernel(const GridInfo g, const RepairArgs a) {
-  const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
-  repair_range<DIM>(g, a, first, (size_t)g.nx * g.ny, stride);
+// Barrier over the CTAs of a cooperative launch (all co-resident), on the counters of the
+// status word.  Thread 0 of each CTA arrives; the last arrival resets the count and
+// advances the generation, the others wait for it.  The wait gives up after a bounded
+// number of polls (about a second), raises ASE_DF_FLAG_SYNC and returns false, so that a
+// barrier that cannot complete ends the kernel instead of holding the GPU.
+__device__ bool grid_barrier(DevState* st) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &st->bar_gen;
+    const unsigned int g0 = *gen;
+    __threadfence();  // this CTA's writes before the arrival
+    ok = 1;
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+      st->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      long long polls = 0;
+      while (*gen == g0) {
+        if (++polls > (1ll << 20)) {
+          atomicOr(&st->flags, 0x10u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
 }
 
+// Repair passes 1..kRepairPasses and the freeze of one stage in one launch (cooperative:
+// every CTA is resident).  Each pass is repair_range over the same cells per thread as the
+// freeze, with a grid barrier between passes; the counters that decide whether another
+// pass runs are read after the barrier, so every CTA takes the same decision.
 template <int DIM>
-__global__ void __launch_bounds__(256) freeze_kernel(const GridInfo g, const RepairArgs a) {
+__global__ void __launch_bounds__(256) repair_all_kernel(const GridInfo g, RepairArgs a) {
+  if (__ldcg(&a.st->cnt[0]) == 0u) return;  // the stage update was physical everywhere
   const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
-  freeze_range<DIM>(g, a, first, (size_t)g.nx * g.ny, stride);
+  const size_t ncell = (size_t)g.nx * g.ny;
+  for (int pass = 1; pass <= kRepairPasses; ++pass) {
+    a.pass = pass;
+    repair_range<DIM>(g, a, first, ncell, stride);
+    if (!grid_barrier(a.st)) return;
+    if (__ldcg(&a.st->cnt[pass]) == 0u) break;  // no cell turned non-physical in this pass
+  }
+  freeze_range<DIM>(g, a, first, ncell, stride);
 }
 
 template <int DIM>
@@ -60,6 +105,8 @@ __global__ void state_kernel(DevState* st, int op, double t) {
     st->max_speed_bits = 0ull;
     st->repaired_total = 0ull;
     st->frozen_total = 0ull;
+    st->bar_count = 0u;
+    st->bar_gen = 0u;
   }
 }
 
@@ -87,18 +134,36 @@ cudaError_t launch_combine(int dim, const GridInfo& g, const CombineArgs& a, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_repair(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s) {
+template <int DIM>
+cudaError_t repair_all_launch(const GridInfo& g, const RepairArgs& a, cudaStream_t s) {
+  // resident CTAs of this kernel on the device, once per process and dimension
+  static std::atomic<int> resident{0};
+  int nres = resident.load();
+  if (nres == 0) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_all_kernel<DIM>, 256, 0);
+    if (e != cudaSuccess) return e;
+    nres = std::max(1, nsm * per_sm);
+    resident.store(nres);
+  }
   const size_t ncell = (size_t)g.nx * g.ny;
-  if (dim == 1) repair_kernel<1><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
-  else repair_kernel<2><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::min<size_t>((size_t)nres, (ncell + 255) / 256));
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, repair_all_kernel<DIM>, g, a);
 }
 
-cudaError_t launch_freeze(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s) {
-  const size_t ncell = (size_t)g.nx * g.ny;
-  if (dim == 1) freeze_kernel<1><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
-  else freeze_kernel<2><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
-  return cudaGetLastError();
+cudaError_t launch_repair_all(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s) {
+  return (dim == 1) ? repair_all_launch<1>(g, a, s) : repair_all_launch<2>(g, a, s);
 }
 
 cudaError_t launch_max_speed(int dim, const GridInfo& g, const SpeedArgs& a, cudaStream_t s) {

@@ -127,14 +127,16 @@ template <int DIM>
 __device__ __forceinline__ void repair_range(const GridInfo& g, const RepairArgs& a, size_t first,
                                              size_t last, size_t stride) {
   constexpr int C = (DIM == 1) ? 3 : 4;
-  if (a.st->cnt[a.pass - 1] == 0u) return;  // no new marks in the previous pass
+  // marks and counters of other threads' cells are read through L2 (ld.cg): in the
+  // single-launch repair they were written by other CTAs during this kernel
+  if (__ldcg(&a.st->cnt[a.pass - 1]) == 0u) return;  // no new marks in the previous pass
   const int nx = g.nx, ny = g.ny;
   const size_t ncell = (size_t)nx * ny;
   const double dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.st->dt;
   const double ts = stage_time(a.st, a.tfrac, dt);  // for time-dependent ghosts
   const unsigned int pass = (unsigned int)a.pass;
   auto marked = [&](int i, int j) {
-    const unsigned int m = a.mark[(size_t)j * nx + i];
+    const unsigned int m = __ldcg(&a.mark[(size_t)j * nx + i]);
     return m >= 1u && m <= pass;
   };
   unsigned int nnew = 0, nbad = 0;
@@ -218,7 +220,7 @@ template <int DIM>
 __device__ __forceinline__ void freeze_range(const GridInfo& g, const RepairArgs& a, size_t first,
                                              size_t last, size_t stride) {
   constexpr int C = (DIM == 1) ? 3 : 4;
-  if (a.st->cnt[0] == 0u) return;  // the stage update was physical everywhere
+  if (__ldcg(&a.st->cnt[0]) == 0u) return;  // the stage update was physical everywhere
   const size_t ncell = (size_t)g.nx * g.ny;
   const double dt = a.dt_fixed > 0.0 ? a.dt_fixed : a.st->dt;
   unsigned int nfrozen = 0;

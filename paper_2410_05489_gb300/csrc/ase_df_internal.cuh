@@ -101,6 +101,9 @@ struct DevState {
   // Algorithm 1 taken by the normal and (2D) the tangential reconstruction, and the Gauss
   // points that took first-order states; slots as kBranchSlots.
   unsigned long long hist[8];
+  // Grid barrier of the single-launch repair (repair_all_kernel): arrivals and generation.
+  // bar_count is 0 between barriers; ase_df_reset clears both.
+  unsigned int bar_count, bar_gen;
 };
 
 // Slots of the branch histogram: linear 9th, 7th, 5th order, WENOZ-AO(5,3)+DF, linear 3rd
@@ -208,8 +211,9 @@ cudaError_t launch_sweep_r9(int dim, int dir, const GridInfo& g, const SweepArgs
 
 cudaError_t launch_combine(int dim, const GridInfo& g, const CombineArgs& a, cudaStream_t s);
 cudaError_t launch_max_speed(int dim, const GridInfo& g, const SpeedArgs& a, cudaStream_t s);
-cudaError_t launch_repair(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s);
-cudaError_t launch_freeze(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s);
+// All repair passes and the freeze of one stage in one cooperative launch (returns at once
+// when the stage update was physical everywhere; a grid barrier between passes).
+cudaError_t launch_repair_all(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s);
 cudaError_t launch_state_kernel(DevState* st, int op, double t, cudaStream_t s);
 
 // Tables of scheme order r (host, exact rational arithmetic, no allocation); false only if a
