@@ -125,12 +125,18 @@ int grid_for(size_t n, int threads) {
   return (int)b;
 }
 
+// Threads per block of the per-cell kernels: 256, or 32 on grids of fewer than 256 cells per
+// SM.  FP64 issues at 2 instructions per cycle per SM, so the per-cell FP64 work of a small
+// grid runs faster spread thinly over many SMs than packed into a few 256-thread CTAs.
+int cell_block(size_t n) { return n < (size_t)device_sm_count() * 256 ? 32 : 256; }
+
 }  // namespace
 
 cudaError_t launch_combine(int dim, const GridInfo& g, const CombineArgs& a, cudaStream_t s) {
   const size_t ncell = (size_t)g.nx * g.ny;
-  if (dim == 1) combine_kernel<1><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
-  else combine_kernel<2><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
+  const int nt = cell_block(ncell);
+  if (dim == 1) combine_kernel<1><<<grid_for(ncell, nt), nt, 0, s>>>(g, a);
+  else combine_kernel<2><<<grid_for(ncell, nt), nt, 0, s>>>(g, a);
   return cudaGetLastError();
 }
 
@@ -168,8 +174,9 @@ cudaError_t launch_repair_all(int dim, const GridInfo& g, const RepairArgs& a, c
 
 cudaError_t launch_max_speed(int dim, const GridInfo& g, const SpeedArgs& a, cudaStream_t s) {
   const size_t ncell = (size_t)g.nx * g.ny;
-  if (dim == 1) max_speed_kernel<1><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
-  else max_speed_kernel<2><<<grid_for(ncell, 256), 256, 0, s>>>(g, a);
+  const int nt = cell_block(ncell);
+  if (dim == 1) max_speed_kernel<1><<<grid_for(ncell, nt), nt, 0, s>>>(g, a);
+  else max_speed_kernel<2><<<grid_for(ncell, nt), nt, 0, s>>>(g, a);
   return cudaGetLastError();
 }
 

@@ -29,8 +29,9 @@ namespace asedf {
 namespace {
 
 // PLAN = false: a uniform grid (x: tile column, y: blocks of TT lines, the last one ragged).
-template <int R, int DIM, int DIR, int TT, bool PLAN>
-__global__ void __launch_bounds__(Tile<R, DIM, TT>::NT, 2)
+// TN, NT: faces along the sweep and threads of a tile (the Tile defaults, or the small 1D tile).
+template <int R, int DIM, int DIR, int TT, bool PLAN, int TN = (DIM == 2) ? 8 : 255, int NT = 256>
+__global__ void __launch_bounds__(NT, (NT == 256) ? 2 : 1)
 sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tables T, const TilePlan P) {
   extern __shared__ double smem[];
   if (DIR == 0 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x <= kRepairPasses) {
@@ -40,22 +41,22 @@ sweep_kernel(const GridInfo g, const SweepArgs args, const __grid_constant__ Tab
   if constexpr (PLAN) {
     int col, b0, tt;
     plan_tile(P, blockIdx.x, col, b0, tt);
-    sweep_tile<R, DIM, DIR, TT>(g, args, T, col * Tile<R, DIM, TT>::TN, b0, tt, smem);
+    sweep_tile<R, DIM, DIR, TT, TN, NT>(g, args, T, col * TN, b0, tt, smem);
   } else {
-    sweep_tile<R, DIM, DIR, TT>(g, args, T, blockIdx.x * Tile<R, DIM, TT>::TN, blockIdx.y * TT, TT, smem);
+    sweep_tile<R, DIM, DIR, TT, TN, NT>(g, args, T, blockIdx.x * TN, blockIdx.y * TT, TT, smem);
   }
 }
 
-template <int R, int DIM, int DIR, int TT, bool PLAN>
+template <int R, int DIM, int DIR, int TT, bool PLAN, int TN = (DIM == 2) ? 8 : 255, int NT = 256>
 cudaError_t launch_grid(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s, dim3 grid,
                         const TilePlan& p) {
-  using TL = Tile<R, DIM, TT>;
+  using TL = Tile<R, DIM, TT, TN, NT>;
   const size_t smem = TL::smem_doubles * sizeof(double);
-  auto kern = sweep_kernel<R, DIM, DIR, TT, PLAN>;
+  auto kern = sweep_kernel<R, DIM, DIR, TT, PLAN, TN, NT>;
   static std::atomic<unsigned long long> attr_done{0ull};
   cudaError_t e = ensure_smem_limit(kern, smem, attr_done);
   if (e != cudaSuccess) return e;
-  kern<<<grid, TL::NT, smem, s>>>(g, a, t, p);
+  kern<<<grid, NT, smem, s>>>(g, a, t, p);
   return cudaGetLastError();
 }
 
@@ -82,6 +83,12 @@ cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaS
     if (cols > 0x7fffffffLL || q > 65535) return cudaErrorInvalidConfiguration;
     return launch_grid<R, DIM, DIR, TT, false>(g, a, t, s, dim3((unsigned)cols, (unsigned)q), none);
   } else {
+    // fewer 255-face tiles than SMs: 31-face tiles in CTAs of 32 threads spread the FP64 work
+    if (cols < device_sm_count()) {
+      using TS = Tile<R, 1, 1, 31, 32>;
+      const long long cs = (n + 1 + TS::TN - 1) / TS::TN;
+      return launch_grid<R, DIM, DIR, TT, false, 31, 32>(g, a, t, s, dim3((unsigned)cs), none);
+    }
     return launch_grid<R, DIM, DIR, TT, false>(g, a, t, s, dim3((unsigned)cols), none);
   }
 }

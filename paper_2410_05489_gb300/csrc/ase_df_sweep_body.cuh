@@ -206,7 +206,10 @@ __device__ __forceinline__ void tang_eval(const double* v, int vs, const Branch&
 // uses 8 x 64 in 2D (measured on GB300 against 16 x 32, 16 x 16, 32 x 16 and 8 x 32: 1.4 %
 // faster than 16 x 32 at order 9, from the smaller share of halo lines); 255 faces in 1D (256
 // reconstructing cells: phase 1 gives every one of the 256 threads one cell).
-template <int R, int DIM, int TT_ = (DIM == 2) ? 64 : 1, int TN_ = (DIM == 2) ? 8 : 255>
+// A 1D sweep of fewer than one 255-face tile per SM takes tiles of 31 faces in CTAs of 32
+// threads (Tile<R, 1, 1, 31, 32>): FP64 issues at 2 instructions per cycle per SM, so one
+// CTA of 256 threads on a 200-cell problem runs its FP64 work on one SM, 16 us per sweep.
+template <int R, int DIM, int TT_ = (DIM == 2) ? 64 : 1, int TN_ = (DIM == 2) ? 8 : 255, int NT_ = 256>
 struct Tile {
   static constexpr int K = (R - 1) / 2;
   static constexpr int C = (DIM == 1) ? 3 : 4;
@@ -214,23 +217,46 @@ struct Tile {
   static constexpr int G = (DIM == 2) ? (R == 3 ? 1 : K) : 1;
   static constexpr int TN = TN_;                     // faces along the sweep
   static constexpr int TT = TT_;                     // lines
-  static constexpr int NT = 256;                     // threads
+  static constexpr int NT = NT_;                     // threads
   static constexpr int NA = TN + 1 + 2 * K;          // staged cells along the sweep
   static constexpr int NB = TT + 2 * KT;             // staged lines
   static constexpr int NQ = TN + 1;                  // cells reconstructed along the sweep
   static constexpr int NSN = TN + 2 * K;             // normal faces staged per line
   static constexpr int NST = TT + 2 * K;             // tangential faces staged per column
-  static constexpr size_t smem_doubles =
+  // queue of deferred fallback items (defer_item) and its two counters, after the arrays
+  static constexpr int QCAP = (NQ * NB > TN * TT) ? NQ * NB : TN * TT;
+  static constexpr size_t queue_offset =
       (size_t)C * NB * NA + 2 * (size_t)C * NB * NQ + (size_t)NB * NSN + (DIM == 2 ? (size_t)NQ * NST : 0);
+  static constexpr size_t smem_doubles = queue_offset + ((size_t)QCAP + 2 + 1) / 2;
 };
+
+// Deferral of the work items whose branch is the WENOZ-AO(5,3)+DF fallback.  Its arithmetic
+// (smoothness indicators, nonlinear weights, four sub-polynomials) is several times that of
+// a linear branch, so a warp holding one such item among linear ones would run the long path
+// with most lanes idle.  A deferred item goes to a queue in shared memory, which every thread
+// of the CTA works through after the linear items.  The lanes of a warp that defer reserve
+// their slots together: one ballot, one shared-memory atomic by the first of them, and each
+// lane's rank among them.  Returns whether this lane deferred its item.
+__device__ __forceinline__ bool defer_item(bool defer, int item, int* queue, unsigned int* count) {
+  const unsigned int active = __activemask();
+  const unsigned int m = __ballot_sync(active, defer);
+  if (m == 0u) return false;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned int base = 0u;
+  if (lane == leader) base = atomicAdd(count, (unsigned int)__popc(m));
+  base = __shfl_sync(active, base, leader);
+  if (defer) queue[base + __popc(m & ((1u << lane) - 1u))] = item;
+  return defer;
+}
 
 // One tile: faces a0 .. a0+TN-1 along the sweep on lines b0 .. b0+tt-1, 1 <= tt <= TT
 // (threadIdx.x is the worker index); smem holds Tile<R, DIM, TT>::smem_doubles doubles,
 // laid out for TT lines whatever tt is.
-template <int R, int DIM, int DIR, int TT_ = (DIM == 2) ? 64 : 1>
+template <int R, int DIM, int DIR, int TT_ = (DIM == 2) ? 64 : 1, int TN_ = (DIM == 2) ? 8 : 255, int NT_ = 256>
 __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& args, const Tables& T, int a0,
                                            int b0, int tt, double* smem) {
-  using TL = Tile<R, DIM, TT_>;
+  using TL = Tile<R, DIM, TT_, TN_, NT_>;
   constexpr int K = TL::K, C = TL::C, KT = TL::KT, G = TL::G;
   constexpr int TN = TL::TN, TT = TL::TT, NT = TL::NT;
   constexpr int NA = TL::NA, NB = TL::NB, NQ = TL::NQ, NSN = TL::NSN, NST = TL::NST;
@@ -252,6 +278,10 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   __shared__ unsigned int hist_s[kBranchSlots];
   const bool counting = args.hist != nullptr;
   if (counting && tid < kBranchSlots) hist_s[tid] = 0u;
+  // queue of deferred fallback items: phase 1 (cells) and phase 2 (faces) share the slots
+  int* s_queue = reinterpret_cast<int*>(smem + TL::queue_offset);
+  unsigned int* s_qn = reinterpret_cast<unsigned int*>(s_queue + TL::QCAP);
+  if (tid < 2) s_qn[tid] = 0u;
   // ---- stage cell averages: cells a0-1-K .. a0+TN-1+K, lines b0-KT .. b0+tt+KT-1 ----
   for (int idx = tid; idx < C * nb * NA; idx += NT) {
     int c, bb, aa;
@@ -287,98 +317,123 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
   // xi = 0 and xi = -1; the two end cells serve one tile face each (qa = 0: its xi = 0
   // value, the left state of face a0; qa = NQ-1: its xi = -1 value), so they come last in
   // the work list and evaluate one point.
-  for (int it = tid; it < NQ * nb; it += NT) {
-    if (it < (NQ - 2) * nb) {
-      int qa, bb;
-      if (DIR == 0) { qa = 1 + it % (NQ - 2); bb = it / (NQ - 2); }
-      else { bb = it % nb; qa = 1 + it / nb; }
+  // Fallback items are deferred (defer_item) and done in a second pass.
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int count = (pass == 0) ? NQ * nb : (int)s_qn[0];
+    for (int k = tid; k < count; k += NT) {
+      const int it = (pass == 0) ? k : s_queue[k];
+      int qa, bb, pt;  // pt -1: an interior cell, both points; 0 / 1: an end cell, one point
+      if (it < (NQ - 2) * nb) {
+        if (DIR == 0) { qa = 1 + it % (NQ - 2); bb = it / (NQ - 2); }
+        else { bb = it % nb; qa = 1 + it / nb; }
+        pt = -1;
+      } else {
+        const int e = it - (NQ - 2) * nb;
+        bb = e % nb;  // pt 0: cell qa = 0 at xi = 0; 1: qa = NQ-1 at xi = -1
+        pt = e / nb;
+        qa = pt * (NQ - 1);
+      }
       const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const double* v = sW + (c * NB + bb) * NA + qa + K;  // W_0 of this cell
-        double out[2];
-        recon_eval<R, 2>(v, 1, br, T, 0, out);
-        sQP[(c * NB + bb) * NQ + qa] = out[0];
-        sQM[(c * NB + bb) * NQ + qa] = out[1];
-      }
-    } else {
-      const int e = it - (NQ - 2) * nb;
-      const int bb = e % nb, pt = e / nb;  // pt 0: cell qa = 0 at xi = 0; 1: qa = NQ-1 at xi = -1
-      const int qa = pt * (NQ - 1);
-      const Branch br = select_branch<R>(sSn + bb * NSN + qa, g.thres);
-      double* dst = pt ? sQM : sQP;
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const double* v = sW + (c * NB + bb) * NA + qa + K;
-        double out[1];
-        recon_eval<R, 1>(v, 1, br, T, pt, out);
-        dst[(c * NB + bb) * NQ + qa] = out[0];
-      }
-    }
-  }
-  __syncthreads();
-
-  // ---- phase 2: faces ----
-  for (int it = tid; it < TN * tt; it += NT) {
-    int fa, tb;
-    if (DIR == 0) { fa = it % TN; tb = it / TN; }
-    else { tb = it % tt; fa = it / tt; }
-    const int f = a0 + fa, b = b0 + tb;
-    if (f > n || b >= mlin) continue;
-    double st[2][G][C];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int qa = fa + side;  // left state: cell f-1 (plus face); right: cell f (minus face)
-      const double* Q = side == 0 ? sQP : sQM;
-      if (counting) {  // the normal branch of this state's cell, as phase 1 chose it
-        const Branch bn = select_branch<R>(sSn + (tb + KT) * NSN + qa, g.thres);
-        atomicAdd(&hist_s[branch_slot(bn.m)], 1u);
-      }
-      if (DIM == 2) {
-        const Branch bt = select_branch<R>(sSt + qa * NST + tb, g.thres);
-        if (counting) atomicAdd(&hist_s[branch_slot(bt.m)], 1u);
+      if (R >= 5 && pass == 0 && defer_item(br.m == 0, it, s_queue, &s_qn[0])) continue;
+      if (pt < 0) {
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const double* v = Q + (c * NB + tb + K) * NQ + qa;
-          double out[G];
-          tang_eval<R, G>(v, NQ, bt, T, out);
-#pragma unroll
-          for (int q = 0; q < G; ++q) st[side][q][c] = out[q];
+          const double* v = sW + (c * NB + bb) * NA + qa + K;  // W_0 of this cell
+          double out[2];
+          recon_eval<R, 2>(v, 1, br, T, 0, out);
+          sQP[(c * NB + bb) * NQ + qa] = out[0];
+          sQM[(c * NB + bb) * NQ + qa] = out[1];
         }
       } else {
+        double* dst = pt ? sQM : sQP;
 #pragma unroll
-        for (int c = 0; c < C; ++c) st[side][0][c] = Q[c * NQ + qa];
+        for (int c = 0; c < C; ++c) {
+          const double* v = sW + (c * NB + bb) * NA + qa + K;
+          double out[1];
+          recon_eval<R, 1>(v, 1, br, T, pt, out);
+          dst[(c * NB + bb) * NQ + qa] = out[0];
+        }
       }
     }
-    // cell averages either side of the face (read by a Gauss point only if it falls back)
-    const double* ca = sW + (tb + KT) * NA + fa + K;
-    const double* cb = ca + 1;
-    double Fs[C];
+    __syncthreads();  // pass 0: the queue is complete; last pass: phase 1 is done
+    if (R < 5) break;
+  }
+
+  // ---- phase 2: faces ----
+  // Faces with a fallback tangential reconstruction on either side are deferred (2D).
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int count = (pass == 0) ? TN * tt : (int)s_qn[1];
+    for (int k = tid; k < count; k += NT) {
+      const int it = (pass == 0) ? k : s_queue[k];
+      int fa, tb;
+      if (DIR == 0) { fa = it % TN; tb = it / TN; }
+      else { tb = it % tt; fa = it / tt; }
+      const int f = a0 + fa, b = b0 + tb;
+      if (f > n || b >= mlin) continue;
+      Branch bt[2];
+      if (DIM == 2) {
+        bt[0] = select_branch<R>(sSt + fa * NST + tb, g.thres);  // the columns of the two states
+        bt[1] = select_branch<R>(sSt + (fa + 1) * NST + tb, g.thres);
+        if (R >= 5 && pass == 0 && defer_item(bt[0].m == 0 || bt[1].m == 0, it, s_queue, &s_qn[1])) continue;
+      }
+      double st[2][G][C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) Fs[c] = 0.0;
-    double ssum = 0.0;
-    unsigned int nfb = 0u;
+      for (int side = 0; side < 2; ++side) {
+        const int qa = fa + side;  // left state: cell f-1 (plus face); right: cell f (minus face)
+        const double* Q = side == 0 ? sQP : sQM;
+        if (counting) {  // the normal branch of this state's cell, as phase 1 chose it
+          const Branch bn = select_branch<R>(sSn + (tb + KT) * NSN + qa, g.thres);
+          atomicAdd(&hist_s[branch_slot(bn.m)], 1u);
+        }
+        if (DIM == 2) {
+          if (counting) atomicAdd(&hist_s[branch_slot(bt[side].m)], 1u);
 #pragma unroll
-    for (int q = 0; q < G; ++q) {
-      double sg;
-      nfb += lf_point_acc<C, NI, TI>(st[0][q], st[1][q], ca, cb, NB * NA, g.gm1, g.gg1, T.hgw[q], g.gm1_hgw[q],
-                                     Fs, sg) ? 1u : 0u;
-      ssum += sg;
+          for (int c = 0; c < C; ++c) {
+            const double* v = Q + (c * NB + tb + K) * NQ + qa;
+            double out[G];
+            tang_eval<R, G>(v, NQ, bt[side], T, out);
+#pragma unroll
+            for (int q = 0; q < G; ++q) st[side][q][c] = out[q];
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < C; ++c) st[side][0][c] = Q[c * NQ + qa];
+        }
+      }
+      // cell averages either side of the face (read by a Gauss point only if it falls back)
+      const double* ca = sW + (tb + KT) * NA + fa + K;
+      const double* cb = ca + 1;
+      double Fs[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) Fs[c] = 0.0;
+      double ssum = 0.0;
+      unsigned int nfb = 0u;
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        double sg;
+        nfb += lf_point_acc<C, NI, TI>(st[0][q], st[1][q], ca, cb, NB * NA, g.gm1, g.gg1, T.hgw[q], g.gm1_hgw[q],
+                                       Fs, sg) ? 1u : 0u;
+        ssum += sg;
+      }
+      if (nfb) {
+        atomicOr(&args.st->flags, 0x2u);
+        if (counting) atomicAdd(&hist_s[kBranchSlots - 1], nfb);
+      }
+      const double sface = (G == 1) ? ssum : ssum * (1.0 / G);
+      if (DIR == 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) args.F[((size_t)c * g.ny + b) * (g.nx + 1) + f] = Fs[c];
+        args.s_out[(size_t)b * (g.nx + 1) + f] = sface;
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) args.F[((size_t)c * (g.ny + 1) + f) * g.nx + b] = Fs[c];
+        args.s_out[(size_t)f * g.nx + b] = sface;
+      }
     }
-    if (nfb) {
-      atomicOr(&args.st->flags, 0x2u);
-      if (counting) atomicAdd(&hist_s[kBranchSlots - 1], nfb);
-    }
-    const double sface = (G == 1) ? ssum : ssum * (1.0 / G);
-    if (DIR == 0) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) args.F[((size_t)c * g.ny + b) * (g.nx + 1) + f] = Fs[c];
-      args.s_out[(size_t)b * (g.nx + 1) + f] = sface;
-    } else {
-#pragma unroll
-      for (int c = 0; c < C; ++c) args.F[((size_t)c * (g.ny + 1) + f) * g.nx + b] = Fs[c];
-      args.s_out[(size_t)f * g.nx + b] = sface;
-    }
+    if (DIM == 1 || R < 5) break;
+    __syncthreads();  // the queue is complete
   }
   if (counting) {
     __syncthreads();
