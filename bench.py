@@ -532,8 +532,13 @@ def batched_bench(A, torch, args):
     from paper_2410_05489_gb300 import batch as Bt
 
     probs = P.batched_problems()
+    order = getattr(args, "batch_order", 0)
     cut = getattr(args, "batch_cut", 0)
-    if cut:  # the first cut/2 1D and the first cut/2 2D problems (the set lists the 256 1D ones first)
+    if order:  # the 2D problems of one order (the first `cut` of them if cut is given)
+        probs = [p for p in probs if p[0].ndim == 2 and p[0].order == order]
+        if cut:
+            probs = probs[:cut]
+    elif cut:  # the first cut/2 1D and the first cut/2 2D problems (the set lists the 256 1D ones first)
         probs = probs[:cut // 2] + probs[256:256 + cut - cut // 2]
     bt = Bt.Batch([p for p, _ in probs], [w for _, w in probs])
     tune = Bt.autotune(bt, steps=1)
@@ -566,9 +571,13 @@ def batched_bench(A, torch, args):
     ms_1 = e0.elapsed_time(e1) / ksteps
     for s_ in solvers:
         s_.close()
+    workload = ("512 problems (256 1D, N log-uniform 128..16384; 256 2D N^2, N log-uniform 64..512), "
+                "random Riemann data, orders 3/5/7/9, outflow, CFL 0.5, seed 20241008")
+    if order or cut:
+        workload = "%d problems of the batched set (%s) -- " % (
+            len(probs), ("2D, order %d" % order) if order else "first 1D and 2D ones") + workload
     return {
-        "workload": "512 problems (256 1D, N log-uniform 128..16384; 256 2D N^2, N log-uniform 64..512), "
-                    "random Riemann data, orders 3/5/7/9, outflow, CFL 0.5, seed 20241008",
+        "workload": workload,
         "cells": cells, "steps": ksteps,
         "value": round(cells * 3 / (ms_b * 1e-3) / 1e6, 3), "unit": UNIT,
         "ms_per_step": round(ms_b, 4),
@@ -1016,6 +1025,8 @@ def main():
                     help="measure every workload configuration (GPU and CPU oracle) instead of the headline line")
     ap.add_argument("--only", choices=("batched", "adjoint"),
                     help="time only the batched or only the adjoint workload (one JSON line; for profiling)")
+    ap.add_argument("--batch-order", type=int, default=0, choices=(0, 3, 5, 7, 9),
+                    help="with --only batched: only the 2D problems of this order")
     ap.add_argument("--batch-cut", type=int, default=0,
                     help="with --only batched: the first N/2 1D and the first N/2 2D problems of the batched set")
     args = ap.parse_args()
