@@ -357,7 +357,7 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
       }
     }
     __syncthreads();  // pass 0: the queue is complete; last pass: phase 1 is done
-    if (R < 5) break;
+    if (R < 5 || s_qn[0] == 0u) break;
   }
 
   // ---- phase 2: faces ----
@@ -432,8 +432,9 @@ __device__ __forceinline__ void sweep_tile(const GridInfo& g, const SweepArgs& a
         args.s_out[(size_t)f * g.nx + b] = sface;
       }
     }
-    if (DIM == 1 || R < 5) break;
+    if (DIM == 1 || R < 5 || pass == 1) break;
     __syncthreads();  // the queue is complete
+    if (s_qn[1] == 0u) break;
   }
   if (counting) {
     __syncthreads();
