@@ -77,7 +77,16 @@ cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaS
     const long long q = (m + TT - 1) / TT;
     if (use_tile_plan(cols, m, TT, slots)) {
       long long tiles;
-      const TilePlan p = make_tile_plan(cols, m, TT, slots, tiles);
+      TilePlan p = make_tile_plan(cols, m, TT, slots, tiles);
+      // the smallest grids: tiles of down to 8 lines while the two concurrent sweeps still fit
+      // in one wave (64^2: 72 tiles per sweep instead of 36, measured +11 %; 128^2 would need two
+      // waves and keeps 16)
+      long long tiles8;
+      const TilePlan p8 = make_tile_plan(cols, m, TT, slots, tiles8, 8);
+      if (tiles8 > tiles && 2 * tiles8 <= slots) {
+        p = p8;
+        tiles = tiles8;
+      }
       return launch_grid<R, DIM, DIR, TT, true>(g, a, t, s, dim3((unsigned)tiles), p);
     }
     if (cols > 0x7fffffffLL || q > 65535) return cudaErrorInvalidConfiguration;

@@ -57,13 +57,15 @@ inline bool use_tile_plan(long long cols, int m, int tt_max, int slots) {
 
 // The plan: tiles of up to tt_max lines need q = ceil(m / tt_max) blocks per column and
 // w = ceil(cols q / slots) waves; the plan fills all w waves with w slots tiles, at most
-// max(q, ceil(m / 16)) blocks per column so that no tile is under ~16 lines.  `tiles` is the
-// CTA count of the launch.  Requires cols >= 1, m >= 1, tt_max >= 1, slots >= 1.
-inline TilePlan make_tile_plan(long long cols, int m, int tt_max, int slots, long long& tiles) {
+// max(q, ceil(m / min_lines)) blocks per column so that no tile is under ~min_lines lines.
+// `tiles` is the CTA count of the launch.  Requires cols >= 1, m >= 1, tt_max >= 1,
+// slots >= 1, min_lines >= 1.
+inline TilePlan make_tile_plan(long long cols, int m, int tt_max, int slots, long long& tiles,
+                               int min_lines = 16) {
   const long long q = (m + tt_max - 1) / tt_max;
   const long long t0 = cols * q;
   const long long target = (t0 + slots - 1) / slots * slots;
-  const long long nb_max = std::max(q, (long long)(m + 15) / 16);
+  const long long nb_max = std::max(q, (long long)(m + min_lines - 1) / min_lines);
   tiles = std::min(target, cols * nb_max);
   TilePlan p;
   p.nb_lo = (int)(tiles / cols);

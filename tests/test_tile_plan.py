@@ -21,4 +21,4 @@ def test_tile_plan_covers_every_face_line_once(tmp_path):
     res = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert res.returncode == 0, res.stdout + res.stderr
     assert res.stdout.startswith("ok "), res.stdout
-    assert int(res.stdout.split()[1]) == 29 * 22 * 7
+    assert int(res.stdout.split()[1]) == 2 * 29 * 22 * 7  # line floors 16 and 8

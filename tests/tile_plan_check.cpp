@@ -1,8 +1,9 @@
 // Host-side check of the sweep's tile plan (csrc/ase_df_tileplan.h), compiled with g++ by
 // tests/test_tile_plan.py.  Over grids of 1 .. 2048 faces and lines and 1 .. 528 CTA slots:
 // every (tile column, line) is covered by exactly one tile, tiles have 1 .. 64 lines, the
-// plan never has fewer tiles than the uniform grid, it fills whole waves unless the 16-line
-// floor caps it, and its first group's tiles are on average at least as tall as the second's.
+// plan never has fewer tiles than the uniform grid, it fills whole waves unless the line floor
+// (16, or 8 for the smallest grids) caps it, and its first group's tiles are on average at
+// least as tall as the second's.
 // Prints "ok <plans checked>" or the first failure.
 #include <cstdio>
 #include <vector>
@@ -24,14 +25,16 @@ int main() {
   const int slots_list[] = {1, 2, 3, 148, 296, 304, 528};
   const int kTN = 8, kTT = 64;
   long long checked = 0;
+  for (int floor_lines : {16, 8})
   for (int faces : faces_list) {
     for (int m : lines_list) {
       for (int slots : slots_list) {
         const long long cols = (faces + kTN - 1) / kTN;
         long long tiles = 0;
-        const TilePlan p = asedf::make_tile_plan(cols, m, kTT, slots, tiles);
+        const TilePlan p = asedf::make_tile_plan(cols, m, kTT, slots, tiles, floor_lines);
         const long long q = (m + kTT - 1) / kTT;
-        const long long nb_max = q > (m + 15) / 16 ? q : (m + 15) / 16;
+        const long long fl = (m + floor_lines - 1) / floor_lines;
+        const long long nb_max = q > fl ? q : fl;
         if (tiles < cols * q) return fail("fewer tiles than the uniform grid", faces, m, slots);
         if (tiles % slots != 0 && tiles != cols * nb_max) return fail("waves not filled", faces, m, slots);
         if ((long long)p.n1 * p.nb_lo + (long long)p.n2 * (p.nb_lo + 1) != tiles)
