@@ -60,11 +60,11 @@ cudaError_t launch_grid(const GridInfo& g, const SweepArgs& a, const Tables& t, 
   return cudaGetLastError();
 }
 
-// 2D: tiles of 8 faces x 64 lines.  While the tiles of a sweep fill at most three waves of
-// the GPU's CTA slots, the CTAs run nearly in step and a partly filled last wave costs a
-// whole tile time, so the wave-filling plan is used (measured on GB300: +7 % on the 512^2
-// vortex, whose 520 tiles of 64 lines become 608 of 51 - 57); on larger grids the CTAs
-// drift apart over the waves, the tail costs little and the uniform grid is kept.
+// 2D: tiles of 8 faces x 64 lines.  While the tiles of a sweep fill at most eight waves of
+// the GPU's CTA slots, a partly filled last wave costs part of a tile time, so the
+// wave-filling plan is used (measured on GB300: +7 % on the 512^2 vortex, whose 520 tiles of 64
+// lines become 608 of 51 - 57; +0.7 % on 1024^2, whose 2064 tiles become 2128 of 60 - 64); on
+// larger grids the uniform grid is kept.
 template <int R, int DIM, int DIR>
 cudaError_t launch(const GridInfo& g, const SweepArgs& a, const Tables& t, cudaStream_t s) {
   constexpr int TT = (DIM == 2) ? 64 : 1;

@@ -60,9 +60,10 @@ int main() {
       }
     }
   }
-  // the two launch forms of the vortex grids on 152 SMs: 512^2 planned, 1024^2 uniform
+  // on 152 SMs: 512^2 and 1024^2 planned (2 and 7 waves), 2048^2 (27 waves) uniform
   if (!asedf::use_tile_plan((513 + 7) / 8, 512, kTT, 304)) return fail("512^2 not planned", 513, 512, 304);
-  if (asedf::use_tile_plan((1025 + 7) / 8, 1024, kTT, 304)) return fail("1024^2 planned", 1025, 1024, 304);
+  if (!asedf::use_tile_plan((1025 + 7) / 8, 1024, kTT, 304)) return fail("1024^2 not planned", 1025, 1024, 304);
+  if (asedf::use_tile_plan((2049 + 7) / 8, 2048, kTT, 304)) return fail("2048^2 planned", 2049, 2048, 304);
   long long tiles = 0;
   const TilePlan p = asedf::make_tile_plan((1025 + 7) / 8, 1024, kTT, 304, tiles);
   if (tiles != 2128 || p.nb_lo != 16 || p.n2 != 64) return fail("1024^2 plan", 1025, 1024, 304);
