@@ -1,12 +1,12 @@
-"""Multi-step parity on shock data at sizes that take both launch forms of the 2D sweep:
-100 SSP-RK3 steps with CFL time steps (computed on the device), GPU against the oracle,
-every cell of the final state within 1e-9 of that component's largest magnitude.
+"""Multi-step parity on shock data at realistic sizes: 100 SSP-RK3 steps with CFL time steps
+(computed on the device), GPU against the oracle, every cell of the final state within 1e-9 of
+that component's largest magnitude.
 
 The workload is Configuration 3 (Sec. 4.3, Example 2; shocks, contacts and their
 interactions from four quadrant states):
-- on 256^2 cells: the wave-filling tile plan;
-- on 1024 x 512 cells (cells twice as wide as high): the uniform 8 x 64 tile grid in both
-  directions.
+- on 256^2 cells: the wave-filling tile plan in one wave per sweep;
+- on 1024 x 512 cells (cells twice as wide as high): the plan over 3.4 waves per sweep (the
+  uniform tile grid of larger sweeps is covered by the residual parity tests).
 
 Each runs at orders 5 and 9. The WENOZ-AO(5,3)+DF fallback takes part in every run (its
 count is asserted on the oracle's branch histogram). The GPU runs the steps as the

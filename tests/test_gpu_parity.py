@@ -235,11 +235,11 @@ def test_residual_parity_tiny_and_edge_grids(A, oracle, shape, order):
 def test_residual_parity_both_tile_grids(A, oracle, order):
     """The two launch forms of the 2D sweep on a 152-SM GPU, every face against the oracle.
     - 256^2: the wave-filling plan, with tile columns of 9 and 10 line blocks of 25 - 29 lines.
-    - 7990 x 70: the uniform 8 x 64 grid in both directions (more than three waves of tiles),
-      with ragged last blocks of 6 and 54 lines.
+    - 12001 x 110: the uniform 8 x 64 grid in both directions (3002 and 2632 tiles, more than
+      the eight waves of 304 CTA slots the plan covers), with ragged last blocks of 46 and 33 lines.
     Smooth data with random sigma, which takes the linear and the WENO/DF branches of the
     order; a face's arithmetic does not depend on the tile that computes it."""
-    for nx, ny in ((256, 256), (7990, 70)):
+    for nx, ny in ((256, 256), (12001, 110)):
         pb = P.Problem(ndim=2, nx=nx, ny=ny, order=order, bc=("outflow",) * 4)
         W = P.smooth_random(pb, 70 + order)
         # order 3 sums two faces: sigma up to 2 takes both of its branches

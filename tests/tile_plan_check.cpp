@@ -64,6 +64,9 @@ int main() {
   if (!asedf::use_tile_plan((513 + 7) / 8, 512, kTT, 304)) return fail("512^2 not planned", 513, 512, 304);
   if (!asedf::use_tile_plan((1025 + 7) / 8, 1024, kTT, 304)) return fail("1024^2 not planned", 1025, 1024, 304);
   if (asedf::use_tile_plan((2049 + 7) / 8, 2048, kTT, 304)) return fail("2048^2 planned", 2049, 2048, 304);
+  // the uniform-grid parity case of tests/test_gpu_parity.py: 12001 x 110, both directions
+  if (asedf::use_tile_plan((12002 + 7) / 8, 110, kTT, 304)) return fail("12001 x 110 x-sweep planned", 12002, 110, 304);
+  if (asedf::use_tile_plan((111 + 7) / 8, 12001, kTT, 304)) return fail("12001 x 110 y-sweep planned", 111, 12001, 304);
   long long tiles = 0;
   const TilePlan p = asedf::make_tile_plan((1025 + 7) / 8, 1024, kTT, 304, tiles);
   if (tiles != 2128 || p.nb_lo != 16 || p.n2 != 64) return fail("1024^2 plan", 1025, 1024, 304);
