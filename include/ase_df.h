@@ -197,8 +197,17 @@ ase_df_status ase_df_step_adjoint(ase_df_ctx* ctx, const double* W, const double
                                   double dt, double* Wbar, double* sxbar, double* sybar, void* stream);
 
 /* Synchronises the stream of the last call and reads the device status word (ASE_DF_FLAG_*),
- * the last dt and the time t.  Returns ASE_DF_E_NONPHYSICAL if that bit is set. */
+ * the last dt and the time t.  Returns ASE_DF_E_TIMEOUT if ASE_DF_FLAG_SYNC is set (a
+ * device wait gave up), else ASE_DF_E_NONPHYSICAL if that bit is set. */
 ase_df_status ase_df_get_status(ase_df_ctx* ctx, uint32_t* flags, double* last_dt, double* t);
+
+/* Self-test of the bounded device waits (failure detection without a GPU fault): launches on
+ * `stream` a cooperative kernel of two CTAs whose grid barrier (the one the positivity repair
+ * uses between its passes) waits for one CTA more than the grid has.  The wait gives up after
+ * about a second, the kernel raises ASE_DF_FLAG_SYNC in the status word and returns, and the
+ * barrier's arrival count is cleared; ase_df_get_status then returns ASE_DF_E_TIMEOUT until
+ * ase_df_reset.  The context stays usable. */
+ase_df_status ase_df_selftest_wait(ase_df_ctx* ctx, void* stream);
 
 /* Diagnostics of the positivity repair of the stage updates (ase_df_step): synchronises,
  * then writes into last_stage[18] (may be NULL) the counts of the most recent stage --

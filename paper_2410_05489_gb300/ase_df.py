@@ -79,6 +79,7 @@ def _load():
         "ase_df_gks_step": ([CTX, _VP, _VP, _VP, _c.c_double, _VP], _c.c_int),
         "ase_df_get_status": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_double), _c.POINTER(_c.c_double)], _c.c_int),
         "ase_df_reset": ([CTX, _c.c_double, _VP], _c.c_int),
+        "ase_df_selftest_wait": ([CTX, _VP], _c.c_int),
         "ase_df_get_repair_stats": ([CTX, _c.POINTER(_c.c_uint32), _c.POINTER(_c.c_uint64),
                                      _c.POINTER(_c.c_uint64)], _c.c_int),
         "ase_df_last_error": ([CTX], _c.c_char_p),
@@ -197,9 +198,14 @@ def ase_df_get_status(ctx) -> Tuple[int, float, float]:
     dt = _c.c_double()
     t = _c.c_double()
     st = _load().ase_df_get_status(ctx, _c.byref(flags), _c.byref(dt), _c.byref(t))
-    if st not in (ASE_DF_OK, 4):
+    if st not in (ASE_DF_OK, 4, 5):  # non-physical and timeout are reported through the flags
         _check(ctx, st)
     return int(flags.value), float(dt.value), float(t.value)
+
+
+def ase_df_selftest_wait(ctx, stream=None) -> None:
+    """A device wait that runs out (about a second): raises FLAG_SYNC in the status word."""
+    _check(ctx, _load().ase_df_selftest_wait(ctx, _stream(stream)))
 
 
 def ase_df_get_repair_stats(ctx):

@@ -906,7 +906,17 @@ ase_df_status ase_df_get_status(ase_df_ctx* c, uint32_t* flags, double* last_dt,
   if (flags) *flags = h.flags;
   if (last_dt) *last_dt = h.last_dt;
   if (t) *t = h.t;
+  if (h.flags & ASE_DF_FLAG_SYNC) return fail(c, ASE_DF_E_TIMEOUT, "a grid barrier on the device gave up waiting");
   if (h.flags & ASE_DF_FLAG_NONPHYSICAL) return fail(c, ASE_DF_E_NONPHYSICAL, "non-physical state on the device");
+  return ASE_DF_OK;
+}
+
+ase_df_status ase_df_selftest_wait(ase_df_ctx* c, void* stream) {
+  if (!c) return ASE_DF_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  cudaError_t e = launch_wait_selftest(c->st, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "wait self-test");
   return ASE_DF_OK;
 }
 

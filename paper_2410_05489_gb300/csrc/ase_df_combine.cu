@@ -42,8 +42,10 @@ __global__ void __launch_bounds__(256) combine_kernel(const GridInfo g, const Co
 // status word.  Thread 0 of each CTA arrives; the last arrival resets the count and
 // advances the generation, the others wait for it.  The wait gives up after a bounded
 // number of polls (about a second), raises ASE_DF_FLAG_SYNC and returns false, so that a
-// barrier that cannot complete ends the kernel instead of holding the GPU.
-__device__ bool grid_barrier(DevState* st) {
+// barrier that cannot complete ends the kernel instead of holding the GPU.  `extra` raises the
+// arrival count the barrier waits for (0 in the solver; 1 in the self-test of the wait, which
+// can then never complete).
+__device__ bool grid_barrier(DevState* st, unsigned int extra = 0u) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -51,7 +53,7 @@ __device__ bool grid_barrier(DevState* st) {
     const unsigned int g0 = *gen;
     __threadfence();  // this CTA's writes before the arrival
     ok = 1;
-    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1 + extra) {
       st->bar_count = 0u;
       __threadfence();
       atomicAdd(&st->bar_gen, 1u);
@@ -90,6 +92,9 @@ __global__ void __launch_bounds__(256) repair_all_kernel(const GridInfo g, Repai
   freeze_range<DIM>(g, a, first, ncell, stride);
 }
 
+// Self-test of the bounded wait: a barrier that expects one CTA more than the grid has.
+__global__ void __launch_bounds__(256) wait_selftest_kernel(DevState* st) { grid_barrier(st, 1u); }
+
 template <int DIM>
 __global__ void __launch_bounds__(256) max_speed_kernel(const GridInfo g, const SpeedArgs a) {
   const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
@@ -107,6 +112,8 @@ __global__ void state_kernel(DevState* st, int op, double t) {
     st->frozen_total = 0ull;
     st->bar_count = 0u;
     st->bar_gen = 0u;
+  } else if (op == 2) {  // the barrier's arrivals after a barrier that gave up
+    st->bar_count = 0u;
   }
 }
 
@@ -166,6 +173,22 @@ cudaError_t repair_all_launch(const GridInfo& g, const RepairArgs& a, cudaStream
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, repair_all_kernel<DIM>, g, a);
+}
+
+cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);  // two CTAs, both resident (cooperative launch)
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, wait_selftest_kernel, st);
+  if (e != cudaSuccess) return e;
+  state_kernel<<<1, 1, 0, s>>>(st, 2, 0.0);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_repair_all(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s) {

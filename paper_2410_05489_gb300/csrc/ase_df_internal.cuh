@@ -214,6 +214,9 @@ cudaError_t launch_max_speed(int dim, const GridInfo& g, const SpeedArgs& a, cud
 // All repair passes and the freeze of one stage in one cooperative launch (returns at once
 // when the stage update was physical everywhere; a grid barrier between passes).
 cudaError_t launch_repair_all(int dim, const GridInfo& g, const RepairArgs& a, cudaStream_t s);
+// A grid barrier that cannot complete (self-test of the bounded wait): raises
+// ASE_DF_FLAG_SYNC after about a second, then clears the barrier's arrival count.
+cudaError_t launch_wait_selftest(DevState* st, cudaStream_t s);
 cudaError_t launch_state_kernel(DevState* st, int op, double t, cudaStream_t s);
 
 // Tables of scheme order r (host, exact rational arithmetic, no allocation); false only if a

@@ -87,3 +87,36 @@ def test_bad_configuration_is_refused(A):
     with pytest.raises(A.AseDfError) as ei:
         A.Solver(P.Problem(ndim=2, nx=3, ny=8, order=9, bc=("reflect", "reflect", "outflow", "outflow")))
     assert ei.value.status == 1
+
+
+def test_bounded_wait_runs_out_and_reports_timeout(A):
+    """Failure detection without a GPU fault: a grid barrier that can never complete (it waits
+    for one CTA more than its grid has) gives up after its poll limit, raises FLAG_SYNC and
+    returns. ase_df_get_status then reports ASE_DF_E_TIMEOUT and the context stays usable: after
+    a reset, steps whose positivity repair runs its passes through the same barrier complete
+    without the flag, as before."""
+    import time
+
+    import torch
+    from test_oracle_scheme import near_vacuum_1d
+
+    pb, W0 = near_vacuum_1d()
+    s = A.Solver(pb, W0)
+    try:
+        t0 = time.perf_counter()
+        A.ase_df_selftest_wait(s.ctx)
+        torch.cuda.synchronize()
+        waited = time.perf_counter() - t0
+        flags, _, _ = s.status()
+        assert flags & A.FLAG_SYNC
+        assert A._load().ase_df_get_status(s.ctx, None, None, None) == 5  # ASE_DF_E_TIMEOUT
+        assert waited < 30.0, waited
+        s.set_state(W0)  # ase_df_reset: clears the status word and the barrier's counters
+        for _ in range(30):
+            s.step()
+        flags, _, _ = s.status()
+        assert not flags & (A.FLAG_SYNC | A.FLAG_NONPHYSICAL), flags
+        _, repaired, _ = A.ase_df_get_repair_stats(s.ctx)
+        assert repaired > 0  # the repair's passes ran through the barrier
+    finally:
+        s.close()
