@@ -149,18 +149,17 @@ cudaError_t launch_combine(int dim, const GridInfo& g, const CombineArgs& a, cud
 
 template <int DIM>
 cudaError_t repair_all_launch(const GridInfo& g, const RepairArgs& a, cudaStream_t s) {
-  // resident CTAs of this kernel on the device, once per process and dimension
-  static std::atomic<int> resident{0};
-  int nres = resident.load();
-  if (nres == 0) {
-    int dev = 0, nsm = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_all_kernel<DIM>, 256, 0);
+  // resident CTAs of this kernel: its CTAs per SM (a property of the kernel on this
+  // architecture, found once per dimension) times the current device's SMs
+  static std::atomic<int> per_sm_cache{0};
+  int per_sm = per_sm_cache.load();
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, repair_all_kernel<DIM>, 256, 0);
     if (e != cudaSuccess) return e;
-    nres = std::max(1, nsm * per_sm);
-    resident.store(nres);
+    per_sm = std::max(1, per_sm);
+    per_sm_cache.store(per_sm);
   }
+  const int nres = per_sm * device_sm_count();
   const size_t ncell = (size_t)g.nx * g.ny;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)std::min<size_t>((size_t)nres, (ncell + 255) / 256));
